@@ -1,0 +1,370 @@
+"""Benchmark of the DE/rand/1 generation step on one GB300 (or N replicas).
+
+Workload (default): the largest single-instance configuration, N = 16384
+individuals x D = 10000 genes, FP32, F = 0.5, Cr = 0.9, Rosenbrock on
+[-5.12, 5.12] with NEC (headline), plus binomial and classic exponential
+crossover and the Ackley objective as side-by-side variants. Both population
+buffers (0.66 GB each) exceed the 129 MB L2, so no flush is needed between
+steps. One step = one generation = one launch of the fused generation kernel.
+
+Prints ONE JSON line. Metric: individual-dims per second per generation
+(N * D * steps / device time), with the HBM roofline fraction of the
+generation kernel, a CPU-oracle baseline, an end-to-end figure through the C
+ABI with host buffers, and the clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (different
+seed); the value is the sum over ranks of N * D * K divided by the slowest
+rank's time ("replicas only": one population has no natural row sharding).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "individual·dims/s per DE generation (NEC vs bin vs seq-exp), % of HBM roofline"
+UNIT = "ind·dims/s"
+WORKLOAD = "rosenbrock_ackley_N16384_D10000"
+N_DEF, D_DEF, F_DEF, CR_DEF, SEED = 16384, 10000, 0.5, 0.9, 1
+BOXES = {"rosenbrock": (-5.12, 5.12), "ackley": (-30.0, 30.0)}
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "gen_nec_rosenbrock_N16384_D10000.md")
+KERNEL_SOURCES = ["common.cuh", "draws.cuh", "objectives.cuh", "gen_kernel.cuh", "philox.cuh"]
+
+
+def kernel_fingerprint() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2101_06599_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (fingerprint match); else None."""
+    try:
+        with open(PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    fp, traffic = None, None
+    for line in text.splitlines():
+        line = line.strip().strip("`").strip()
+        if line.startswith("kernel_fingerprint:"):
+            fp = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch_full_size:"):
+            try:
+                traffic = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                traffic = None
+    return traffic if fp == kernel_fingerprint() else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.2)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(N, D, gens, d_accepts, d_masked):
+    """Bytes a generation must move: every parent row (4 N D), the three donor
+    genes of every masked gene (12 M), every accepted row (4 A D), and per row
+    its fitness read, slot byte read and write (6 N) plus the fitness write of
+    accepted rows (4 A)."""
+    return 4.0 * N * D * gens + 12.0 * d_masked + 4.0 * d_accepts * D + 6.0 * N * gens + 4.0 * d_accepts
+
+
+def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, sampler=None):
+    lo, hi = BOXES[obj]
+    opt = DE.Optimizer(N, D, F=F_DEF, CR=CR_DEF, xo=xo, obj=obj, bounds=(lo, hi), seed=seed)
+    try:
+        s = opt.stream
+        opt.run(warmup)
+        if ramp_s > 0:
+            t0 = time.time()
+            while time.time() - t0 < ramp_s:
+                opt.run(warmup)
+                opt.synchronize()
+        opt.synchronize()
+        st0 = opt.stats()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(s)
+        opt.run(steps)
+        ev1.record(s)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        barrier()
+        st1 = opt.stats()
+        d_acc = st1["accepts"] - st0["accepts"]
+        d_msk = st1["masked_genes"] - st0["masked_genes"]
+        threads, vec = opt.launch()
+        return opt, ms, d_acc, d_msk, (threads, vec)
+    except Exception:
+        opt.close()
+        raise
+
+
+_dist = None
+
+
+def barrier():
+    if _dist is not None:
+        _dist.barrier()
+
+
+def max_over_ranks(torch, v):
+    if _dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    _dist.all_reduce(t, op=_dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(torch, v):
+    if _dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    _dist.all_reduce(t, op=_dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_generation_rate(N, D, obj, xo, budget_s, rows_per_step=None, steps=None, warmup=0):
+    """Time the CPU oracle (single thread) on generations of the same workload.
+    Returns (ind_dims_per_s, rows_per_step, steps_timed, seconds)."""
+    import oracle as O
+    lo, hi = BOXES[obj]
+    pop = O.init(N, D, lo, hi, SEED)
+    fit = O.evaluate(obj, pop)
+    if rows_per_step is None:
+        t0 = time.perf_counter()
+        O.step(pop, fit, F_DEF, CR_DEF, xo, obj, lo, hi, SEED, 0, rows=(0, 64), want_trial=False)
+        per_row = (time.perf_counter() - t0) / 64
+        n_steps = steps if steps else 1
+        rows_per_step = int(max(64, min(N, budget_s / max(n_steps, 1) / max(per_row, 1e-9))))
+    g = 0
+    for _ in range(warmup):
+        r = O.step(pop, fit, F_DEF, CR_DEF, xo, obj, lo, hi, SEED, g, rows=(0, rows_per_step), want_trial=False)
+        pop, fit, g = r.pop, r.fit, g + 1
+    timed, t_tot = 0, 0.0
+    target_steps = steps if steps else None
+    while True:
+        t0 = time.perf_counter()
+        r = O.step(pop, fit, F_DEF, CR_DEF, xo, obj, lo, hi, SEED, g, rows=(0, rows_per_step), want_trial=False)
+        t_tot += time.perf_counter() - t0
+        pop, fit, g, timed = r.pop, r.fit, g + 1, timed + 1
+        if target_steps is not None:
+            if timed >= target_steps:
+                break
+        elif t_tot >= budget_s:
+            break
+    return rows_per_step * D * timed / t_tot, rows_per_step, timed, t_tot
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps, warmup = args.steps, args.warmup
+    budget = 150.0
+    rate, rows, timed, secs = oracle_generation_rate(N_DEF, D_DEF, "rosenbrock", "nec", budget,
+                                                     steps=steps, warmup=warmup)
+    sample = ("%d oracle generations over rows [0, %d) of the N=%d, D=%d Rosenbrock population "
+              "(donors from all N rows), NEC, F=0.5, Cr=0.9; single thread" % (timed, rows, N_DEF, D_DEF))
+    line = {
+        "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": timed,
+        "warmup": warmup, "ms_per_step": 1e3 * secs / timed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 mutation, f64 fitness", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "objective": "rosenbrock", "crossover": "nec", "N": N_DEF,
+                   "D": D_DEF, "F": F_DEF, "CR": CR_DEF},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2101_06599_gb300 import de as DE
+
+    global _dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        _dist = dist
+    DE.load_library()
+    N, D, K, W = N_DEF, D_DEF, args.steps, args.warmup
+    seed = SEED + rank
+
+    # headline: NEC on Rosenbrock, clocks sampled across the ramp and the timed region
+    with ClockSampler(local) as clk:
+        opt, ms, d_acc, d_msk, shape = time_variant(DE, torch, N, D, "nec", "rosenbrock", K, W, seed,
+                                                    ramp_s=1.0)
+    ms_max = max_over_ranks(torch, ms)
+    units = float(N) * D * K
+    value = sum_over_ranks(torch, units) / (ms_max / 1e3)
+    bytes_alg = algorithmic_bytes(N, D, K, d_acc, d_msk)
+    avg_launch_s = ms / 1e3 / K
+    peak, peak_src = measured_hbm_peak()
+    achieved = bytes_alg / K / avg_launch_s / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_src,
+                "kernel": "gen_kernel<NEC, Rosenbrock, vec4=%d> x %d threads/row" % (shape[1], shape[0]),
+                "algorithmic_bytes_per_launch": bytes_alg / K, "avg_launch_us": avg_launch_s * 1e6,
+                "m_masked_fraction": d_msk / (N * D * K), "a_acceptance": d_acc / (N * K)}
+
+    # end to end through the C ABI with host buffers: upload the population from
+    # pinned memory (evaluated on the device), K generations, best row + value read back each step
+    e2e = None
+    if not args.no_e2e:
+        from paper_2101_06599_gb300 import workloads as Wk
+        host = torch.from_numpy(Wk.population(N, D, *BOXES["rosenbrock"], seed + 1000)).pin_memory()
+        host_np = host.numpy()
+        xbest = torch.empty(D, dtype=torch.float32).pin_memory().numpy()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        DE.de_set_population(opt.ctx, host_np, None)
+        for _ in range(K):
+            DE.de_step(opt.ctx)
+            DE.de_best(opt.ctx, xbest)
+        t1 = time.perf_counter()
+        e2e_s = max_over_ranks(torch, t1 - t0)
+        e2e = {"value": sum_over_ranks(torch, units) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 4.0 * N * D / K, "d2h_bytes_per_step": 4.0 * D + 32,
+               "job": "de_set_population(host pinned N x D) + %d x (de_step + de_best to host)" % K}
+    opt.close()
+
+    variants = {}
+    if not args.no_variants:
+        for obj in ("rosenbrock", "ackley"):
+            for xo in ("nec", "bin", "exp"):
+                o2, ms2, a2, m2, sh2 = time_variant(DE, torch, N, D, xo, obj, K, W, seed)
+                o2.close()
+                b2 = algorithmic_bytes(N, D, K, a2, m2)
+                ach2 = b2 / (ms2 / 1e3) / 1e9
+                variants.setdefault(obj, {})[xo] = {
+                    "value": units / (ms2 / 1e3), "ms_per_gen": ms2 / K, "hbm_gbs": ach2, "frac": ach2 / peak,
+                    "m": m2 / (N * D * K), "a": a2 / (N * K), "launch": list(sh2)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, rows, timed, secs = oracle_generation_rate(N, D, "rosenbrock", "nec", 12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d generation(s) of the CPU oracle over rows [0, %d) of the same N=%d x D=%d "
+                         "Rosenbrock/NEC workload (donors from all N rows), %.1f s, single thread"
+                         % (timed, rows, N, D, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "objective": "rosenbrock", "crossover": "nec", "N": N, "D": D,
+                       "F": F_DEF, "CR": CR_DEF, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (two 0.66 GB population buffers), no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
+            "clocks": clk.summary(), "variants": variants,
+        }
+        print(json.dumps(line))
+    if _dist is not None:
+        _dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * de.h — C ABI of the GB300 (sm_103a) differential-evolution generation
+ * library (libde.so).
+ *
+ * The method is DE/rand/1 as parallelised in Pan, "Performance Analysis and
+ * Improvement of Parallel Differential Evolution" (arXiv 2101.06599):
+ * one generation = donor draws, crossover mask (binomial, Eq. 2 / Alg. 7;
+ * classic exponential, Alg. 8; new exponential crossover NEC, Eq. 9 with
+ * Alg. 9 / Alg. 10), differential mutation on the masked genes (Eq. 1),
+ * bound repair, evaluation of the whole trial population, and greedy
+ * selection (Alg. 2). The calls follow the paper's statement of the problem:
+ * parameters Cr, F, Np and a stop criterion (Alg. 1 / Alg. 2, first line),
+ * evaluation as its own stage (Section 2, before Alg. 2), best value and best
+ * generation as outputs (Tables III-V).
+ *
+ * Conventions for every call:
+ *  - Return value: DE_OK (0) or a positive de_status code; nothing calls
+ *    exit/abort and no kernel traps. de_strerror() names a code.
+ *  - Host pointers are caller-owned, read or written during the call only,
+ *    never retained. Host arrays are dense row-major (row length D floats).
+ *  - Device memory is owned by the context, obtained from the allocator set
+ *    with de_set_allocator (cudaMalloc if none), and released by
+ *    de_destroy.
+ *  - Work is queued on the CUDA stream given to de_create (NULL = legacy
+ *    default stream). de_step/de_run only enqueue; errors raised by queued
+ *    work surface at the next call that synchronises (de_best, de_stats,
+ *    de_get_population, de_save, de_synchronize) as DE_ECUDA.
+ *  - A context is not thread-safe; use one host thread per context.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key (seed low
+ * word, seed high word) and counter (block, row, generation, stream<<24 |
+ * instance). Every draw is a pure function of (seed, instance, generation,
+ * row), so draws do not depend on the launch shape, and de_save/de_load
+ * resume bit-identically. FP32 fitness sums are reduced in a fixed order
+ * set by the launch shape (de_set_launch), so a run is deterministic for a
+ * given shape.
+ */
+#ifndef DE_H
+#define DE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef enum {
+  DE_OK = 0,
+  DE_EINVAL = 1,       /* invalid argument (see each call)                   */
+  DE_ENOMEM = 2,       /* device or host allocation failed                   */
+  DE_ECUDA = 3,        /* a CUDA runtime call or queued kernel failed        */
+  DE_ETIMEOUT = 4,     /* a bounded device-side wait gave up                 */
+  DE_ESTATE = 5,       /* call not valid for this context's state            */
+  DE_EUNSUPPORTED = 6  /* valid request this build does not implement        */
+} de_status;
+
+/* ---- crossover (Section 3) -------------------------------------------- */
+typedef enum {
+  DE_XOVER_BIN = 0,    /* binomial: gene j crosses iff rand < Cr or j = j_rand (Eq. 2, Alg. 7) */
+  DE_XOVER_EXP = 1,    /* classic exponential: sequential walk from j_rand (Alg. 8)            */
+  DE_XOVER_NEC = 2     /* new exponential: L from Eq. (9), genes ((j - j_rand) mod D) < L       */
+} de_crossover;
+
+/* ---- objectives -------------------------------------------------------- */
+typedef enum {
+  DE_OBJ_SPHERE = 0,        /* sum x^2                                            */
+  DE_OBJ_RASTRIGIN = 1,     /* 10 D + sum (x^2 - 10 cos 2 pi x)                   */
+  DE_OBJ_ACKLEY = 2,        /* Section 4; inner constant b (de_objparams)          */
+  DE_OBJ_ROSENBROCK = 3,    /* Section 4: sum_{j<D-1} 100 (x_j^2 - x_{j+1})^2 + (1 - x_j)^2 */
+  DE_OBJ_GRIEWANK = 4,      /* Section 4: sum x^2 / 4000 - prod cos(x_j / sqrt j) + 1 */
+  DE_OBJ_ELLIPTIC = 5,      /* sum 10^(6 j / (D-1)) x_j^2, j = 0 .. D-1            */
+  DE_OBJ_SR_RASTRIGIN = 6,  /* Rastrigin of z = R (x - o)                          */
+  DE_OBJ_SR_ELLIPTIC = 7    /* elliptic of z = R (x - o)                           */
+} de_objective;
+
+/* Precision of the z = R (x - o) product of the shifted-rotated objectives. */
+typedef enum { DE_PREC_FP32 = 0, DE_PREC_TF32 = 1, DE_PREC_BF16 = 2 } de_precision;
+
+/* Search box, the same for every dimension (Section 4 gives one interval
+ * per function). Requires lo < hi, both finite. Trial genes are clipped to
+ * [lo, hi] (bound repair; the paper names none). */
+typedef struct { float lo, hi; } de_bounds;
+
+/* Optional objective parameters; pass NULL for the defaults. */
+typedef struct {
+  double ackley_b;          /* Ackley inner constant; 0 selects 0.2 (Section 4 prints 0.02) */
+  const float *shift;       /* host, D floats: o of the shifted-rotated objectives (copied) */
+  const float *rotation;    /* host, D*D floats, row-major R (copied)                       */
+  de_precision prec;        /* shifted-rotated objectives: product precision                */
+  int32_t incumbent_every;  /* shifted-rotated: FP64 re-evaluation of the best every K
+                               generations (0 selects 50)                                  */
+} de_objparams;
+
+/* Counters kept on the device and read by de_stats. */
+typedef struct {
+  int64_t generation;       /* generations completed                                     */
+  uint64_t accepts;         /* trials that replaced their parent, summed over generations */
+  uint64_t masked_genes;    /* genes taken from the mutant: sum of L (exp, NEC) or of the
+                               mask popcount (bin), summed over generations               */
+  uint64_t reselected;      /* shifted-rotated, low precision: rows re-evaluated in FP32  */
+  int64_t best_gen;         /* generation at which the best value last strictly improved  */
+  double best_f;            /* best fitness (FP32 value, widened)                          */
+  int32_t best_index;       /* row holding it; lowest index on ties                       */
+} de_stats_t;
+
+typedef struct de_ctx de_ctx;
+
+/* ---- device memory ----------------------------------------------------- */
+/* Allocator used by every later de_create / de_batch_create. alloc returns a
+ * device pointer of at least `bytes` bytes aligned to 256 bytes, or NULL;
+ * free releases it. `stream` is the context's stream. Pass NULL, NULL to go
+ * back to cudaMalloc/cudaFree. Process-wide; not thread-safe. */
+typedef void *(*de_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*de_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+int de_set_allocator(de_alloc_fn alloc, de_free_fn free_fn, void *user);
+
+/* ---- lifecycle --------------------------------------------------------- */
+/* Create a population of N individuals with D genes (Alg. 2, first lines):
+ * x_ij = clip(lo + (hi - lo) * u_ij) with u_ij = (w >> 8) * 2^-24 from
+ * Philox stream 0, then evaluate every row (the call returns after this
+ * set-up has finished on the device).
+ *   N >= 4 (three distinct donors other than i), N < 2^31 / 4;
+ *   1 <= D <= 32768; N * D < 2^40;
+ *   F finite; CR in [0, 1]; xo and obj valid enum values;
+ *   shifted-rotated objectives need p->shift and p->rotation.
+ * Errors: DE_EINVAL, DE_ENOMEM, DE_ECUDA, DE_EUNSUPPORTED. */
+int de_create(de_ctx **out, int32_t N, int32_t D, float F, double CR,
+              de_crossover xo, de_objective obj, const de_objparams *p,
+              de_bounds b, uint64_t seed, void *cuda_stream);
+
+/* Release every buffer of the context (synchronises its stream). NULL is a no-op. */
+void de_destroy(de_ctx *ctx);
+
+/* ---- generations (Alg. 2, loop body) ----------------------------------- */
+/* Enqueue one generation: draws, crossover, mutation of masked genes, clip,
+ * evaluation of every trial (FP32), strict '<' selection, best tracking. */
+int de_step(de_ctx *ctx);
+
+/* Enqueue `generations` (>= 0) generations. Runs of 2 or more are captured
+ * once per distinct count into a CUDA graph and replayed. */
+int de_run(de_ctx *ctx, int32_t generations);
+
+/* Block until the context's stream is idle; DE_ECUDA if queued work failed. */
+int de_synchronize(de_ctx *ctx);
+
+/* ---- results ----------------------------------------------------------- */
+/* Best individual so far (synchronises). Any output pointer may be NULL.
+ * x_out: host, D floats. f_out: its fitness. idx_out: its row (lowest index
+ * on ties). best_gen_out: generation of the last strict improvement (0 =
+ * the initial population). */
+int de_best(de_ctx *ctx, float *x_out, double *f_out, int32_t *idx_out,
+            int64_t *best_gen_out);
+
+/* Device counters (synchronises). */
+int de_stats(de_ctx *ctx, de_stats_t *out);
+
+/* Copy the population (host N x D floats) and fitness (host N floats) out;
+ * either may be NULL (synchronises). */
+int de_get_population(de_ctx *ctx, float *pop_out, float *fit_out);
+
+/* Replace the population with host N x D floats. fit = NULL evaluates every
+ * row on the device; otherwise N host floats are taken as given. The best
+ * is recomputed and best_gen set to the current generation. Genes are taken
+ * as given (not clipped). Synchronises. */
+int de_set_population(de_ctx *ctx, const float *pop, const float *fit);
+
+/* ---- checkpoint / resume ----------------------------------------------- */
+/* Serialise the whole state (parameters, generation, counters, best,
+ * population, fitness). With buf = NULL, *len receives the size needed;
+ * otherwise *len must be at least that and receives the bytes written.
+ * Synchronises. */
+int de_save(de_ctx *ctx, void *buf, size_t *len);
+
+/* Restore a state saved by de_save into a context created with the same N,
+ * D, F, CR, crossover, objective, bounds and seed (DE_EINVAL otherwise).
+ * The resumed run is bit-identical to an uninterrupted one. */
+int de_load(de_ctx *ctx, const void *buf, size_t len);
+
+/* ---- test hook ----------------------------------------------------------- */
+/* Run one generation exactly like de_step and also report, per row, the
+ * trial vector (host N x D floats), its FP32 fitness (N floats), the
+ * selection decision (N bytes, 1 = accepted) and the draws (N x 5 int32:
+ * r1, r2, r3, j_rand, L where L is the segment length for exp/NEC and the
+ * mask popcount for bin). Any output may be NULL. Synchronises. */
+int de_debug_step(de_ctx *ctx, float *trial_out, float *ftrial_out,
+                  uint8_t *accept_out, int32_t *draws_out);
+
+/* ---- batched instances --------------------------------------------------- */
+/* One independent DE problem of a batch. */
+typedef struct {
+  int32_t N, D;
+  float F;
+  double CR;
+  de_crossover xo;
+  de_objective obj;          /* non-rotated objectives only */
+  de_bounds b;
+} de_instance_spec;
+
+/* Create a context running n_inst independent instances; instance k draws
+ * from Philox instance field k (k < 2^24). de_step / de_run advance every
+ * instance by one generation per step. Same per-instance limits as
+ * de_create. */
+int de_batch_create(de_ctx **out, int32_t n_inst, const de_instance_spec *specs,
+                    uint64_t seed, void *cuda_stream);
+
+/* Best of instance `inst` (synchronises); outputs as de_best, x_out has the
+ * instance's D floats. */
+int de_batch_best(de_ctx *ctx, int32_t inst, float *x_out, double *f_out,
+                  int32_t *idx_out, int64_t *best_gen_out);
+
+/* ---- launch shape --------------------------------------------------------- */
+/* Each row is processed by one CTA of `threads` threads (multiple of 32,
+ * <= 512), each holding `vec4` float4 slots of the row in registers (vec4 in
+ * {1, 2, 4, 8, 16}); threads * vec4 * 4 must cover D. de_create picks a
+ * shape; this overrides it (tuning only: draws are unchanged, FP32 fitness
+ * rounding may change). DE_EINVAL if the shape does not fit. */
+int de_set_launch(de_ctx *ctx, int32_t threads, int32_t vec4);
+int de_get_launch(de_ctx *ctx, int32_t *threads, int32_t *vec4);
+
+/* ---- misc ----------------------------------------------------------------- */
+const char *de_strerror(int code);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int de_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DE_H */

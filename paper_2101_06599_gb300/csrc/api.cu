@@ -1,0 +1,548 @@
+// api.cu — the C ABI of libde.so (declarations and contracts in include/de.h).
+//
+// Host responsibilities only: argument validation, device buffers, the
+// NEC threshold table, launch-shape choice, CUDA-graph capture of de_run,
+// checkpoints. Every step of a generation runs in the device kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/de.h"
+#include "internal.h"
+
+using namespace de;
+
+namespace {
+
+de_alloc_fn g_alloc = nullptr;
+de_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
+struct Block {
+  void* ptr;
+  size_t bytes;
+};
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? DE_OK : DE_ECUDA; }
+
+}  // namespace
+
+struct de_ctx {
+  int32_t N = 0, D = 0, pitch = 0, D4 = 0;
+  float F = 0.f;
+  double CR = 0.0;
+  int xo = 0, obj = 0;
+  de_bounds b{0.f, 0.f};
+  uint64_t seed = 0;
+  uint32_t inst = 0;
+  double ackley_b = 0.2;
+  cudaStream_t stream = nullptr;
+  int block = 32, vidx = 0;
+  GenParams p{};
+  std::vector<Block> blocks;
+  std::map<int32_t, cudaGraphExec_t> graphs;
+  void* staging = nullptr;       // device: best row gather
+  void* host_pinned = nullptr;   // host: staging copy and state reads
+  size_t host_pinned_bytes = 0;
+  long long host_gen = 0;
+};
+
+namespace {
+
+void* ctx_alloc(de_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (g_alloc) {
+    p = g_alloc(bytes, (void*)c->stream, g_alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->blocks.push_back({p, bytes});
+  return p;
+}
+
+void ctx_free(de_ctx* c, void* p) {
+  for (size_t k = 0; k < c->blocks.size(); ++k) {
+    if (c->blocks[k].ptr == p) {
+      if (g_free) g_free(p, c->blocks[k].bytes, (void*)c->stream, g_alloc_user);
+      else cudaFree(p);
+      c->blocks.erase(c->blocks.begin() + (long)k);
+      return;
+    }
+  }
+}
+
+void drop_graphs(de_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+// Launch shape: T threads (multiple of 32, <= 512) x V float4 slots per
+// thread with T * V >= D4. Prefer the smallest V whose T fits in 256
+// threads, else in 512.
+void choose_launch(int D4, int& block, int& vidx) {
+  for (int limit : {256, 512}) {
+    for (int k = 0; k < 5; ++k) {
+      const int V = kVecChoices[k];
+      int T = (D4 + V - 1) / V;
+      T = ((T + 31) / 32) * 32;
+      if (T <= limit) {
+        block = T;
+        vidx = k;
+        return;
+      }
+    }
+  }
+  block = 512;
+  vidx = 4;
+}
+
+bool is_rotated(int obj) { return obj == DE_OBJ_SR_RASTRIGIN || obj == DE_OBJ_SR_ELLIPTIC; }
+
+cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
+  switch (c->xo) {
+    case DE_XOVER_BIN: return launch_gen_bin(c->obj, c->vidx, p, c->block, c->stream);
+    case DE_XOVER_EXP: return launch_gen_exp(c->obj, c->vidx, p, c->block, c->stream);
+    default: return launch_gen_nec(c->obj, c->vidx, p, c->block, c->stream);
+  }
+}
+
+int evaluate_population(de_ctx* c) {
+  cudaError_t e = launch_reset_best(c->p, c->stream);
+  if (e == cudaSuccess) e = launch_eval(c->obj, c->vidx, c->p, c->block, c->stream);
+  if (e == cudaSuccess) e = launch_close_eval(c->p, c->stream);
+  return cuda_status(e);
+}
+
+int sync_stream(de_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return DE_ECUDA;
+  return cuda_status(cudaGetLastError());
+}
+
+constexpr uint32_t kSaveMagic = 0x42474544u;   // "DEGB"
+constexpr uint32_t kSaveVersion = 1u;
+
+struct SaveHeader {
+  uint32_t magic, version;
+  int32_t N, D;
+  float F, lo, hi, pad0;
+  double CR, ackley_b;
+  int32_t xo, obj;
+  uint64_t seed;
+  uint32_t inst, pad1;
+  DevState st;
+};
+
+}  // namespace
+
+extern "C" {
+
+int de_version(void) { return 100; }
+
+const char* de_strerror(int code) {
+  switch (code) {
+    case DE_OK: return "ok";
+    case DE_EINVAL: return "invalid argument";
+    case DE_ENOMEM: return "out of memory";
+    case DE_ECUDA: return "CUDA error";
+    case DE_ETIMEOUT: return "device-side wait timed out";
+    case DE_ESTATE: return "call not valid in this state";
+    case DE_EUNSUPPORTED: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+int de_set_allocator(de_alloc_fn alloc, de_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return DE_EINVAL;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return DE_OK;
+}
+
+void de_destroy(de_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  while (!c->blocks.empty()) ctx_free(c, c->blocks.back().ptr);
+  if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  delete c;
+}
+
+int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossover xo,
+              de_objective obj, const de_objparams* prm, de_bounds b, uint64_t seed,
+              void* cuda_stream) {
+  if (!out) return DE_EINVAL;
+  *out = nullptr;
+  if (N < 4 || N > (1 << 29) || D < 1 || D > 32768) return DE_EINVAL;
+  if ((long long)N * (long long)D >= (1LL << 40)) return DE_EINVAL;
+  if (!std::isfinite(F) || !(CR >= 0.0 && CR <= 1.0)) return DE_EINVAL;
+  if ((int)xo < DE_XOVER_BIN || (int)xo > DE_XOVER_NEC) return DE_EINVAL;
+  if ((int)obj < DE_OBJ_SPHERE || (int)obj > DE_OBJ_SR_ELLIPTIC) return DE_EINVAL;
+  if (!std::isfinite(b.lo) || !std::isfinite(b.hi) || !(b.lo < b.hi)) return DE_EINVAL;
+  if (is_rotated(obj)) {
+    if (!prm || !prm->shift || !prm->rotation) return DE_EINVAL;
+    return DE_EUNSUPPORTED;
+  }
+  double ackley_b = 0.2;
+  if (prm && prm->ackley_b != 0.0) {
+    if (!std::isfinite(prm->ackley_b)) return DE_EINVAL;
+    ackley_b = prm->ackley_b;
+  }
+
+  de_ctx* c = new (std::nothrow) de_ctx();
+  if (!c) return DE_ENOMEM;
+  c->N = N;
+  c->D = D;
+  c->pitch = ((D + 7) / 8) * 8;
+  c->D4 = (D + 3) / 4;
+  c->F = F;
+  c->CR = CR;
+  c->xo = (int)xo;
+  c->obj = (int)obj;
+  c->b = b;
+  c->seed = seed;
+  c->inst = 0;
+  c->ackley_b = ackley_b;
+  c->stream = (cudaStream_t)cuda_stream;
+  choose_launch(c->D4, c->block, c->vidx);
+
+  // NEC thresholds T_n - 1, T_n = ceil(c_n 2^32), c_1 = Cr, c_n = fl(c_{n-1} Cr);
+  // stop before the first T_n <= 1 or at n = D - 1.
+  std::vector<uint32_t> tm1;
+  if (CR > 0.0 && CR < 1.0) {
+    double cn = CR;
+    for (int n = 1; n <= D - 1; ++n) {
+      const double Tn = std::ceil(cn * 4294967296.0);
+      if (Tn <= 1.0) break;
+      tm1.push_back((uint32_t)(Tn - 1.0));
+      cn = cn * CR;
+    }
+  }
+
+  const size_t pop_bytes = (size_t)N * (size_t)c->pitch * sizeof(float);
+  float* pop0 = (float*)ctx_alloc(c, pop_bytes);
+  float* pop1 = (float*)ctx_alloc(c, pop_bytes);
+  float* fit = (float*)ctx_alloc(c, (size_t)N * sizeof(float));
+  uint8_t* slots = (uint8_t*)ctx_alloc(c, 2 * (size_t)N);
+  DevState* st = (DevState*)ctx_alloc(c, sizeof(DevState));
+  uint32_t* nec = (uint32_t*)ctx_alloc(c, std::max<size_t>(1, tm1.size()) * sizeof(uint32_t));
+  c->staging = ctx_alloc(c, kStagingHeader + (size_t)c->pitch * sizeof(float));
+  c->host_pinned_bytes = std::max(kStagingHeader + (size_t)c->pitch * sizeof(float), sizeof(DevState));
+  if (!pop0 || !pop1 || !fit || !slots || !st || !nec || !c->staging ||
+      cudaMallocHost(&c->host_pinned, c->host_pinned_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    de_destroy(c);
+    return DE_ENOMEM;
+  }
+
+  GenParams& p = c->p;
+  p.pop0 = pop0;
+  p.pop1 = pop1;
+  p.fit = fit;
+  p.slots = slots;
+  p.st = st;
+  p.nec_tm1 = nec;
+  p.nT = (int)tm1.size();
+  p.N = N;
+  p.D = D;
+  p.pitch = c->pitch;
+  p.D4 = c->D4;
+  p.F = F;
+  p.lo = b.lo;
+  p.hi = b.hi;
+  p.cr_mode = (CR <= 0.0) ? kCrZero : (CR >= 1.0 ? kCrOne : kCrGeneral);
+  p.cr_t = (unsigned long long)std::ceil(CR * 4294967296.0);
+  p.key = Key2{(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32)};
+  p.inst = 0;
+  p.ackley_b = (float)ackley_b;
+  p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
+
+  DevState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.best_key = ~0ULL;
+  s0.best_f = INFINITY;
+  cudaError_t e = cudaMemsetAsync(pop0, 0, pop_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pop1, 0, pop_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, 2 * (size_t)N, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && !tm1.empty())
+    e = cudaMemcpyAsync(nec, tm1.data(), tm1.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_init(p, c->stream);
+  int rc = cuda_status(e);
+  if (rc == DE_OK) rc = evaluate_population(c);
+  // the threshold table lives in pageable memory: make sure it was consumed
+  if (rc == DE_OK) rc = sync_stream(c);
+  if (rc != DE_OK) {
+    de_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DE_OK;
+}
+
+int de_step(de_ctx* c) {
+  if (!c) return DE_EINVAL;
+  const int rc = cuda_status(launch_generation(c, c->p));
+  if (rc == DE_OK) c->host_gen++;
+  return rc;
+}
+
+int de_run(de_ctx* c, int32_t generations) {
+  if (!c || generations < 0) return DE_EINVAL;
+  if (generations == 0) return DE_OK;
+  if (generations == 1 || c->stream == nullptr) {
+    for (int32_t k = 0; k < generations; ++k) {
+      const int rc = de_step(c);
+      if (rc != DE_OK) return rc;
+    }
+    return DE_OK;
+  }
+  auto it = c->graphs.find(generations);
+  if (it == c->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return DE_ECUDA;
+    cudaError_t le = cudaSuccess;
+    for (int32_t k = 0; k < generations && le == cudaSuccess; ++k) le = launch_generation(c, c->p);
+    e = cudaStreamEndCapture(c->stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return DE_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return DE_ECUDA;
+    it = c->graphs.emplace(generations, exec).first;
+  }
+  const cudaError_t e = cudaGraphLaunch(it->second, c->stream);
+  if (e != cudaSuccess) return DE_ECUDA;
+  c->host_gen += generations;
+  return DE_OK;
+}
+
+int de_synchronize(de_ctx* c) {
+  if (!c) return DE_EINVAL;
+  return sync_stream(c);
+}
+
+int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* best_gen_out) {
+  if (!c) return DE_EINVAL;
+  cudaError_t e = launch_best_gather(c->p, c->staging, c->stream);
+  const size_t bytes = kStagingHeader + (size_t)c->D * sizeof(float);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->host_pinned, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return DE_ECUDA;
+  const int rc = sync_stream(c);
+  if (rc != DE_OK) return rc;
+  const unsigned char* h = static_cast<const unsigned char*>(c->host_pinned);
+  if (f_out) std::memcpy(f_out, h, sizeof(double));
+  if (best_gen_out) std::memcpy(best_gen_out, h + 8, sizeof(int64_t));
+  if (idx_out) std::memcpy(idx_out, h + 16, sizeof(int32_t));
+  if (x_out) std::memcpy(x_out, h + kStagingHeader, (size_t)c->D * sizeof(float));
+  return DE_OK;
+}
+
+int de_stats(de_ctx* c, de_stats_t* out) {
+  if (!c || !out) return DE_EINVAL;
+  if (cudaMemcpyAsync(c->host_pinned, c->p.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return DE_ECUDA;
+  const int rc = sync_stream(c);
+  if (rc != DE_OK) return rc;
+  DevState s;
+  std::memcpy(&s, c->host_pinned, sizeof(s));
+  out->generation = s.gen;
+  out->accepts = s.accepts;
+  out->masked_genes = s.masked;
+  out->reselected = s.reselected;
+  out->best_gen = s.best_gen;
+  out->best_f = (double)s.best_f;
+  out->best_index = (int32_t)(uint32_t)(s.best_key & 0xFFFFFFFFull);
+  return DE_OK;
+}
+
+int de_get_population(de_ctx* c, float* pop_out, float* fit_out) {
+  if (!c) return DE_EINVAL;
+  cudaError_t e = launch_normalize(c->p, c->stream);
+  if (e == cudaSuccess && pop_out)
+    e = cudaMemcpy2DAsync(pop_out, (size_t)c->D * sizeof(float), c->p.pop0, (size_t)c->pitch * sizeof(float),
+                          (size_t)c->D * sizeof(float), (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && fit_out)
+    e = cudaMemcpyAsync(fit_out, c->p.fit, (size_t)c->N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return DE_ECUDA;
+  return sync_stream(c);
+}
+
+int de_set_population(de_ctx* c, const float* pop, const float* fit) {
+  if (!c || !pop) return DE_EINVAL;
+  // the current generation's slot half is cleared: buffer 0 holds every row
+  cudaError_t e = cudaMemsetAsync(c->p.slots + (size_t)(c->host_gen & 1) * c->N, 0, (size_t)c->N, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(c->p.pop0, (size_t)c->pitch * sizeof(float), pop, (size_t)c->D * sizeof(float),
+                          (size_t)c->D * sizeof(float), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return DE_ECUDA;
+  int rc;
+  if (fit) {
+    e = cudaMemcpyAsync(c->p.fit, fit, (size_t)c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_reset_best(c->p, c->stream);
+    if (e == cudaSuccess) e = launch_best_from_fit(c->p, c->stream);
+    if (e == cudaSuccess) e = launch_close_eval(c->p, c->stream);
+    rc = cuda_status(e);
+  } else {
+    rc = evaluate_population(c);
+  }
+  if (rc != DE_OK) return rc;
+  return sync_stream(c);
+}
+
+int de_save(de_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return DE_EINVAL;
+  const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
+  if (!buf) {
+    *len = need;
+    return DE_OK;
+  }
+  if (*len < need) return DE_EINVAL;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  SaveHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kSaveMagic;
+  h.version = kSaveVersion;
+  h.N = c->N;
+  h.D = c->D;
+  h.F = c->F;
+  h.lo = c->b.lo;
+  h.hi = c->b.hi;
+  h.CR = c->CR;
+  h.ackley_b = c->ackley_b;
+  h.xo = c->xo;
+  h.obj = c->obj;
+  h.seed = c->seed;
+  h.inst = c->inst;
+  int rc = de_get_population(c, reinterpret_cast<float*>(o + sizeof(SaveHeader)),
+                             reinterpret_cast<float*>(o + sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float)));
+  if (rc != DE_OK) return rc;
+  if (cudaMemcpyAsync(c->host_pinned, c->p.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return DE_ECUDA;
+  rc = sync_stream(c);
+  if (rc != DE_OK) return rc;
+  std::memcpy(&h.st, c->host_pinned, sizeof(DevState));
+  std::memcpy(o, &h, sizeof(h));
+  *len = need;
+  return DE_OK;
+}
+
+int de_load(de_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf || len < sizeof(SaveHeader)) return DE_EINVAL;
+  SaveHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
+  if (h.magic != kSaveMagic || h.version != kSaveVersion || len < need) return DE_EINVAL;
+  if (h.N != c->N || h.D != c->D || h.F != c->F || h.CR != c->CR || h.xo != c->xo || h.obj != c->obj ||
+      h.lo != c->b.lo || h.hi != c->b.hi || h.seed != c->seed || h.inst != c->inst || h.ackley_b != c->ackley_b)
+    return DE_EINVAL;
+  if (h.st.gen < 0 || h.st.best_gen < 0 || h.st.best_gen > h.st.gen ||
+      (h.st.best_key & 0xFFFFFFFFull) >= (unsigned long long)c->N)
+    return DE_EINVAL;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  DevState s = h.st;
+  s.done = 0u;
+  cudaError_t e = cudaMemcpyAsync(c->p.st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->p.slots + (size_t)(s.gen & 1) * c->N, 0, (size_t)c->N, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(c->p.pop0, (size_t)c->pitch * sizeof(float), in + sizeof(SaveHeader),
+                          (size_t)c->D * sizeof(float), (size_t)c->D * sizeof(float), (size_t)c->N,
+                          cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->p.fit, in + sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float),
+                        (size_t)c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return DE_ECUDA;
+  const int rc = sync_stream(c);
+  if (rc == DE_OK) c->host_gen = s.gen;
+  return rc;
+}
+
+int de_debug_step(de_ctx* c, float* trial_out, float* ftrial_out, uint8_t* accept_out, int32_t* draws_out) {
+  if (!c) return DE_EINVAL;
+  GenParams p = c->p;
+  float* dtrial = trial_out ? (float*)ctx_alloc(c, (size_t)c->N * c->pitch * sizeof(float)) : nullptr;
+  float* dft = ftrial_out ? (float*)ctx_alloc(c, (size_t)c->N * sizeof(float)) : nullptr;
+  uint8_t* dacc = accept_out ? (uint8_t*)ctx_alloc(c, (size_t)c->N) : nullptr;
+  int* ddr = draws_out ? (int*)ctx_alloc(c, (size_t)c->N * 5 * sizeof(int)) : nullptr;
+  int rc = DE_OK;
+  if ((trial_out && !dtrial) || (ftrial_out && !dft) || (accept_out && !dacc) || (draws_out && !ddr)) rc = DE_ENOMEM;
+  if (rc == DE_OK) {
+    p.dbg_trial = dtrial;
+    p.dbg_ftrial = dft;
+    p.dbg_accept = dacc;
+    p.dbg_draws = ddr;
+    rc = cuda_status(launch_generation(c, p));
+    if (rc == DE_OK) c->host_gen++;
+  }
+  cudaError_t e = cudaSuccess;
+  if (rc == DE_OK && trial_out)
+    e = cudaMemcpy2DAsync(trial_out, (size_t)c->D * sizeof(float), dtrial, (size_t)c->pitch * sizeof(float),
+                          (size_t)c->D * sizeof(float), (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK && e == cudaSuccess && ftrial_out)
+    e = cudaMemcpyAsync(ftrial_out, dft, (size_t)c->N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK && e == cudaSuccess && accept_out)
+    e = cudaMemcpyAsync(accept_out, dacc, (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK && e == cudaSuccess && draws_out)
+    e = cudaMemcpyAsync(draws_out, ddr, (size_t)c->N * 5 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK) rc = (e == cudaSuccess) ? sync_stream(c) : DE_ECUDA;
+  else cudaStreamSynchronize(c->stream);
+  if (dtrial) ctx_free(c, dtrial);
+  if (dft) ctx_free(c, dft);
+  if (dacc) ctx_free(c, dacc);
+  if (ddr) ctx_free(c, ddr);
+  return rc;
+}
+
+int de_set_launch(de_ctx* c, int32_t threads, int32_t vec4) {
+  if (!c) return DE_EINVAL;
+  int vidx = -1;
+  for (int k = 0; k < 5; ++k)
+    if (kVecChoices[k] == vec4) vidx = k;
+  if (vidx < 0 || threads < 32 || threads > kMaxThreads || threads % 32 != 0) return DE_EINVAL;
+  if ((long long)threads * vec4 < c->D4) return DE_EINVAL;
+  c->block = threads;
+  c->vidx = vidx;
+  drop_graphs(c);
+  return DE_OK;
+}
+
+int de_get_launch(de_ctx* c, int32_t* threads, int32_t* vec4) {
+  if (!c) return DE_EINVAL;
+  if (threads) *threads = c->block;
+  if (vec4) *vec4 = kVecChoices[c->vidx];
+  return DE_OK;
+}
+
+int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs, uint64_t seed,
+                    void* cuda_stream) {
+  (void)n_inst; (void)specs; (void)seed; (void)cuda_stream;
+  if (!out) return DE_EINVAL;
+  *out = nullptr;
+  return DE_EUNSUPPORTED;
+}
+
+int de_batch_best(de_ctx* c, int32_t inst, float* x_out, double* f_out, int32_t* idx_out,
+                  int64_t* best_gen_out) {
+  (void)c; (void)inst; (void)x_out; (void)f_out; (void)idx_out; (void)best_gen_out;
+  return DE_EUNSUPPORTED;
+}
+
+}  // extern "C"

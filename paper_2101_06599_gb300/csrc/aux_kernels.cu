@@ -1,0 +1,156 @@
+// aux_kernels.cu — initial population, whole-population evaluation, best
+// tracking helpers and slot normalisation.
+#include "gen_kernel.cuh"
+#include "internal.h"
+
+namespace de {
+
+// Alg. 2, first lines: x_ij = clip(lo + (hi - lo) * u_ij), u_ij = (w >> 8) 2^-24,
+// with w = word j of the row's INIT stream; each operation rounded once.
+__global__ void init_kernel(const __grid_constant__ GenParams p) {
+  const size_t total = (size_t)p.N * (size_t)p.D4;
+  const float range = __fsub_rn(p.hi, p.lo);
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / (size_t)p.D4);
+    const int q = (int)(idx - (size_t)i * p.D4);
+    const uint4 w = philox_block(p.key, kStreamInit, p.inst, 0u, (uint32_t)i, (uint32_t)q);
+    float4 v;
+    const int j0 = 4 * q;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float u = (float)(word_of(w, (uint32_t)e) >> 8) * (1.0f / 16777216.0f);
+      const float xv = clip_box(__fadd_rn(p.lo, __fmul_rn(range, u)), p.lo, p.hi);
+      lane_of(v, e) = (j0 + e < p.D) ? xv : 0.0f;
+    }
+    reinterpret_cast<float4*>(p.pop0 + (size_t)i * p.pitch)[q] = v;
+  }
+}
+
+template <int OBJ, int V>
+__global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant__ GenParams p) {
+  __shared__ float red[4][32];
+  __shared__ float s_first[(OBJ == kRosenbrock) ? V : 1][32];
+  const int i = blockIdx.x;
+  const int t = threadIdx.x, T = blockDim.x;
+  const long long gen = p.st->gen;
+  const int si = p.slots[(size_t)(gen & 1) * p.N + i];
+  const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)i * p.pitch);
+  float4 x[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const int q = t + k * T;
+    x[k] = (q < p.D4) ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  int cnt = 0;
+  const float f = block_row_fitness<OBJ, V>(x, cnt, p, s_first, red);
+  if (t == 0) {
+    p.fit[i] = f;
+    atomicMin(&p.st->best_key, best_key_of(f, i));
+  }
+}
+
+template <int OBJ>
+static cudaError_t launch_eval_obj(int vidx, const GenParams& p, int block, cudaStream_t s) {
+  const dim3 grid((unsigned)p.N), blk((unsigned)block);
+  switch (vidx) {
+    case 0: eval_kernel<OBJ, 1><<<grid, blk, 0, s>>>(p); break;
+    case 1: eval_kernel<OBJ, 2><<<grid, blk, 0, s>>>(p); break;
+    case 2: eval_kernel<OBJ, 4><<<grid, blk, 0, s>>>(p); break;
+    case 3: eval_kernel<OBJ, 8><<<grid, blk, 0, s>>>(p); break;
+    case 4: eval_kernel<OBJ, 16><<<grid, blk, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(int obj, int vidx, const GenParams& p, int block, cudaStream_t s) {
+  switch (obj) {
+    case kSphere: return launch_eval_obj<kSphere>(vidx, p, block, s);
+    case kRastrigin: return launch_eval_obj<kRastrigin>(vidx, p, block, s);
+    case kAckley: return launch_eval_obj<kAckley>(vidx, p, block, s);
+    case kRosenbrock: return launch_eval_obj<kRosenbrock>(vidx, p, block, s);
+    case kGriewank: return launch_eval_obj<kGriewank>(vidx, p, block, s);
+    case kElliptic: return launch_eval_obj<kElliptic>(vidx, p, block, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+__global__ void reset_best_kernel(DevState* st) { st->best_key = ~0ULL; }
+
+__global__ void best_from_fit_kernel(const __grid_constant__ GenParams p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += gridDim.x * blockDim.x) {
+    float f = p.fit[i];
+    if (f != f) {
+      f = __int_as_float(0x7F800000);
+      p.fit[i] = f;
+    }
+    atomicMin(&p.st->best_key, best_key_of(f, i));
+  }
+}
+
+__global__ void close_eval_kernel(DevState* st) {
+  st->best_f = from_ordered_bits((uint32_t)(st->best_key >> 32));
+  st->best_gen = st->gen;
+  st->done = 0u;
+}
+
+__global__ void best_gather_kernel(const __grid_constant__ GenParams p, unsigned char* staging) {
+  const unsigned long long bk = p.st->best_key;
+  int idx = (int)(uint32_t)(bk & 0xFFFFFFFFull);
+  if (idx < 0 || idx >= p.N) idx = 0;   // only before any evaluation
+  const long long gen = p.st->gen;
+  const int si = p.slots[(size_t)(gen & 1) * p.N + idx];
+  const float* row = (si ? p.pop1 : p.pop0) + (size_t)idx * p.pitch;
+  float* out = reinterpret_cast<float*>(staging + kStagingHeader);
+  for (int j = threadIdx.x; j < p.D; j += blockDim.x) out[j] = row[j];
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<double*>(staging) = (double)from_ordered_bits((uint32_t)(bk >> 32));
+    *reinterpret_cast<long long*>(staging + 8) = p.st->best_gen;
+    *reinterpret_cast<int*>(staging + 16) = idx;
+  }
+}
+
+__global__ void normalize_kernel(const __grid_constant__ GenParams p) {
+  const int i = blockIdx.x;
+  uint8_t* sl = p.slots + (size_t)(p.st->gen & 1) * p.N;
+  if (sl[i] == 0) return;
+  const float4* src = reinterpret_cast<const float4*>(p.pop1 + (size_t)i * p.pitch);
+  float4* dst = reinterpret_cast<float4*>(p.pop0 + (size_t)i * p.pitch);
+  for (int q = threadIdx.x; q < p.D4; q += blockDim.x) dst[q] = src[q];
+  __syncthreads();
+  if (threadIdx.x == 0) sl[i] = 0;
+}
+
+static unsigned grid_for(size_t work, unsigned block) {
+  size_t g = (work + block - 1) / block;
+  if (g > 152u * 32u) g = 152u * 32u;   // 152 SMs; grid-stride beyond that
+  return (unsigned)(g ? g : 1);
+}
+
+cudaError_t launch_init(const GenParams& p, cudaStream_t s) {
+  init_kernel<<<grid_for((size_t)p.N * p.D4, 256), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+cudaError_t launch_reset_best(const GenParams& p, cudaStream_t s) {
+  reset_best_kernel<<<1, 1, 0, s>>>(p.st);
+  return cudaGetLastError();
+}
+cudaError_t launch_best_from_fit(const GenParams& p, cudaStream_t s) {
+  best_from_fit_kernel<<<grid_for((size_t)p.N, 256), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+cudaError_t launch_close_eval(const GenParams& p, cudaStream_t s) {
+  close_eval_kernel<<<1, 1, 0, s>>>(p.st);
+  return cudaGetLastError();
+}
+cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s) {
+  best_gather_kernel<<<1, 256, 0, s>>>(p, static_cast<unsigned char*>(staging));
+  return cudaGetLastError();
+}
+cudaError_t launch_normalize(const GenParams& p, cudaStream_t s) {
+  normalize_kernel<<<(unsigned)p.N, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace de

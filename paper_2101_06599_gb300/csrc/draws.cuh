@@ -1,0 +1,91 @@
+// draws.cuh — integer-exact draw rules of one generation (device side).
+//
+// All randomness is Philox words; every rule below is integer arithmetic,
+// so any two implementations of the same rules agree bit for bit.
+//
+//  - randint(m) = (w * m) >> 32 (multiply-shift; bias <= m / 2^32).
+//  - Donors (DE/rand/1, Eq. 1): r1 = randint(N-1) on word 0 of the row's IDX
+//    block, then every excluded value e <= r1 in ascending order shifts it up
+//    by one (excluded = {i}); r2 likewise from word 1 with {i, r1}, r3 from
+//    word 2 with {i, r1, r2}: uniform over ordered distinct triples, != i.
+//  - j_rand = randint(D) on word 3 (Alg. 7 and Alg. 10 both draw it).
+//  - rand(0,1) < Cr is w < ceil(Cr * 2^32), i.e. w / 2^32 < Cr exactly.
+//  - NEC length, Eq. (9): for U = w / 2^32 in (0, 1) and Cr in (0, 1),
+//    ceil(ln U / ln Cr) = 1 + #{n >= 1 : U < Cr^n}. With Cr^n taken as the
+//    FP64 product c_n = fl(c_{n-1} Cr) and T_n = ceil(c_n 2^32),
+//    U < c_n  <=>  w < T_n  <=>  w <= T_n - 1, and T_n does not increase
+//    with n, so L = 1 + (largest n <= D - 1 with w <= T_n - 1), found by
+//    binary search in a table of T_n - 1. The table stops before the first
+//    T_n <= 1 (no w >= 1 passes it); w = 0 is U = 0, where ln U = -inf and
+//    L = D. Cr = 0 gives L = 1 and Cr = 1 gives L = D.
+//  - Classic exponential crossover (Alg. 8): after copying L genes the walk
+//    draws word L-1 of the row's EXP stream and continues iff w < ceil(Cr
+//    2^32) and L < D.
+#pragma once
+#include "common.cuh"
+
+namespace de {
+
+__device__ __forceinline__ int randint_w(uint32_t w, uint32_t m) {
+  return (int)(((unsigned long long)w * (unsigned long long)m) >> 32);
+}
+
+struct RowDraws {
+  int r1, r2, r3, jrand, L;
+};
+
+// Donors and j_rand of row i in generation g.
+__device__ __forceinline__ void draw_donors(const GenParams& p, uint32_t g, int i, RowDraws& d) {
+  const uint4 b = philox_block(p.key, kStreamIdx, p.inst, g, (uint32_t)i, 0u);
+  int e0 = i;                                  // sorted excluded values e0 < e1 < e2
+  int v = randint_w(b.x, (uint32_t)(p.N - 1));
+  v += (v >= e0);
+  d.r1 = v;
+  int e1;
+  if (v < e0) { e1 = e0; e0 = v; } else { e1 = v; }
+  v = randint_w(b.y, (uint32_t)(p.N - 2));
+  v += (v >= e0);
+  v += (v >= e1);
+  d.r2 = v;
+  int e2;
+  if (v < e0) { e2 = e1; e1 = e0; e0 = v; }
+  else if (v < e1) { e2 = e1; e1 = v; }
+  else { e2 = v; }
+  v = randint_w(b.z, (uint32_t)(p.N - 3));
+  v += (v >= e0);
+  v += (v >= e1);
+  v += (v >= e2);
+  d.r3 = v;
+  d.jrand = randint_w(b.w, (uint32_t)p.D);
+}
+
+// NEC segment length of row i, Eq. (9) through the threshold table.
+__device__ __forceinline__ int nec_length(const GenParams& p, uint32_t g, int i) {
+  if (p.cr_mode == kCrZero) return 1;
+  if (p.cr_mode == kCrOne) return p.D;
+  const uint32_t w = philox_block(p.key, kStreamLen, p.inst, g, (uint32_t)i, 0u).x;
+  if (w == 0u) return p.D;
+  int lo = 0, hi = min(p.D - 1, p.nT);         // answer n* in [lo, hi]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (w <= __ldg(p.nec_tm1 + (mid - 1))) lo = mid; else hi = mid - 1;
+  }
+  return 1 + lo;
+}
+
+// Alg. 8's sequential walk: returns L.
+__device__ __forceinline__ int exp_walk_length(const GenParams& p, uint32_t g, int i) {
+  int L = 1;
+  uint32_t k = 0;
+  uint4 blk = make_uint4(0, 0, 0, 0);
+  while (L < p.D) {
+    if ((k & 3u) == 0u) blk = philox_block(p.key, kStreamExp, p.inst, g, (uint32_t)i, k >> 2);
+    const uint32_t w = word_of(blk, k & 3u);
+    ++k;
+    if (!((unsigned long long)w < p.cr_t)) break;
+    ++L;
+  }
+  return L;
+}
+
+}  // namespace de

@@ -1,0 +1,34 @@
+// internal.h — host-side launchers of the device kernels (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace de {
+
+// Generation kernels, one translation unit per crossover. vidx indexes
+// kVecChoices (float4 slots per thread: 1, 2, 4, 8, 16).
+cudaError_t launch_gen_bin(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
+cudaError_t launch_gen_exp(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
+cudaError_t launch_gen_nec(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
+
+// Uniform initial population into slot buffer 0 (Philox stream INIT).
+cudaError_t launch_init(const GenParams& p, cudaStream_t s);
+// Fitness of every row (current slots) into fit[], folding each row into
+// best_key (reset it first with launch_reset_best).
+cudaError_t launch_eval(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
+// best_key <- all ones.
+cudaError_t launch_reset_best(const GenParams& p, cudaStream_t s);
+// Fold the given fit[] into best_key (after launch_reset_best).
+cudaError_t launch_best_from_fit(const GenParams& p, cudaStream_t s);
+// best_f <- value of best_key, best_gen <- gen.
+cudaError_t launch_close_eval(const GenParams& p, cudaStream_t s);
+// staging <- {double f, int64 best_gen, int32 idx, pad, row[D]} of the best row.
+cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s);
+// Move every row held in slot buffer 1 to slot buffer 0 and clear its slot
+// bit, so that buffer 0 holds the whole population.
+cudaError_t launch_normalize(const GenParams& p, cudaStream_t s);
+
+constexpr size_t kStagingHeader = 32;
+
+}  // namespace de

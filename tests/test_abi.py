@@ -1,0 +1,80 @@
+"""The C-ABI library loads on a machine without a GPU, exports every call
+include/*.h declares, and rejects invalid arguments before touching CUDA."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2101_06599_gb300 import build as B
+from paper_2101_06599_gb300 import de as DE
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(de_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return DE.load_library()
+
+
+def test_header_declares_the_calls():
+    names = declared_functions()
+    for required in ("de_create", "de_step", "de_run", "de_best", "de_stats", "de_destroy",
+                     "de_get_population", "de_set_population", "de_save", "de_load", "de_debug_step",
+                     "de_batch_create", "de_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_version(lib):
+    assert DE.de_strerror(0) == "ok"
+    assert DE.de_strerror(DE.DE_EINVAL) == "invalid argument"
+    assert DE.de_version() >= 100
+
+
+@pytest.mark.parametrize("kw", [
+    dict(N=3), dict(D=0), dict(D=40000), dict(CR=1.5), dict(CR=-0.1), dict(CR=float("nan")),
+    dict(F=float("nan")), dict(F=float("inf")), dict(bounds=(1.0, 1.0)), dict(bounds=(2.0, -2.0)),
+    dict(bounds=(float("-inf"), 0.0)), dict(xo=7), dict(obj=99),
+])
+def test_create_rejects_invalid_arguments(lib, kw):
+    args = dict(N=16, D=8, F=0.5, CR=0.9, xo="nec", obj="sphere", bounds=(-1.0, 1.0), seed=1)
+    args.update(kw)
+    with pytest.raises(DE.DEError) as e:
+        DE.de_create(**args)
+    assert e.value.code == DE.DE_EINVAL
+
+
+def test_rotated_objective_needs_shift_and_rotation(lib):
+    with pytest.raises(DE.DEError) as e:
+        DE.de_create(16, 8, 0.5, 0.9, "nec", "sr_rastrigin", (-100.0, 100.0), 1)
+    assert e.value.code == DE.DE_EINVAL
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.de_step(None) == DE.DE_EINVAL
+    assert lib.de_run(None, 3) == DE.DE_EINVAL
+    assert lib.de_synchronize(None) == DE.DE_EINVAL
+    assert lib.de_best(None, None, None, None, None) == DE.DE_EINVAL
+    lib.de_destroy(None)
+
+
+def test_allocator_hook_must_be_paired(lib):
+    assert lib.de_set_allocator(DE._alloc_cb, DE._FREE_FN(), None) == DE.DE_EINVAL
+    assert lib.de_set_allocator(DE._ALLOC_FN(), DE._FREE_FN(), None) == DE.DE_OK

@@ -1,0 +1,230 @@
+"""GPU parity of the fused generation kernel against the CPU oracle.
+
+Every test here runs libde.so's CUDA kernels through the C ABI (ctypes
+binding) and compares element by element with the oracle on the same seeded
+inputs:
+  - draws (r1, r2, r3, j_rand, L) and trial vectors: bit-exact;
+  - FP32 fitness: |f32 - f64| <= 1e-5 max(1, |f64|);
+  - selections: identical wherever the FP64 margin exceeds the two
+    tolerances (|f(u) - f(x)| > tol(u) + tol(x)); the rest is counted.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2101_06599_gb300 import de as DE
+from paper_2101_06599_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+def tol(f):
+    return RTOL * np.maximum(1.0, np.abs(f))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    DE.load_library()
+
+
+def make(N, D, xo, obj, CR=0.9, F=0.5, seed=1, bounds=None):
+    lo, hi = bounds if bounds is not None else W.BOXES[obj]
+    return DE.Optimizer(N, D, F=F, CR=CR, xo=xo, obj=obj, bounds=(lo, hi), seed=seed), lo, hi
+
+
+def check_fitness(f32, f64, what):
+    f32 = np.asarray(f32, np.float64)
+    bad = np.abs(f32 - f64) > tol(f64)
+    assert not bad.any(), "%s: %d rows off, e.g. %r vs %r" % (what, bad.sum(), f32[bad][:3], f64[bad][:3])
+
+
+def one_step_parity(opt, lo, hi, xo, obj, F, CR, seed, pop=None):
+    """Shared parent population -> one GPU debug step and one oracle step."""
+    N, D = opt.N, opt.D
+    if pop is None:
+        pop = W.population(N, D, lo, hi, seed + 100)
+    opt.set_population(pop)
+    gpu_pop, gpu_fit = opt.population()
+    assert np.array_equal(gpu_pop.view(np.uint32), pop.view(np.uint32))
+    fit64 = O.evaluate(obj, pop)
+    check_fitness(gpu_fit, fit64, "parent fitness")
+    g = opt.stats()["generation"]
+    trial, ft, acc, draws = opt.debug_step()
+    s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g)
+    assert np.array_equal(draws, s.draws), "draws differ"
+    assert np.array_equal(trial.view(np.uint32), s.trial.view(np.uint32)), "trials differ"
+    check_fitness(ft, s.ftrial, "trial fitness")
+    amb = np.abs(s.ftrial - fit64) <= tol(s.ftrial) + tol(fit64)
+    assert np.array_equal(acc[~amb], s.accept[~amb]), "selection differs outside the ambiguity band"
+    new_pop, new_fit = opt.population()
+    exp_pop = np.where(acc[:, None], trial, pop)
+    assert np.array_equal(new_pop.view(np.uint32), exp_pop.view(np.uint32))
+    assert np.array_equal(new_fit[acc], ft[acc]) and np.array_equal(new_fit[~acc], gpu_fit[~acc])
+    return s, acc, int(amb.sum())
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+@pytest.mark.parametrize("obj", ["sphere", "rastrigin", "ackley", "rosenbrock", "griewank", "elliptic"])
+@pytest.mark.parametrize("N,D,CR", [(37, 29, 0.9), (64, 1000, 0.5), (20, 4097, 0.9), (48, 130, 0.1)])
+def test_one_generation_parity(xo, obj, N, D, CR):
+    F, seed = 0.5, 7
+    opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
+    try:
+        one_step_parity(opt, lo, hi, xo, obj, F, CR, seed)
+    finally:
+        opt.close()
+
+
+@pytest.mark.parametrize("N,D", [(16, 8), (100, 30), (7, 1001), (5, 9999)])
+def test_init_parity(N, D):
+    for obj in ("rastrigin", "ackley"):
+        lo, hi = W.BOXES[obj]
+        opt = DE.Optimizer(N, D, 0.5, 0.9, "nec", obj, (lo, hi), seed=3)
+        try:
+            pop, fit = opt.population()
+            ref = O.init(N, D, lo, hi, 3)
+            assert np.array_equal(pop.view(np.uint32), ref.view(np.uint32))
+            check_fitness(fit, O.evaluate(obj, ref), "initial fitness")
+            x, f, idx, bg = opt.best()
+            assert idx == int(np.argmin(fit)) and f == fit[idx] and bg == 0
+            assert np.array_equal(x, pop[idx])
+        finally:
+            opt.close()
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+def test_lockstep_generations_sphere_N100_D30(xo):
+    """200 generations of the sphere workload; every generation is checked
+    against the oracle stepping from the GPU's own population."""
+    N, D, F, CR, seed, obj = 100, 30, 0.5, 0.9, 1, "sphere"
+    opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
+    try:
+        ambiguous = 0
+        f_start = opt.best()[1]
+        for g in range(200):
+            pop, fit32 = opt.population()
+            fit64 = O.evaluate(obj, pop)
+            check_fitness(fit32, fit64, "gen %d fitness" % g)
+            trial, ft, acc, draws = opt.debug_step()
+            s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g)
+            assert np.array_equal(draws, s.draws)
+            assert np.array_equal(trial.view(np.uint32), s.trial.view(np.uint32))
+            amb = np.abs(s.ftrial - fit64) <= tol(s.ftrial) + tol(fit64)
+            assert np.array_equal(acc[~amb], s.accept[~amb])
+            ambiguous += int((acc != s.accept).sum())
+        _, f_end, _, bg = opt.best()
+        assert f_end < 1e-2 * f_start and bg > 100
+        print("decisions that differed inside the ambiguity band:", ambiguous)
+    finally:
+        opt.close()
+
+
+def test_run_graph_matches_steps_and_stats():
+    N, D = 96, 200
+    a, lo, hi = make(N, D, "nec", "rastrigin", seed=5)
+    b, _, _ = make(N, D, "nec", "rastrigin", seed=5)
+    try:
+        acc_total, masked_total = 0, 0
+        for _ in range(12):
+            _, _, acc, draws = a.debug_step()
+            acc_total += int(acc.sum())
+            masked_total += int(draws[:, 4].astype(np.int64).sum())
+        b.run(5)
+        b.run(7)
+        pa, fa = a.population()
+        pb, fb = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+        sa, sb = a.stats(), b.stats()
+        assert sa["generation"] == sb["generation"] == 12
+        assert sa["accepts"] == sb["accepts"] == acc_total
+        assert sa["masked_genes"] == sb["masked_genes"] == masked_total
+        x, f, idx, bg = b.best()
+        assert idx == int(np.argmin(fb)) and f == fb[idx] and np.array_equal(x, pb[idx])
+        assert 0 <= bg <= 12 and sb["best_gen"] == bg
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+def test_save_load_resumes_bit_identically(xo):
+    N, D = 50, 77
+    a, lo, hi = make(N, D, xo, "ackley", CR=0.7, seed=9)
+    b, _, _ = make(N, D, xo, "ackley", CR=0.7, seed=9)
+    try:
+        a.run(6)
+        blob = a.save()
+        a.run(9)
+        b.load(blob)
+        b.run(9)
+        pa, fa = a.population()
+        pb, fb = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+        assert a.stats() == b.stats()
+        assert a.best()[1:] == b.best()[1:]
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+def test_edge_cases(xo):
+    F = 0.5
+    # D = 1: the only gene is j_rand and L = 1 = D
+    for (N, D, CR, obj) in [(4, 1, 0.9, "sphere"), (4, 5, 0.0, "rastrigin"), (9, 33, 1.0, "rosenbrock"),
+                            (600, 3, 0.5, "griewank"), (4, 7, 0.3, "elliptic")]:
+        opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=11)
+        try:
+            s, acc, _ = one_step_parity(opt, lo, hi, xo, obj, F, CR, 11)
+            if CR == 0.0:
+                assert np.all(s.L == 1)
+            if CR == 1.0 or D == 1:
+                assert np.all(s.L == D)
+        finally:
+            opt.close()
+
+
+def test_maximum_row_length_and_launch_shapes():
+    N, D, obj, xo = 6, 32768, "rosenbrock", "nec"
+    opt, lo, hi = make(N, D, xo, obj, CR=0.99, seed=2)
+    try:
+        one_step_parity(opt, lo, hi, xo, obj, 0.5, 0.99, 2)
+    finally:
+        opt.close()
+    # the same step under other launch shapes: identical draws and trials
+    N, D = 12, 1000
+    pop = W.population(N, D, -5.12, 5.12, 4)
+    ref = None
+    for (T, V) in [(256, 1), (128, 2), (64, 4), (32, 8), (32, 16)]:
+        opt, lo, hi = make(N, D, "bin", "rastrigin", CR=0.5, seed=4)
+        try:
+            opt.set_launch(T, V)
+            assert opt.launch() == (T, V)
+            opt.set_population(pop)
+            trial, ft, acc, draws = opt.debug_step()
+            if ref is None:
+                ref = (trial, ft, draws)
+            assert np.array_equal(trial.view(np.uint32), ref[0].view(np.uint32))
+            assert np.array_equal(draws, ref[2])
+            assert np.allclose(ft, ref[1], rtol=RTOL, atol=RTOL)
+        finally:
+            opt.close()
+
+
+def test_ties_keep_parent_on_gpu():
+    N, D = 8, 10
+    pop = np.tile(W.population(1, D, -5, 5, 3), (N, 1))
+    opt, lo, hi = make(N, D, "nec", "rastrigin", seed=1)
+    try:
+        opt.set_population(pop)
+        trial, ft, acc, _ = opt.debug_step()
+        assert np.array_equal(trial, pop) and not acc.any()
+    finally:
+        opt.close()
