@@ -268,6 +268,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
+    ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -286,7 +288,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         _dist = dist
     DE.load_library()
-    N, D, K, W = N_DEF, D_DEF, args.steps, args.warmup
+    N, D, K, W = args.N, args.D, args.steps, args.warmup
     seed = SEED + rank
 
     # headline: NEC on Rosenbrock, clocks sampled across the ramp and the timed region
