@@ -39,8 +39,9 @@ WORKLOAD = "rosenbrock_ackley_N16384_D10000"
 N_DEF, D_DEF, F_DEF, CR_DEF, SEED = 16384, 10000, 0.5, 0.9, 1
 BOXES = {"rosenbrock": (-5.12, 5.12), "ackley": (-30.0, 30.0)}
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "gen_nec_rosenbrock_N16384_D10000.md")
-KERNEL_SOURCES = ["common.cuh", "draws.cuh", "objectives.cuh", "gen_kernel.cuh", "philox.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "gen_pipe_nec_rosenbrock_N16384_D10000.md")
+KERNEL_SOURCES = ["common.cuh", "draws.cuh", "objectives.cuh", "gen_kernel.cuh", "gen_pipe.cuh", "ptx.cuh",
+                  "philox.cuh"]
 
 
 def kernel_fingerprint() -> str:
@@ -171,8 +172,14 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         st1 = opt.stats()
         d_acc = st1["accepts"] - st0["accepts"]
         d_msk = st1["masked_genes"] - st0["masked_genes"]
-        threads, vec = opt.launch()
-        return opt, ms, d_acc, d_msk, (threads, vec)
+        if opt.kernel() == 2:
+            nc, stages, span = opt.pipeline()
+            shape = "gen_pipe_kernel<%s, %s>: 1 CTA/SM, 1 producer warp + %d consumers, %d stages, " \
+                    "donor spans of %d floats" % (xo.upper(), obj, nc, stages, span)
+        else:
+            threads, vec = opt.launch()
+            shape = "gen_kernel<%s, %s, vec4=%d> x %d threads/row" % (xo.upper(), obj, vec, threads)
+        return opt, ms, d_acc, d_msk, shape
     except Exception:
         opt.close()
         raise
@@ -305,7 +312,7 @@ def main():
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
-                "kernel": "gen_kernel<NEC, Rosenbrock, vec4=%d> x %d threads/row" % (shape[1], shape[0]),
+                "kernel": shape,
                 "algorithmic_bytes_per_launch": bytes_alg / K, "avg_launch_us": avg_launch_s * 1e6,
                 "m_masked_fraction": d_msk / (N * D * K), "a_acceptance": d_acc / (N * K)}
 
@@ -341,7 +348,7 @@ def main():
                 ach2 = b2 / (ms2 / 1e3) / 1e9
                 variants.setdefault(obj, {})[xo] = {
                     "value": units / (ms2 / 1e3), "ms_per_gen": ms2 / K, "hbm_gbs": ach2, "frac": ach2 / peak,
-                    "m": m2 / (N * D * K), "a": a2 / (N * K), "launch": list(sh2)}
+                    "m": m2 / (N * D * K), "a": a2 / (N * K), "kernel": sh2}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -219,6 +219,24 @@ int de_batch_best(de_ctx *ctx, int32_t inst, float *x_out, double *f_out,
 int de_set_launch(de_ctx *ctx, int32_t threads, int32_t vec4);
 int de_get_launch(de_ctx *ctx, int32_t *threads, int32_t *vec4);
 
+/* Generation kernel: 0 = automatic, 1 = one CTA per row (row held in
+ * registers; every crossover, every D), 2 = persistent pipelined kernel (one
+ * CTA per SM, a producer warp streams parent rows and the masked donor spans
+ * into a shared-memory ring with bulk TMA copies; classic exponential and NEC
+ * only; DE_EUNSUPPORTED for binomial or when a stage does not fit in shared
+ * memory). Automatic picks 2 for exp / NEC when D >= 2048 and at least three
+ * stages fit. Draws and trials are the same under both kernels. */
+int de_set_kernel(de_ctx *ctx, int32_t kind);
+/* The kernel in use: 1 or 2. */
+int de_get_kernel(de_ctx *ctx, int32_t *kind);
+/* Pipelined kernel shape: consumer threads per CTA (multiple of 32, 32..512;
+ * default 256) and shared-memory stages (2..8; 0 = as many as fit). */
+int de_set_pipeline(de_ctx *ctx, int32_t consumer_threads, int32_t stages);
+/* The pipelined kernel's shape: consumer threads, stages, and the floats of
+ * each donor span buffer (segments longer than that read their donor genes
+ * from global memory). DE_EUNSUPPORTED if the kernel is not available. */
+int de_get_pipeline(de_ctx *ctx, int32_t *consumer_threads, int32_t *stages, int32_t *span_floats);
+
 /* ---- misc ----------------------------------------------------------------- */
 const char *de_strerror(int code);
 

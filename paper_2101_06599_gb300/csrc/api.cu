@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/de.h"
+#include "gen_pipe.cuh"
 #include "internal.h"
 
 using namespace de;
@@ -43,6 +44,15 @@ struct de_ctx {
   double ackley_b = 0.2;
   cudaStream_t stream = nullptr;
   int block = 32, vidx = 0;
+  // kernel choice: 0 = automatic, 1 = row per CTA, 2 = pipelined (exp / NEC)
+  int kernel_req = 0;
+  bool use_pipe = false;
+  bool pipe_ok = false;
+  PipeParams pp{};
+  int pipe_grid = 0, pipe_block = 32 + 256;
+  int pipe_stages_req = 0;       // 0 = as many as fit
+  size_t pipe_smem = 0;
+  int sm_count = 0, smem_optin = 0;
   GenParams p{};
   std::vector<Block> blocks;
   std::map<int32_t, cudaGraphExec_t> graphs;
@@ -106,7 +116,56 @@ void choose_launch(int D4, int& block, int& vidx) {
 
 bool is_rotated(int obj) { return obj == DE_OBJ_SR_RASTRIGIN || obj == DE_OBJ_SR_ELLIPTIC; }
 
+// Pipelined kernel geometry. Donor span buffers hold the segment lengths
+// that occur with probability >= 1e-6 (P(L > n) = Cr^n; longer segments read
+// their donor genes from global memory), capped at min(D + 8, 1024) floats.
+// Stages: as many as fit in the opt-in shared memory (<= 8), or the
+// requested count.
+void configure_pipe(de_ctx* c) {
+  c->pipe_ok = false;
+  if (c->xo == DE_XOVER_BIN || c->sm_count <= 0 || c->smem_optin <= 0) return;
+  const int row_floats = 4 * c->D4;
+  int need = 16;
+  if (c->CR >= 1.0) need = c->D + 8;
+  else if (c->CR > 0.0) need = (int)std::min(1.0e6, std::ceil(std::log(1e-6) / std::log(c->CR))) + 16;
+  const int segcap = std::max(16, std::min(std::min(((c->D + 3) & ~3) + 8, 1024), (need + 3) & ~3));
+  const int stage_floats = ((row_floats + 3 * segcap + 31) / 32) * 32;
+  const int tcap = (c->xo == DE_XOVER_NEC && c->p.nT <= kPipeTableCap) ? c->p.nT : 0;
+  int S = 0;
+  for (int s = kPipeMaxStages; s >= 2; --s) {
+    if (pipe_layout(s, tcap, stage_floats).total <= (unsigned)c->smem_optin) {
+      S = s;
+      break;
+    }
+  }
+  if (S < 2) return;
+  if (c->pipe_stages_req >= 2 && c->pipe_stages_req < S) S = c->pipe_stages_req;
+  c->pp.stages = S;
+  c->pp.segcap = segcap;
+  c->pp.tcap = tcap;
+  c->pp.row_floats = row_floats;
+  c->pp.stage_floats = stage_floats;
+  c->pipe_smem = pipe_layout(S, tcap, stage_floats).total;
+  c->pipe_grid = std::min(c->N, c->sm_count);
+  if (prepare_gen_pipe(c->xo, c->obj, c->pipe_smem) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c->pipe_ok = true;
+}
+
+void resolve_kernel(de_ctx* c) {
+  if (c->kernel_req == 2) c->use_pipe = c->pipe_ok;
+  else if (c->kernel_req == 1) c->use_pipe = false;
+  else c->use_pipe = c->pipe_ok && c->D >= 2048 && c->pp.stages >= 3;
+}
+
 cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
+  if (c->use_pipe) {
+    PipeParams pp = c->pp;
+    pp.g = p;
+    return launch_gen_pipe(c->xo, c->obj, pp, c->pipe_grid, c->pipe_block, c->pipe_smem, c->stream);
+  }
   switch (c->xo) {
     case DE_XOVER_BIN: return launch_gen_bin(c->obj, c->vidx, p, c->block, c->stream);
     case DE_XOVER_EXP: return launch_gen_exp(c->obj, c->vidx, p, c->block, c->stream);
@@ -266,6 +325,15 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   p.ackley_b = (float)ackley_b;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
 
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  cudaGetLastError();
+  configure_pipe(c);
+  resolve_kernel(c);
+
   DevState s0;
   std::memset(&s0, 0, sizeof(s0));
   s0.best_key = ~0ULL;
@@ -333,7 +401,14 @@ int de_run(de_ctx* c, int32_t generations) {
 
 int de_synchronize(de_ctx* c) {
   if (!c) return DE_EINVAL;
-  return sync_stream(c);
+  if (cudaMemcpyAsync(c->host_pinned, &c->p.st->error, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return DE_ECUDA;
+  const int rc = sync_stream(c);
+  if (rc != DE_OK) return rc;
+  unsigned err;
+  std::memcpy(&err, c->host_pinned, sizeof(err));
+  return err ? (int)err : DE_OK;
 }
 
 int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* best_gen_out) {
@@ -346,6 +421,9 @@ int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* b
   const int rc = sync_stream(c);
   if (rc != DE_OK) return rc;
   const unsigned char* h = static_cast<const unsigned char*>(c->host_pinned);
+  int derr = 0;
+  std::memcpy(&derr, h + 20, sizeof(int));
+  if (derr) return derr;
   if (f_out) std::memcpy(f_out, h, sizeof(double));
   if (best_gen_out) std::memcpy(best_gen_out, h + 8, sizeof(int64_t));
   if (idx_out) std::memcpy(idx_out, h + 16, sizeof(int32_t));
@@ -362,6 +440,7 @@ int de_stats(de_ctx* c, de_stats_t* out) {
   if (rc != DE_OK) return rc;
   DevState s;
   std::memcpy(&s, c->host_pinned, sizeof(s));
+  if (s.error) return (int)s.error;
   out->generation = s.gen;
   out->accepts = s.accepts;
   out->masked_genes = s.masked;
@@ -521,6 +600,43 @@ int de_set_launch(de_ctx* c, int32_t threads, int32_t vec4) {
   c->block = threads;
   c->vidx = vidx;
   drop_graphs(c);
+  return DE_OK;
+}
+
+int de_set_kernel(de_ctx* c, int32_t kind) {
+  if (!c || kind < 0 || kind > 2) return DE_EINVAL;
+  if (kind == 2 && !c->pipe_ok) return DE_EUNSUPPORTED;
+  c->kernel_req = kind;
+  resolve_kernel(c);
+  drop_graphs(c);
+  return DE_OK;
+}
+
+int de_get_kernel(de_ctx* c, int32_t* kind) {
+  if (!c || !kind) return DE_EINVAL;
+  *kind = c->use_pipe ? 2 : 1;
+  return DE_OK;
+}
+
+int de_set_pipeline(de_ctx* c, int32_t consumer_threads, int32_t stages) {
+  if (!c) return DE_EINVAL;
+  if (consumer_threads < 32 || consumer_threads > 32 * kPipeMaxConsumerWarps || consumer_threads % 32 != 0)
+    return DE_EINVAL;
+  if (stages != 0 && (stages < 2 || stages > kPipeMaxStages)) return DE_EINVAL;
+  c->pipe_block = 32 + consumer_threads;
+  c->pipe_stages_req = stages;
+  configure_pipe(c);
+  resolve_kernel(c);
+  drop_graphs(c);
+  return DE_OK;
+}
+
+int de_get_pipeline(de_ctx* c, int32_t* consumer_threads, int32_t* stages, int32_t* span_floats) {
+  if (!c) return DE_EINVAL;
+  if (!c->pipe_ok) return DE_EUNSUPPORTED;
+  if (consumer_threads) *consumer_threads = c->pipe_block - 32;
+  if (stages) *stages = c->pp.stages;
+  if (span_floats) *span_floats = c->pp.segcap;
   return DE_OK;
 }
 

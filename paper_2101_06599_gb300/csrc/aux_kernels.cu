@@ -108,6 +108,7 @@ __global__ void best_gather_kernel(const __grid_constant__ GenParams p, unsigned
     *reinterpret_cast<double*>(staging) = (double)from_ordered_bits((uint32_t)(bk >> 32));
     *reinterpret_cast<long long*>(staging + 8) = p.st->best_gen;
     *reinterpret_cast<int*>(staging + 16) = idx;
+    *reinterpret_cast<int*>(staging + 20) = (int)p.st->error;
   }
 }
 

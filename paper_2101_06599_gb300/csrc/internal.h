@@ -29,6 +29,12 @@ cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s
 // bit, so that buffer 0 holds the whole population.
 cudaError_t launch_normalize(const GenParams& p, cudaStream_t s);
 
+// Pipelined generation kernel (exp / NEC); PipeParams in gen_pipe.cuh.
+struct PipeParams;
+cudaError_t prepare_gen_pipe(int xo, int obj, size_t smem);
+cudaError_t launch_gen_pipe(int xo, int obj, const PipeParams& pp, int grid, int block, size_t smem,
+                            cudaStream_t s);
+
 constexpr size_t kStagingHeader = 32;
 
 }  // namespace de

@@ -19,6 +19,21 @@
 
 namespace de {
 
+// sin^2(pi x) = r^2 Q(r^2), r = x - rint(x) (exact), Q a degree-5 fit of
+// sin^2(pi sqrt t) / t on t in [0, 1/4]; coefficients from sin2pi_poly.py
+// (relative error of the fit 1.4e-8, of the FP32 evaluation ~2e-7).
+__device__ __forceinline__ float sin2pi(float x) {
+  const float r = x - rintf(x);
+  const float t = r * r;
+  float q = -3.335728645e+00f;
+  q = fmaf(q, t, 1.303679657e+01f);
+  q = fmaf(q, t, -3.009848022e+01f);
+  q = fmaf(q, t, 4.272692108e+01f);
+  q = fmaf(q, t, -3.246966171e+01f);
+  q = fmaf(q, t, 9.869604111e+00f);
+  return q * t;
+}
+
 struct Acc {
   float a, b, c;   // partial sums (meaning depends on the objective)
 };
@@ -33,12 +48,10 @@ __device__ __forceinline__ void accum_gene(Acc& s, float x, int j, const GenPara
   if constexpr (OBJ == kSphere) {
     s.a = fmaf(x, x, s.a);
   } else if constexpr (OBJ == kRastrigin) {
-    const float sp = sinpif(x);
-    s.a += fmaf(x, x, 20.0f * sp * sp);
+    s.a += fmaf(x, x, 20.0f * sin2pi(x));
   } else if constexpr (OBJ == kAckley) {
-    const float sp = sinpif(x);
     s.a = fmaf(x, x, s.a);
-    s.b = fmaf(sp, sp, s.b);
+    s.b += sin2pi(x);
   } else if constexpr (OBJ == kGriewank) {
     s.a = fmaf(x, x, s.a);
     const float y = x * rsqrtf((float)(j + 1));

@@ -90,6 +90,10 @@ def load_library(build_if_missing: bool = True):
         "de_debug_step": ([vp, vp, vp, vp, vp], C.c_int),
         "de_set_launch": ([vp, i32, i32], C.c_int),
         "de_get_launch": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "de_set_kernel": ([vp, i32], C.c_int),
+        "de_get_kernel": ([vp, C.POINTER(i32)], C.c_int),
+        "de_set_pipeline": ([vp, i32, i32], C.c_int),
+        "de_get_pipeline": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "de_batch_create": ([C.POINTER(vp), i32, C.POINTER(de_instance_spec), C.c_uint64, vp], C.c_int),
         "de_batch_best": ([vp, i32, vp, C.POINTER(f64), C.POINTER(i32), C.POINTER(i64)], C.c_int),
     }
@@ -258,6 +262,29 @@ def de_get_launch(ctx):
     return t.value, v.value
 
 
+def de_set_kernel(ctx, kind):
+    _check(load_library().de_set_kernel(C.c_void_p(ctx), int(kind)), "de_set_kernel")
+
+
+def de_get_kernel(ctx):
+    k = C.c_int32()
+    _check(load_library().de_get_kernel(C.c_void_p(ctx), C.byref(k)), "de_get_kernel")
+    return k.value
+
+
+def de_set_pipeline(ctx, consumer_threads, stages=0):
+    _check(load_library().de_set_pipeline(C.c_void_p(ctx), int(consumer_threads), int(stages)),
+           "de_set_pipeline")
+
+
+def de_get_pipeline(ctx):
+    """(consumer_threads, stages, span_floats) of the pipelined kernel."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load_library().de_get_pipeline(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(c)),
+           "de_get_pipeline")
+    return a.value, b.value, c.value
+
+
 def de_batch_create(specs, seed, stream=None):
     L = load_library()
     arr = (de_instance_spec * len(specs))()
@@ -344,6 +371,18 @@ class Optimizer:
 
     def launch(self):
         return de_get_launch(self.ctx)
+
+    def set_kernel(self, kind):
+        de_set_kernel(self.ctx, kind)
+
+    def kernel(self):
+        return de_get_kernel(self.ctx)
+
+    def set_pipeline(self, consumer_threads, stages=0):
+        de_set_pipeline(self.ctx, consumer_threads, stages)
+
+    def pipeline(self):
+        return de_get_pipeline(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

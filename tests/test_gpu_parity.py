@@ -228,3 +228,92 @@ def test_ties_keep_parent_on_gpu():
         assert np.array_equal(trial, pop) and not acc.any()
     finally:
         opt.close()
+
+
+# ---- the pipelined kernel (exp / NEC) --------------------------------------------------------
+@pytest.mark.parametrize("xo", ["exp", "nec"])
+@pytest.mark.parametrize("obj", ["sphere", "rastrigin", "ackley", "rosenbrock", "griewank", "elliptic"])
+@pytest.mark.parametrize("N,D,CR", [(37, 29, 0.9), (300, 1000, 0.5), (20, 4097, 0.9), (160, 2048, 0.1)])
+def test_pipeline_kernel_parity(xo, obj, N, D, CR):
+    F, seed = 0.5, 13
+    opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
+    try:
+        opt.set_kernel(2)
+        assert opt.kernel() == 2
+        one_step_parity(opt, lo, hi, xo, obj, F, CR, seed)
+    finally:
+        opt.close()
+
+
+@pytest.mark.parametrize("xo", ["exp", "nec"])
+@pytest.mark.parametrize("N,D,CR,consumers,stages", [
+    (64, 4000, 0.999, 256, 0),     # long segments: many exceed the donor span buffer (global fallback)
+    (40, 8000, 0.9999, 128, 3),    # NEC table larger than the shared-memory copy (global search)
+    (4, 1, 0.9, 32, 0),            # D = 1
+    (500, 3, 0.0, 512, 2),         # Cr = 0: L = 1
+    (33, 130, 1.0, 64, 5),         # Cr = 1: L = D, the segment wraps onto itself
+])
+def test_pipeline_kernel_edges(xo, N, D, CR, consumers, stages):
+    F, seed, obj = 0.7, 21, "rosenbrock"
+    opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
+    try:
+        opt.set_kernel(2)
+        opt.set_pipeline(consumers, stages)
+        nc, st, span = opt.pipeline()
+        assert nc == consumers and (stages == 0 or st == stages) and span >= 16
+        s, acc, _ = one_step_parity(opt, lo, hi, xo, obj, F, CR, seed)
+        if CR == 0.0:
+            assert np.all(s.L == 1)
+        if CR == 1.0:
+            assert np.all(s.L == D)
+    finally:
+        opt.close()
+
+
+@pytest.mark.parametrize("xo", ["exp", "nec"])
+def test_pipeline_matches_row_kernel_over_generations(xo):
+    N, D, obj = 700, 2500, "ackley"
+    a, lo, hi = make(N, D, xo, obj, CR=0.9, seed=3)
+    b, _, _ = make(N, D, xo, obj, CR=0.9, seed=3)
+    try:
+        a.set_kernel(1)
+        b.set_kernel(2)
+        for g in range(6):
+            ta, fa, acca, da = a.debug_step()
+            tb, fb, accb, db = b.debug_step()
+            assert np.array_equal(da, db)
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            assert np.allclose(fa, fb, rtol=2 * RTOL, atol=2 * RTOL)
+            # the two kernels reduce in different orders: decisions may differ only in near-ties
+            pa, ffa = a.population()
+            pb, ffb = b.population()
+            if not np.array_equal(pa.view(np.uint32), pb.view(np.uint32)):
+                b.set_population(pa, ffa)       # re-align and continue
+        b.run(4)
+        st = b.stats()
+        assert st["generation"] == 10
+    finally:
+        a.close()
+        b.close()
+
+
+def test_pipeline_graph_save_load():
+    N, D, xo, obj = 300, 3000, "nec", "rastrigin"
+    a, lo, hi = make(N, D, xo, obj, CR=0.9, seed=8)
+    b, _, _ = make(N, D, xo, obj, CR=0.9, seed=8)
+    try:
+        assert a.kernel() == 2 and b.kernel() == 2            # chosen automatically at D >= 2048
+        a.run(5)
+        blob = a.save()
+        a.run(7)
+        b.load(blob)
+        for _ in range(7):
+            b.step()
+        pa, fa = a.population()
+        pb, fb = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+        assert a.stats() == b.stats()
+    finally:
+        a.close()
+        b.close()
