@@ -173,9 +173,9 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         d_acc = st1["accepts"] - st0["accepts"]
         d_msk = st1["masked_genes"] - st0["masked_genes"]
         if opt.kernel() == 2:
-            nc, stages, span = opt.pipeline()
-            shape = "gen_pipe_kernel<%s, %s>: 1 CTA/SM, 1 producer warp + %d consumers, %d stages, " \
-                    "donor spans of %d floats" % (xo.upper(), obj, nc, stages, span)
+            nc, stages, span, cps = opt.pipeline()
+            shape = "gen_pipe_kernel<%s, %s>: %d CTA/SM, 1 producer warp + %d consumers, %d stages, " \
+                    "donor spans of %d floats" % (xo.upper(), obj, cps, nc, stages, span)
         else:
             threads, vec = opt.launch()
             shape = "gen_kernel<%s, %s, vec4=%d> x %d threads/row" % (xo.upper(), obj, vec, threads)

@@ -230,12 +230,16 @@ int de_set_kernel(de_ctx *ctx, int32_t kind);
 /* The kernel in use: 1 or 2. */
 int de_get_kernel(de_ctx *ctx, int32_t *kind);
 /* Pipelined kernel shape: consumer threads per CTA (multiple of 32, 32..512;
- * default 256) and shared-memory stages (2..8; 0 = as many as fit). */
-int de_set_pipeline(de_ctx *ctx, int32_t consumer_threads, int32_t stages);
-/* The pipelined kernel's shape: consumer threads, stages, and the floats of
- * each donor span buffer (segments longer than that read their donor genes
- * from global memory). DE_EUNSUPPORTED if the kernel is not available. */
-int de_get_pipeline(de_ctx *ctx, int32_t *consumer_threads, int32_t *stages, int32_t *span_floats);
+ * default 256), shared-memory stages (2..8; 0 = as many as fit) and CTAs per
+ * SM (1 or 2; two CTAs split the SM's shared memory; 0 = two when two stages
+ * fit, else one). DE_EINVAL otherwise. */
+int de_set_pipeline(de_ctx *ctx, int32_t consumer_threads, int32_t stages, int32_t ctas_per_sm);
+/* The pipelined kernel's shape: consumer threads, stages, the floats of each
+ * donor span buffer (segments longer than that read their donor genes from
+ * global memory) and CTAs per SM; any pointer may be NULL. DE_EUNSUPPORTED
+ * if the kernel is not available. */
+int de_get_pipeline(de_ctx *ctx, int32_t *consumer_threads, int32_t *stages, int32_t *span_floats,
+                    int32_t *ctas_per_sm);
 
 /* ---- misc ----------------------------------------------------------------- */
 const char *de_strerror(int code);

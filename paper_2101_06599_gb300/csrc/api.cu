@@ -51,6 +51,9 @@ struct de_ctx {
   PipeParams pp{};
   int pipe_grid = 0, pipe_block = 32 + 256;
   int pipe_stages_req = 0;       // 0 = as many as fit
+  int pipe_cps = 0;              // CTAs per SM (1 or 2); 0 = automatic
+  int smem_per_sm = 0;
+  int pp_cps = 1;                // CTAs per SM in use
   size_t pipe_smem = 0;
   int sm_count = 0, smem_optin = 0;
   GenParams p{};
@@ -131,14 +134,21 @@ void configure_pipe(de_ctx* c) {
   const int segcap = std::max(16, std::min(std::min(((c->D + 3) & ~3) + 8, 1024), (need + 3) & ~3));
   const int stage_floats = ((row_floats + 3 * segcap + 31) / 32) * 32;
   const int tcap = (c->xo == DE_XOVER_NEC && c->p.nT <= kPipeTableCap) ? c->p.nT : 0;
-  int S = 0;
-  for (int s = kPipeMaxStages; s >= 2; --s) {
-    if (pipe_layout(s, tcap, stage_floats).total <= (unsigned)c->smem_optin) {
-      S = s;
-      break;
-    }
-  }
+  // Two CTAs per SM share the SM's shared memory (1 KB per CTA is reserved).
+  // Automatic: two CTAs (each with its own producer, so the per-row consumer
+  // chains of one overlap the other's) when two stages fit in half an SM;
+  // else one CTA.
+  auto stages_for = [&](int cps) {
+    const int budget = (cps == 1) ? c->smem_optin : std::min(c->smem_optin, c->smem_per_sm / cps - 1024);
+    for (int s = kPipeMaxStages; s >= 2; --s)
+      if (pipe_layout(s, tcap, stage_floats).total <= (unsigned)budget) return s;
+    return 0;
+  };
+  int cps = c->pipe_cps;
+  if (cps == 0) cps = (stages_for(2) >= 2) ? 2 : 1;
+  int S = stages_for(cps);
   if (S < 2) return;
+  c->pp_cps = cps;
   if (c->pipe_stages_req >= 2 && c->pipe_stages_req < S) S = c->pipe_stages_req;
   c->pp.stages = S;
   c->pp.segcap = segcap;
@@ -146,7 +156,7 @@ void configure_pipe(de_ctx* c) {
   c->pp.row_floats = row_floats;
   c->pp.stage_floats = stage_floats;
   c->pipe_smem = pipe_layout(S, tcap, stage_floats).total;
-  c->pipe_grid = std::min(c->N, c->sm_count);
+  c->pipe_grid = std::min(c->N, c->sm_count * cps);
   if (prepare_gen_pipe(c->xo, c->obj, c->pipe_smem) != cudaSuccess) {
     cudaGetLastError();
     return;
@@ -329,6 +339,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   if (cudaGetDevice(&dev) == cudaSuccess) {
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   }
   cudaGetLastError();
   configure_pipe(c);
@@ -618,22 +629,26 @@ int de_get_kernel(de_ctx* c, int32_t* kind) {
   return DE_OK;
 }
 
-int de_set_pipeline(de_ctx* c, int32_t consumer_threads, int32_t stages) {
+int de_set_pipeline(de_ctx* c, int32_t consumer_threads, int32_t stages, int32_t ctas_per_sm) {
   if (!c) return DE_EINVAL;
   if (consumer_threads < 32 || consumer_threads > 32 * kPipeMaxConsumerWarps || consumer_threads % 32 != 0)
     return DE_EINVAL;
   if (stages != 0 && (stages < 2 || stages > kPipeMaxStages)) return DE_EINVAL;
+  if (ctas_per_sm < 0 || ctas_per_sm > 2) return DE_EINVAL;
   c->pipe_block = 32 + consumer_threads;
   c->pipe_stages_req = stages;
+  c->pipe_cps = ctas_per_sm;
   configure_pipe(c);
   resolve_kernel(c);
   drop_graphs(c);
   return DE_OK;
 }
 
-int de_get_pipeline(de_ctx* c, int32_t* consumer_threads, int32_t* stages, int32_t* span_floats) {
+int de_get_pipeline(de_ctx* c, int32_t* consumer_threads, int32_t* stages, int32_t* span_floats,
+                    int32_t* ctas_per_sm) {
   if (!c) return DE_EINVAL;
   if (!c->pipe_ok) return DE_EUNSUPPORTED;
+  if (ctas_per_sm) *ctas_per_sm = c->pp_cps;
   if (consumer_threads) *consumer_threads = c->pipe_block - 32;
   if (stages) *stages = c->pp.stages;
   if (span_floats) *span_floats = c->pp.segcap;

@@ -2,7 +2,7 @@
 // segment crossovers (classic exponential, Alg. 8; NEC, Eq. 9 + Alg. 9/10)
 // at large D.
 //
-// Grid = one CTA per SM; CTA b owns rows b, b + G, b + 2G, ... Each CTA has
+// Grid = one or two CTAs per SM; CTA b owns rows b, b + G, b + 2G, ... Each CTA has
 // one producer warp and NC consumer threads, and a ring of S shared-memory
 // stages. A stage holds one parent row and the masked segments of its three
 // donor rows, filled by bulk TMA copies (cp.async.bulk) that complete on the
@@ -242,7 +242,9 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
       // 1. masked genes: piece 0 = [jrand, min(jrand + L, D)), piece 1 = [0, jrand + L - D)
       const int e0 = min(m.jrand + m.L, p.D);
       const int wrap = m.jrand + m.L - p.D;
+      bool patched = false;
       for (int j = m.jrand + ct; j < e0; j += NC) {
+        patched = true;
         float a1, a2, a3;
         if (m.seg_ok) {
           const int o = j - m.a0;
@@ -253,6 +255,7 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
         row[j] = clip_box(mutate(a1, a2, a3, p.F), p.lo, p.hi);
       }
       for (int j = ct; j < wrap; j += NC) {
+        patched = true;
         float a1, a2, a3;
         if (m.seg_ok) {
           const int o = m.len0 + j;
@@ -262,7 +265,7 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
         }
         row[j] = clip_box(mutate(a1, a2, a3, p.F), p.lo, p.hi);
       }
-      fence_proxy_async_smem();                   // patches precede the stage's next bulk fill
+      if (patched) fence_proxy_async_smem();      // patches precede the stage's next bulk fill
       named_bar_sync(2, NC);                      // patched genes visible to every consumer
 
       // 2. fitness of the trial, from shared memory
@@ -294,10 +297,13 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
 
       // 3. every consumer forms the same row value and decision
       Acc r{0.0f, 0.0f, 0.0f};
-      for (int w = 0; w < NCW; ++w) {
-        r.a += ps[4 * w + 0];
-        r.b += ps[4 * w + 1];
-        r.c += ps[4 * w + 2];
+#pragma unroll
+      for (int w = 0; w < kPipeMaxConsumerWarps; ++w) {
+        if (w < NCW) {
+          r.a += ps[4 * w + 0];
+          r.b += ps[4 * w + 1];
+          r.c += ps[4 * w + 2];
+        }
       }
       float f = finalize_fitness<OBJ>(r, p);
       if (f != f) f = __int_as_float(0x7F800000);

@@ -92,8 +92,8 @@ def load_library(build_if_missing: bool = True):
         "de_get_launch": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "de_set_kernel": ([vp, i32], C.c_int),
         "de_get_kernel": ([vp, C.POINTER(i32)], C.c_int),
-        "de_set_pipeline": ([vp, i32, i32], C.c_int),
-        "de_get_pipeline": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "de_set_pipeline": ([vp, i32, i32, i32], C.c_int),
+        "de_get_pipeline": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "de_batch_create": ([C.POINTER(vp), i32, C.POINTER(de_instance_spec), C.c_uint64, vp], C.c_int),
         "de_batch_best": ([vp, i32, vp, C.POINTER(f64), C.POINTER(i32), C.POINTER(i64)], C.c_int),
     }
@@ -272,17 +272,17 @@ def de_get_kernel(ctx):
     return k.value
 
 
-def de_set_pipeline(ctx, consumer_threads, stages=0):
-    _check(load_library().de_set_pipeline(C.c_void_p(ctx), int(consumer_threads), int(stages)),
-           "de_set_pipeline")
+def de_set_pipeline(ctx, consumer_threads, stages=0, ctas_per_sm=0):
+    _check(load_library().de_set_pipeline(C.c_void_p(ctx), int(consumer_threads), int(stages),
+                                          int(ctas_per_sm)), "de_set_pipeline")
 
 
 def de_get_pipeline(ctx):
-    """(consumer_threads, stages, span_floats) of the pipelined kernel."""
-    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(load_library().de_get_pipeline(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(c)),
+    """(consumer_threads, stages, span_floats, ctas_per_sm) of the pipelined kernel."""
+    a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load_library().de_get_pipeline(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
            "de_get_pipeline")
-    return a.value, b.value, c.value
+    return a.value, b.value, c.value, d.value
 
 
 def de_batch_create(specs, seed, stream=None):
@@ -378,8 +378,8 @@ class Optimizer:
     def kernel(self):
         return de_get_kernel(self.ctx)
 
-    def set_pipeline(self, consumer_threads, stages=0):
-        de_set_pipeline(self.ctx, consumer_threads, stages)
+    def set_pipeline(self, consumer_threads, stages=0, ctas_per_sm=0):
+        de_set_pipeline(self.ctx, consumer_threads, stages, ctas_per_sm)
 
     def pipeline(self):
         return de_get_pipeline(self.ctx)

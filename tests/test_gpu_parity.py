@@ -252,14 +252,17 @@ def test_pipeline_kernel_parity(xo, obj, N, D, CR):
     (4, 1, 0.9, 32, 0),            # D = 1
     (500, 3, 0.0, 512, 2),         # Cr = 0: L = 1
     (33, 130, 1.0, 64, 5),         # Cr = 1: L = D, the segment wraps onto itself
+    (2000, 5000, 0.9, 128, -2),    # two CTAs per SM (stages as many as fit)
 ])
 def test_pipeline_kernel_edges(xo, N, D, CR, consumers, stages):
     F, seed, obj = 0.7, 21, "rosenbrock"
     opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
     try:
         opt.set_kernel(2)
-        opt.set_pipeline(consumers, stages)
-        nc, st, span = opt.pipeline()
+        cps = 2 if stages < 0 else 1
+        stages = max(stages, 0)
+        opt.set_pipeline(consumers, stages, cps)
+        nc, st, span, cps = opt.pipeline()
         assert nc == consumers and (stages == 0 or st == stages) and span >= 16
         s, acc, _ = one_step_parity(opt, lo, hi, xo, obj, F, CR, seed)
         if CR == 0.0:
