@@ -167,7 +167,7 @@ void configure_pipe(de_ctx* c) {
 void resolve_kernel(de_ctx* c) {
   if (c->kernel_req == 2) c->use_pipe = c->pipe_ok;
   else if (c->kernel_req == 1) c->use_pipe = false;
-  else c->use_pipe = c->pipe_ok && c->D >= 2048 && c->pp.stages >= 3;
+  else c->use_pipe = c->pipe_ok && c->D >= 2048;
 }
 
 cudaError_t launch_generation(de_ctx* c, const GenParams& p) {

@@ -320,3 +320,16 @@ def test_pipeline_graph_save_load():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("D", [2048, 10000, 16000])
+def test_automatic_kernel_choice_at_large_rows(D):
+    for xo in ("exp", "nec", "bin"):
+        opt, lo, hi = make(64, D, xo, "rosenbrock", seed=1)
+        try:
+            assert opt.kernel() == (1 if xo == "bin" else 2)
+            if xo != "bin":
+                nc, stages, span, cps = opt.pipeline()
+                assert stages >= 2 and cps in (1, 2) and nc == 256
+        finally:
+            opt.close()
