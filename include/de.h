@@ -241,6 +241,36 @@ int de_set_pipeline(de_ctx *ctx, int32_t consumer_threads, int32_t stages, int32
 int de_get_pipeline(de_ctx *ctx, int32_t *consumer_threads, int32_t *stages, int32_t *span_floats,
                     int32_t *ctas_per_sm);
 
+/* ---- one generation without allocating ------------------------------------- */
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * call cudaMalloc: plug-ins running inside another framework that owns every
+ * device allocation and only lends buffers, code that must not implicitly
+ * synchronise the device (cudaMalloc and cudaFree may), and programs that
+ * reserve a fixed memory budget at start-up.
+ *
+ * One DE/rand/1/NEC generation on caller-owned device buffers; the call
+ * allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ * Its scratch (generation state, slot bytes, NEC thresholds; 256 + 2*65536 +
+ * 4*32768 bytes) is a fixed array compiled into the library, held by every GPU
+ * that loads the library until the process exits.
+ *   pop_in, pop_out: device, N rows of `pitch` floats (pitch >= D, a multiple
+ *     of 4; both bases 16-byte aligned; distinct buffers); pop_in is read only.
+ *   fit_in, fit_out: device, N floats (distinct buffers).
+ *   Row i of pop_out / fit_out receives the trial and its FP32 fitness if the
+ *   trial is strictly better than fit_in[i], else a copy of the parent row and
+ *   fit_in[i]. Draws come from Philox with (seed, generation): the result
+ *   equals what de_step computes at that generation from the same population.
+ *   Objectives: sphere .. elliptic (Ackley constant 0.2); bounds as de_create.
+ * Limits: 4 <= N <= 65536, 1 <= D <= 32768; larger sizes return DE_EINVAL.
+ * Work is queued on `cuda_stream`. The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call reuses
+ * the same scratch and clears what must start at zero; calls that overlap on
+ * the GPU (different streams or host threads) race on it. */
+int de_nec_step_noalloc(const float *pop_in, const float *fit_in, float *pop_out, float *fit_out,
+                        int32_t N, int32_t D, int32_t pitch, float F, double CR, de_objective obj,
+                        de_bounds b, uint64_t seed, int64_t generation, void *cuda_stream);
+
 /* ---- misc ----------------------------------------------------------------- */
 const char *de_strerror(int code);
 

@@ -96,6 +96,8 @@ def load_library(build_if_missing: bool = True):
         "de_get_pipeline": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "de_batch_create": ([C.POINTER(vp), i32, C.POINTER(de_instance_spec), C.c_uint64, vp], C.c_int),
         "de_batch_best": ([vp, i32, vp, C.POINTER(f64), C.POINTER(i32), C.POINTER(i64)], C.c_int),
+        "de_nec_step_noalloc": ([vp, vp, vp, vp, i32, i32, i32, f32, f64, C.c_int, de_bounds, C.c_uint64,
+                                 i64, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -304,6 +306,18 @@ def de_batch_best(ctx, inst, x_out=None):
     _check(load_library().de_batch_best(C.c_void_p(ctx), int(inst), xp, C.byref(f), C.byref(idx), C.byref(bg)),
            "de_batch_best")
     return f.value, idx.value, bg.value
+
+
+def de_nec_step_noalloc(pop_in, fit_in, pop_out, fit_out, N, D, pitch, F, CR, obj, bounds, seed,
+                        generation, stream=None):
+    """One NEC generation on caller-owned device buffers (addresses as ints);
+    the library allocates nothing for it. See include/de.h."""
+    obj_i = OBJECTIVE[obj] if isinstance(obj, str) else int(obj)
+    _check(load_library().de_nec_step_noalloc(
+        C.c_void_p(pop_in), C.c_void_p(fit_in), C.c_void_p(pop_out), C.c_void_p(fit_out), int(N), int(D),
+        int(pitch), float(F), float(CR), obj_i, de_bounds(float(bounds[0]), float(bounds[1])),
+        int(seed) & (2**64 - 1), int(generation), C.c_void_p(stream) if stream else None),
+        "de_nec_step_noalloc")
 
 
 # ---- convenience object --------------------------------------------------------
