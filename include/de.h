@@ -198,10 +198,22 @@ typedef struct {
   de_bounds b;
 } de_instance_spec;
 
-/* Create a context running n_inst independent instances; instance k draws
- * from Philox instance field k (k < 2^24). de_step / de_run advance every
- * instance by one generation per step. Same per-instance limits as
- * de_create. */
+/* Create a context running n_inst independent instances (1 <= n_inst <=
+ * 2^24); instance k draws from Philox instance field k, so instance k of a
+ * batch reproduces a single population whose draws use instance field k.
+ * Each instance keeps its own population, fitness, counters and best. One
+ * de_step / de_run step advances every instance by one generation in one
+ * kernel launch: the instances are cut into tiles of 256 / G rows with G
+ * threads per row (G set per instance, see de_batch_set_groups) and the
+ * tiles are walked in longest-first order. Per-instance limits as de_create
+ * with D <= 16384 and non-rotated objectives (Ackley constant 0.2). The
+ * initial populations are drawn and evaluated before the call returns.
+ * Single-population calls (de_best, de_get_population, de_set_population,
+ * de_debug_step, de_set_kernel, ...) return DE_ESTATE on a batch; de_save
+ * and de_load return DE_EUNSUPPORTED. de_stats returns totals: summed
+ * accepts and masked genes, the common generation, and in best_f / best_gen
+ * / best_index the best value over all instances, its generation and the
+ * instance that holds it. */
 int de_batch_create(de_ctx **out, int32_t n_inst, const de_instance_spec *specs,
                     uint64_t seed, void *cuda_stream);
 
@@ -209,6 +221,27 @@ int de_batch_create(de_ctx **out, int32_t n_inst, const de_instance_spec *specs,
  * instance's D floats. */
 int de_batch_best(de_ctx *ctx, int32_t inst, float *x_out, double *f_out,
                   int32_t *idx_out, int64_t *best_gen_out);
+
+/* Counters of instance `inst`, as de_stats for a single population. */
+int de_batch_stats(de_ctx *ctx, int32_t inst, de_stats_t *out);
+
+/* Population I/O of instance `inst`, as de_get_population /
+ * de_set_population (host arrays of N_inst x D_inst floats). */
+int de_batch_get_population(de_ctx *ctx, int32_t inst, float *pop_out, float *fit_out);
+int de_batch_set_population(de_ctx *ctx, int32_t inst, const float *pop, const float *fit);
+
+/* Test hook: one generation of every instance, reporting for instance
+ * `inst` what de_debug_step reports for a single population. */
+int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftrial_out,
+                        uint8_t *accept_out, int32_t *draws_out);
+
+/* Tile shape per instance: threads per row G (a power of two, 4..256, with
+ * ceil(ceil(D/4) / G) <= 16; 0 = the default, the smallest such G). Tuning
+ * only: draws are unchanged, FP32 fitness rounding may change. */
+int de_batch_set_groups(de_ctx *ctx, const int32_t *groups);
+int de_batch_get_groups(de_ctx *ctx, int32_t *groups);
+/* Number of instances (0 for a single-population context). */
+int de_batch_size(de_ctx *ctx, int32_t *n_inst);
 
 /* ---- launch shape --------------------------------------------------------- */
 /* Each row is processed by one CTA of `threads` threads (multiple of 32,

@@ -12,60 +12,19 @@
 #include <new>
 #include <vector>
 
-#include "../../include/de.h"
-#include "gen_pipe.cuh"
-#include "internal.h"
+#include "ctx.h"
 
-using namespace de;
+using namespace de_host;
+
+namespace de_host {
 
 namespace {
-
 de_alloc_fn g_alloc = nullptr;
 de_free_fn g_free = nullptr;
 void* g_alloc_user = nullptr;
-
-struct Block {
-  void* ptr;
-  size_t bytes;
-};
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? DE_OK : DE_ECUDA; }
-
 }  // namespace
 
-struct de_ctx {
-  int32_t N = 0, D = 0, pitch = 0, D4 = 0;
-  float F = 0.f;
-  double CR = 0.0;
-  int xo = 0, obj = 0;
-  de_bounds b{0.f, 0.f};
-  uint64_t seed = 0;
-  uint32_t inst = 0;
-  double ackley_b = 0.2;
-  cudaStream_t stream = nullptr;
-  int block = 32, vidx = 0;
-  // kernel choice: 0 = automatic, 1 = row per CTA, 2 = pipelined (exp / NEC)
-  int kernel_req = 0;
-  bool use_pipe = false;
-  bool pipe_ok = false;
-  PipeParams pp{};
-  int pipe_grid = 0, pipe_block = 32 + 256;
-  int pipe_stages_req = 0;       // 0 = as many as fit
-  int pipe_cps = 0;              // CTAs per SM (1 or 2); 0 = automatic
-  int smem_per_sm = 0;
-  int pp_cps = 1;                // CTAs per SM in use
-  size_t pipe_smem = 0;
-  int sm_count = 0, smem_optin = 0;
-  GenParams p{};
-  std::vector<Block> blocks;
-  std::map<int32_t, cudaGraphExec_t> graphs;
-  void* staging = nullptr;       // device: best row gather
-  void* host_pinned = nullptr;   // host: staging copy and state reads
-  size_t host_pinned_bytes = 0;
-  long long host_gen = 0;
-};
-
-namespace {
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? DE_OK : DE_ECUDA; }
 
 void* ctx_alloc(de_ctx* c, size_t bytes) {
   if (bytes == 0) bytes = 256;
@@ -119,6 +78,21 @@ void choose_launch(int D4, int& block, int& vidx) {
 
 bool is_rotated(int obj) { return obj == DE_OBJ_SR_RASTRIGIN || obj == DE_OBJ_SR_ELLIPTIC; }
 
+std::vector<uint32_t> nec_thresholds(double CR, int D) {
+  const std::vector<uint32_t> tm1 = nec_thresholds(CR, D);
+  return tm1;
+}
+
+bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de_bounds b) {
+  if (N < 4 || N > (1 << 29) || D < 1 || D > 32768) return false;
+  if ((long long)N * (long long)D >= (1LL << 40)) return false;
+  if (!std::isfinite(F) || !(CR >= 0.0 && CR <= 1.0)) return false;
+  if (xo < DE_XOVER_BIN || xo > DE_XOVER_NEC) return false;
+  if (obj < DE_OBJ_SPHERE || obj > DE_OBJ_SR_ELLIPTIC) return false;
+  if (!std::isfinite(b.lo) || !std::isfinite(b.hi) || !(b.lo < b.hi)) return false;
+  return true;
+}
+
 // Pipelined kernel geometry. Donor span buffers hold the segment lengths
 // that occur with probability >= 1e-6 (P(L > n) = Cr^n; longer segments read
 // their donor genes from global memory), capped at min(D + 8, 1024) floats.
@@ -171,6 +145,7 @@ void resolve_kernel(de_ctx* c) {
 }
 
 cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
+  if (c->batch) return batch_launch_generation(c, false, -1);
   if (c->use_pipe) {
     PipeParams pp = c->pp;
     pp.g = p;
@@ -251,12 +226,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
               void* cuda_stream) {
   if (!out) return DE_EINVAL;
   *out = nullptr;
-  if (N < 4 || N > (1 << 29) || D < 1 || D > 32768) return DE_EINVAL;
-  if ((long long)N * (long long)D >= (1LL << 40)) return DE_EINVAL;
-  if (!std::isfinite(F) || !(CR >= 0.0 && CR <= 1.0)) return DE_EINVAL;
-  if ((int)xo < DE_XOVER_BIN || (int)xo > DE_XOVER_NEC) return DE_EINVAL;
-  if ((int)obj < DE_OBJ_SPHERE || (int)obj > DE_OBJ_SR_ELLIPTIC) return DE_EINVAL;
-  if (!std::isfinite(b.lo) || !std::isfinite(b.hi) || !(b.lo < b.hi)) return DE_EINVAL;
+  if (!valid_problem(N, D, F, CR, (int)xo, (int)obj, b)) return DE_EINVAL;
   if (is_rotated(obj)) {
     if (!prm || !prm->shift || !prm->rotation) return DE_EINVAL;
     return DE_EUNSUPPORTED;
@@ -286,16 +256,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
 
   // NEC thresholds T_n - 1, T_n = ceil(c_n 2^32), c_1 = Cr, c_n = fl(c_{n-1} Cr);
   // stop before the first T_n <= 1 or at n = D - 1.
-  std::vector<uint32_t> tm1;
-  if (CR > 0.0 && CR < 1.0) {
-    double cn = CR;
-    for (int n = 1; n <= D - 1; ++n) {
-      const double Tn = std::ceil(cn * 4294967296.0);
-      if (Tn <= 1.0) break;
-      tm1.push_back((uint32_t)(Tn - 1.0));
-      cn = cn * CR;
-    }
-  }
+  const std::vector<uint32_t> tm1 = nec_thresholds(CR, D);
 
   const size_t pop_bytes = (size_t)N * (size_t)c->pitch * sizeof(float);
   float* pop0 = (float*)ctx_alloc(c, pop_bytes);
@@ -412,6 +373,7 @@ int de_run(de_ctx* c, int32_t generations) {
 
 int de_synchronize(de_ctx* c) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return sync_stream(c);
   if (cudaMemcpyAsync(c->host_pinned, &c->p.st->error, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream) !=
       cudaSuccess)
     return DE_ECUDA;
@@ -424,6 +386,7 @@ int de_synchronize(de_ctx* c) {
 
 int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* best_gen_out) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   cudaError_t e = launch_best_gather(c->p, c->staging, c->stream);
   const size_t bytes = kStagingHeader + (size_t)c->D * sizeof(float);
   if (e == cudaSuccess)
@@ -444,6 +407,7 @@ int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* b
 
 int de_stats(de_ctx* c, de_stats_t* out) {
   if (!c || !out) return DE_EINVAL;
+  if (c->batch) return batch_stats(c, out);
   if (cudaMemcpyAsync(c->host_pinned, c->p.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=
       cudaSuccess)
     return DE_ECUDA;
@@ -464,6 +428,7 @@ int de_stats(de_ctx* c, de_stats_t* out) {
 
 int de_get_population(de_ctx* c, float* pop_out, float* fit_out) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   cudaError_t e = launch_normalize(c->p, c->stream);
   if (e == cudaSuccess && pop_out)
     e = cudaMemcpy2DAsync(pop_out, (size_t)c->D * sizeof(float), c->p.pop0, (size_t)c->pitch * sizeof(float),
@@ -476,6 +441,7 @@ int de_get_population(de_ctx* c, float* pop_out, float* fit_out) {
 
 int de_set_population(de_ctx* c, const float* pop, const float* fit) {
   if (!c || !pop) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   // the current generation's slot half is cleared: buffer 0 holds every row
   cudaError_t e = cudaMemsetAsync(c->p.slots + (size_t)(c->host_gen & 1) * c->N, 0, (size_t)c->N, c->stream);
   if (e == cudaSuccess)
@@ -498,6 +464,7 @@ int de_set_population(de_ctx* c, const float* pop, const float* fit) {
 
 int de_save(de_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return DE_EINVAL;
+  if (c->batch) return DE_EUNSUPPORTED;
   const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
   if (!buf) {
     *len = need;
@@ -535,7 +502,9 @@ int de_save(de_ctx* c, void* buf, size_t* len) {
 }
 
 int de_load(de_ctx* c, const void* buf, size_t len) {
-  if (!c || !buf || len < sizeof(SaveHeader)) return DE_EINVAL;
+  if (!c || !buf) return DE_EINVAL;
+  if (c->batch) return DE_EUNSUPPORTED;
+  if (len < sizeof(SaveHeader)) return DE_EINVAL;
   SaveHeader h;
   std::memcpy(&h, buf, sizeof(h));
   const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
@@ -567,6 +536,7 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
 
 int de_debug_step(de_ctx* c, float* trial_out, float* ftrial_out, uint8_t* accept_out, int32_t* draws_out) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   GenParams p = c->p;
   float* dtrial = trial_out ? (float*)ctx_alloc(c, (size_t)c->N * c->pitch * sizeof(float)) : nullptr;
   float* dft = ftrial_out ? (float*)ctx_alloc(c, (size_t)c->N * sizeof(float)) : nullptr;
@@ -603,6 +573,7 @@ int de_debug_step(de_ctx* c, float* trial_out, float* ftrial_out, uint8_t* accep
 
 int de_set_launch(de_ctx* c, int32_t threads, int32_t vec4) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   int vidx = -1;
   for (int k = 0; k < 5; ++k)
     if (kVecChoices[k] == vec4) vidx = k;
@@ -616,6 +587,7 @@ int de_set_launch(de_ctx* c, int32_t threads, int32_t vec4) {
 
 int de_set_kernel(de_ctx* c, int32_t kind) {
   if (!c || kind < 0 || kind > 2) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   if (kind == 2 && !c->pipe_ok) return DE_EUNSUPPORTED;
   c->kernel_req = kind;
   resolve_kernel(c);
@@ -625,12 +597,14 @@ int de_set_kernel(de_ctx* c, int32_t kind) {
 
 int de_get_kernel(de_ctx* c, int32_t* kind) {
   if (!c || !kind) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   *kind = c->use_pipe ? 2 : 1;
   return DE_OK;
 }
 
 int de_set_pipeline(de_ctx* c, int32_t consumer_threads, int32_t stages, int32_t ctas_per_sm) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   if (consumer_threads < 32 || consumer_threads > 32 * kPipeMaxConsumerWarps || consumer_threads % 32 != 0)
     return DE_EINVAL;
   if (stages != 0 && (stages < 2 || stages > kPipeMaxStages)) return DE_EINVAL;
@@ -647,6 +621,7 @@ int de_set_pipeline(de_ctx* c, int32_t consumer_threads, int32_t stages, int32_t
 int de_get_pipeline(de_ctx* c, int32_t* consumer_threads, int32_t* stages, int32_t* span_floats,
                     int32_t* ctas_per_sm) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   if (!c->pipe_ok) return DE_EUNSUPPORTED;
   if (ctas_per_sm) *ctas_per_sm = c->pp_cps;
   if (consumer_threads) *consumer_threads = c->pipe_block - 32;
@@ -657,23 +632,10 @@ int de_get_pipeline(de_ctx* c, int32_t* consumer_threads, int32_t* stages, int32
 
 int de_get_launch(de_ctx* c, int32_t* threads, int32_t* vec4) {
   if (!c) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
   if (threads) *threads = c->block;
   if (vec4) *vec4 = kVecChoices[c->vidx];
   return DE_OK;
-}
-
-int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs, uint64_t seed,
-                    void* cuda_stream) {
-  (void)n_inst; (void)specs; (void)seed; (void)cuda_stream;
-  if (!out) return DE_EINVAL;
-  *out = nullptr;
-  return DE_EUNSUPPORTED;
-}
-
-int de_batch_best(de_ctx* c, int32_t inst, float* x_out, double* f_out, int32_t* idx_out,
-                  int64_t* best_gen_out) {
-  (void)c; (void)inst; (void)x_out; (void)f_out; (void)idx_out; (void)best_gen_out;
-  return DE_EUNSUPPORTED;
 }
 
 }  // extern "C"

@@ -1,0 +1,82 @@
+// ctx.h — the opaque de_ctx of the C ABI and host helpers shared by the
+// single-population API (api.cu) and the batched API (batch_api.cu).
+#pragma once
+#include <cstddef>
+#include <map>
+#include <vector>
+
+#include "../../include/de.h"
+#include "gen_pipe.cuh"
+#include "internal.h"
+
+using namespace de;
+
+namespace de_host {
+struct Block {
+  void* ptr;
+  size_t bytes;
+};
+}  // namespace de_host
+
+struct de_ctx {
+  int32_t N = 0, D = 0, pitch = 0, D4 = 0;
+  float F = 0.f;
+  double CR = 0.0;
+  int xo = 0, obj = 0;
+  de_bounds b{0.f, 0.f};
+  uint64_t seed = 0;
+  uint32_t inst = 0;
+  double ackley_b = 0.2;
+  cudaStream_t stream = nullptr;
+  int block = 32, vidx = 0;
+  // kernel choice: 0 = automatic, 1 = row per CTA, 2 = pipelined (exp / NEC)
+  int kernel_req = 0;
+  bool use_pipe = false;
+  bool pipe_ok = false;
+  PipeParams pp{};
+  int pipe_grid = 0, pipe_block = 32 + 256;
+  int pipe_stages_req = 0;       // 0 = as many as fit
+  int pipe_cps = 0;              // CTAs per SM (1 or 2); 0 = automatic
+  int smem_per_sm = 0;
+  int pp_cps = 1;                // CTAs per SM in use
+  size_t pipe_smem = 0;
+  int sm_count = 0, smem_optin = 0;
+  GenParams p{};
+  std::vector<de_host::Block> blocks;
+  std::map<int32_t, cudaGraphExec_t> graphs;
+  void* staging = nullptr;       // device: best row gather
+  void* host_pinned = nullptr;   // host: staging copy and state reads
+  size_t host_pinned_bytes = 0;
+  long long host_gen = 0;
+  // batched contexts (de_batch_create); the fields above then describe nothing
+  bool batch = false;
+  int n_inst = 0;
+  std::vector<GenParams> bp;          // per instance, device pointers into the arena
+  std::vector<int> bobj, bxo, bgroup, bt0, bt1;   // objective, crossover, group, tile range
+  std::vector<double> bcr;
+  std::vector<float> bF;
+  std::vector<de_bounds> bb;
+  de::BatchInst* d_insts = nullptr;
+  de::BatchTile* d_tiles = nullptr;
+  de::DevState* d_states = nullptr;
+  int ntiles = 0, batch_grid = 0, max_pitch = 0;
+};
+
+
+
+namespace de_host {
+int cuda_status(cudaError_t e);
+void* ctx_alloc(de_ctx* c, size_t bytes);
+void ctx_free(de_ctx* c, void* p);
+void drop_graphs(de_ctx* c);
+void choose_launch(int D4, int& block, int& vidx);
+int sync_stream(de_ctx* c);
+// NEC thresholds T_n - 1 = ceil(c_n 2^32) - 1, c_1 = Cr, c_n = fl(c_{n-1} Cr),
+// up to n = D - 1 or before the first T_n <= 1.
+std::vector<uint32_t> nec_thresholds(double CR, int D);
+// Validation shared by de_create and de_batch_create (non-rotated objectives).
+bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de_bounds b);
+// Batched contexts (batch_api.cu).
+cudaError_t batch_launch_generation(de_ctx* c, bool with_debug_of_inst, int inst);
+int batch_stats(de_ctx* c, de_stats_t* out);
+}  // namespace de_host

@@ -35,6 +35,22 @@ cudaError_t prepare_gen_pipe(int xo, int obj, size_t smem);
 cudaError_t launch_gen_pipe(int xo, int obj, const PipeParams& pp, int grid, int block, size_t smem,
                             cudaStream_t s);
 
+// Batched instances (batch_kernel.cu): one descriptor per instance and a
+// tile list; a tile is 256 / group rows of one instance.
+struct BatchInst {
+  GenParams g;
+  int obj, xo, group, tiles;
+};
+struct BatchTile {
+  int inst, row0;
+};
+constexpr int kBatchThreadsHost = 256;
+constexpr int kBatchMaxGroup = 256;
+constexpr int kBatchMaxD4PerLane = 16;
+cudaError_t launch_batch_gen(const BatchInst* insts, const BatchTile* tiles, int ntiles, int grid, bool eval_only,
+                             cudaStream_t s);
+cudaError_t launch_batch_reset_best(DevState* states, int n, cudaStream_t s);
+
 constexpr size_t kStagingHeader = 32;
 
 }  // namespace de

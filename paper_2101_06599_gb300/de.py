@@ -96,6 +96,13 @@ def load_library(build_if_missing: bool = True):
         "de_get_pipeline": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "de_batch_create": ([C.POINTER(vp), i32, C.POINTER(de_instance_spec), C.c_uint64, vp], C.c_int),
         "de_batch_best": ([vp, i32, vp, C.POINTER(f64), C.POINTER(i32), C.POINTER(i64)], C.c_int),
+        "de_batch_stats": ([vp, i32, C.POINTER(de_stats_t)], C.c_int),
+        "de_batch_get_population": ([vp, i32, vp, vp], C.c_int),
+        "de_batch_set_population": ([vp, i32, vp, vp], C.c_int),
+        "de_batch_debug_step": ([vp, i32, vp, vp, vp, vp], C.c_int),
+        "de_batch_set_groups": ([vp, C.POINTER(i32)], C.c_int),
+        "de_batch_get_groups": ([vp, C.POINTER(i32)], C.c_int),
+        "de_batch_size": ([vp, C.POINTER(i32)], C.c_int),
         "de_nec_step_noalloc": ([vp, vp, vp, vp, i32, i32, i32, f32, f64, C.c_int, de_bounds, C.c_uint64,
                                  i64, vp], C.c_int),
     }
@@ -308,6 +315,49 @@ def de_batch_best(ctx, inst, x_out=None):
     return f.value, idx.value, bg.value
 
 
+def de_batch_stats(ctx, inst):
+    s = de_stats_t()
+    _check(load_library().de_batch_stats(C.c_void_p(ctx), int(inst), C.byref(s)), "de_batch_stats")
+    return {k: getattr(s, k) for k, _ in de_stats_t._fields_}
+
+
+def de_batch_get_population(ctx, inst, pop_out, fit_out):
+    _check(load_library().de_batch_get_population(C.c_void_p(ctx), int(inst), _host_ptr(pop_out, np.float32, 1, True),
+                                                  _host_ptr(fit_out, np.float32, 1, True)),
+           "de_batch_get_population")
+
+
+def de_batch_set_population(ctx, inst, pop, fit=None):
+    _check(load_library().de_batch_set_population(C.c_void_p(ctx), int(inst), _host_ptr(pop, np.float32, 1, False),
+                                                  _host_ptr(fit, np.float32, 1, False)),
+           "de_batch_set_population")
+
+
+def de_batch_debug_step(ctx, inst, trial_out=None, ftrial_out=None, accept_out=None, draws_out=None):
+    _check(load_library().de_batch_debug_step(
+        C.c_void_p(ctx), int(inst), _host_ptr(trial_out, np.float32, 1, True),
+        _host_ptr(ftrial_out, np.float32, 1, True), _host_ptr(accept_out, np.uint8, 1, True),
+        _host_ptr(draws_out, np.int32, 1, True)), "de_batch_debug_step")
+
+
+def de_batch_size(ctx):
+    n = C.c_int32()
+    _check(load_library().de_batch_size(C.c_void_p(ctx), C.byref(n)), "de_batch_size")
+    return n.value
+
+
+def de_batch_set_groups(ctx, groups):
+    arr = (C.c_int32 * len(groups))(*[int(g) for g in groups])
+    _check(load_library().de_batch_set_groups(C.c_void_p(ctx), arr), "de_batch_set_groups")
+
+
+def de_batch_get_groups(ctx):
+    n = de_batch_size(ctx)
+    arr = (C.c_int32 * n)()
+    _check(load_library().de_batch_get_groups(C.c_void_p(ctx), arr), "de_batch_get_groups")
+    return [int(v) for v in arr]
+
+
 def de_nec_step_noalloc(pop_in, fit_in, pop_out, fit_out, N, D, pitch, F, CR, obj, bounds, seed,
                         generation, stream=None):
     """One NEC generation on caller-owned device buffers (addresses as ints);
@@ -318,6 +368,81 @@ def de_nec_step_noalloc(pop_in, fit_in, pop_out, fit_out, N, D, pitch, F, CR, ob
         int(pitch), float(F), float(CR), obj_i, de_bounds(float(bounds[0]), float(bounds[1])),
         int(seed) & (2**64 - 1), int(generation), C.c_void_p(stream) if stream else None),
         "de_nec_step_noalloc")
+
+
+class Batch:
+    """Many independent DE instances on the current CUDA device, advanced
+    together (de_batch_create / de_step / de_run / de_batch_best ...).
+
+    specs: list of dicts with N, D, obj, bounds and optionally F, CR, xo."""
+
+    def __init__(self, specs, seed=1, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libde needs a CUDA GPU; no CPU fallback exists")
+        use_torch_allocator(True)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.specs = [dict(s) for s in specs]
+        self.ctx = de_batch_create(self.specs, seed, self.stream.cuda_stream)
+
+    def __len__(self):
+        return len(self.specs)
+
+    def step(self):
+        de_step(self.ctx)
+
+    def run(self, generations):
+        de_run(self.ctx, generations)
+
+    def synchronize(self):
+        de_synchronize(self.ctx)
+
+    def stats(self, inst=None):
+        return de_stats(self.ctx) if inst is None else de_batch_stats(self.ctx, inst)
+
+    def best(self, inst):
+        x = np.empty(self.specs[inst]["D"], dtype=np.float32)
+        f, idx, bg = de_batch_best(self.ctx, inst, x)
+        return x, f, idx, bg
+
+    def population(self, inst):
+        N, D = self.specs[inst]["N"], self.specs[inst]["D"]
+        pop = np.empty((N, D), dtype=np.float32)
+        fit = np.empty(N, dtype=np.float32)
+        de_batch_get_population(self.ctx, inst, pop, fit)
+        return pop, fit
+
+    def set_population(self, inst, pop, fit=None):
+        pop = np.ascontiguousarray(pop, dtype=np.float32)
+        if fit is not None:
+            fit = np.ascontiguousarray(fit, dtype=np.float32)
+        de_batch_set_population(self.ctx, inst, pop, fit)
+
+    def debug_step(self, inst):
+        N, D = self.specs[inst]["N"], self.specs[inst]["D"]
+        trial = np.empty((N, D), dtype=np.float32)
+        ft = np.empty(N, dtype=np.float32)
+        acc = np.empty(N, dtype=np.uint8)
+        dr = np.empty((N, 5), dtype=np.int32)
+        de_batch_debug_step(self.ctx, inst, trial, ft, acc, dr)
+        return trial, ft, acc.astype(bool), dr
+
+    def groups(self):
+        return de_batch_get_groups(self.ctx)
+
+    def set_groups(self, groups):
+        de_batch_set_groups(self.ctx, groups)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            de_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience object --------------------------------------------------------
