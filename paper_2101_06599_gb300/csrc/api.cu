@@ -79,7 +79,16 @@ void choose_launch(int D4, int& block, int& vidx) {
 bool is_rotated(int obj) { return obj == DE_OBJ_SR_RASTRIGIN || obj == DE_OBJ_SR_ELLIPTIC; }
 
 std::vector<uint32_t> nec_thresholds(double CR, int D) {
-  const std::vector<uint32_t> tm1 = nec_thresholds(CR, D);
+  std::vector<uint32_t> tm1;
+  if (CR > 0.0 && CR < 1.0) {
+    double cn = CR;
+    for (int n = 1; n <= D - 1; ++n) {
+      const double Tn = std::ceil(cn * 4294967296.0);
+      if (Tn <= 1.0) break;
+      tm1.push_back((uint32_t)(Tn - 1.0));
+      cn = cn * CR;
+    }
+  }
   return tm1;
 }
 

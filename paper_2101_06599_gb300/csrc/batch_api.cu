@@ -159,7 +159,7 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   unsigned char* arena = (unsigned char*)ctx_alloc(c, bytes);
   c->d_insts = (BatchInst*)ctx_alloc(c, (size_t)n_inst * sizeof(BatchInst));
   c->staging = ctx_alloc(c, kStagingHeader + (size_t)c->max_pitch * sizeof(float));
-  c->host_pinned_bytes = kStagingHeader + (size_t)c->max_pitch * sizeof(float);
+  c->host_pinned_bytes = std::max(kStagingHeader + (size_t)c->max_pitch * sizeof(float), sizeof(DevState));
   if (!arena || !c->d_insts || !c->staging || cudaMallocHost(&c->host_pinned, c->host_pinned_bytes) != cudaSuccess) {
     cudaGetLastError();
     de_destroy(c);

@@ -78,3 +78,18 @@ def test_null_context_calls_are_rejected(lib):
 def test_allocator_hook_must_be_paired(lib):
     assert lib.de_set_allocator(DE._alloc_cb, DE._FREE_FN(), None) == DE.DE_EINVAL
     assert lib.de_set_allocator(DE._ALLOC_FN(), DE._FREE_FN(), None) == DE.DE_OK
+
+
+def test_create_without_a_device_fails_cleanly(lib):
+    """On a machine without a GPU a valid request reaches allocation and
+    fails there with a status code (exercises the whole host set-up path)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(DE.DEError) as e:
+        DE.de_create(64, 100, 0.5, 0.9, "nec", "sphere", (-1.0, 1.0), 1)
+    assert e.value.code in (DE.DE_ENOMEM, DE.DE_ECUDA)
+    specs = [dict(N=8, D=5, obj="sphere", bounds=(-1.0, 1.0)), dict(N=16, D=300, obj="ackley", bounds=(-30.0, 30.0))]
+    with pytest.raises(DE.DEError) as e:
+        DE.de_batch_create(specs, 1)
+    assert e.value.code in (DE.DE_ENOMEM, DE.DE_ECUDA)
