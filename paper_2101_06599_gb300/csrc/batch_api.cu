@@ -6,7 +6,9 @@
 // one DevState per instance (contiguous, so the totals are one copy).
 // Tiles: instance k is cut into ceil(N_k / R_k) tiles of R_k = 256 / G_k
 // rows; the tile list is ordered by tile cost (R_k D_k, descending), a
-// longest-processing-time schedule for the grid-stride walk.
+// longest-processing-time schedule for the grid-stride walk. A second list
+// of 256-row tiles drives the plan kernel; plans (32 bytes per row of every
+// instance) live in one buffer indexed by the instance's first row.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,6 +35,7 @@ static int upload_insts(de_ctx* c) {
     h[k].xo = c->bxo[k];
     h[k].group = c->bgroup[k];
     h[k].tiles = c->bt1[k] - c->bt0[k];
+    h[k].row_base = c->brow_base[k];
   }
   if (cudaMemcpyAsync(c->d_insts, h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, c->stream) !=
       cudaSuccess)
@@ -68,24 +71,35 @@ static int build_tiles(de_ctx* c) {
   return upload_insts(c);
 }
 
-// Evaluate the parents of instances whose tiles lie in [t0, t1) (all when the
-// range is the whole list): reset their best keys first.
+// Evaluate the parents of every instance (inst < 0) or of one instance.
 static int batch_evaluate(de_ctx* c, int inst) {
   cudaError_t e;
-  if (inst < 0) {
-    e = launch_batch_reset_best(c->d_states, c->n_inst, c->stream);
-    if (e == cudaSuccess) e = launch_batch_gen(c->d_insts, c->d_tiles, c->ntiles, c->batch_grid, true, c->stream);
-  } else {
-    e = launch_reset_best(c->bp[inst], c->stream);
-    if (e == cudaSuccess)
-      e = launch_batch_gen(c->d_insts, c->d_tiles + c->bt0[inst], c->bt1[inst] - c->bt0[inst], c->batch_grid, true,
-                           c->stream);
-  }
+  if (inst < 0)
+    e = launch_batch_evaluate(c->d_insts, c->d_tiles, c->ntiles, c->d_states, 0, c->n_inst, c->batch_grid,
+                              c->stream);
+  else
+    e = launch_batch_evaluate(c->d_insts, c->d_tiles + c->bt0[inst], c->bt1[inst] - c->bt0[inst], c->d_states,
+                              inst, 1, c->batch_grid, c->stream);
   return cuda_status(e);
 }
 
 cudaError_t batch_launch_generation(de_ctx* c, bool, int) {
-  return launch_batch_gen(c->d_insts, c->d_tiles, c->ntiles, c->batch_grid, false, c->stream);
+  return launch_batch_generation(c->d_insts, c->d_tiles, c->ntiles, c->d_ptiles, c->nptiles, c->d_plans,
+                                 c->d_states, c->n_inst, c->batch_grid, c->stream);
+}
+
+// Plan tiles: 256 consecutive rows of one instance, instances in order.
+static int build_plan_tiles(de_ctx* c) {
+  std::vector<BatchTile> pt;
+  for (int k = 0; k < c->n_inst; ++k)
+    for (int r = 0; r < c->bp[k].N; r += kBatchThreadsHost) pt.push_back(BatchTile{k, r});
+  c->d_ptiles = (BatchTile*)ctx_alloc(c, pt.size() * sizeof(BatchTile));
+  if (!c->d_ptiles) return DE_ENOMEM;
+  c->nptiles = (int)pt.size();
+  if (cudaMemcpyAsync(c->d_ptiles, pt.data(), pt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess)
+    return DE_ECUDA;
+  return sync_stream(c);
 }
 
 int batch_stats(de_ctx* c, de_stats_t* out) {
@@ -176,6 +190,17 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   c->bb.resize((size_t)n_inst);
   std::vector<DevState> st0((size_t)n_inst);
   std::memset(st0.data(), 0, st0.size() * sizeof(DevState));
+  c->brow_base.resize((size_t)n_inst);
+  long long rows = 0;
+  for (int k = 0; k < n_inst; ++k) {
+    c->brow_base[k] = rows;
+    rows += specs[k].N;
+  }
+  c->d_plans = (RowPlan32*)ctx_alloc(c, (size_t)rows * sizeof(RowPlan32));
+  if (!c->d_plans) {
+    de_destroy(c);
+    return DE_ENOMEM;
+  }
   for (int k = 0; k < n_inst; ++k) {
     const de_instance_spec& s = specs[k];
     GenParams& p = c->bp[k];
@@ -219,6 +244,7 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   for (int k = 0; k < n_inst && e == cudaSuccess; ++k) e = launch_init(c->bp[k], c->stream);
   int rc = cuda_status(e);
   if (rc == DE_OK) rc = sync_stream(c);              // host tables and states consumed
+  if (rc == DE_OK) rc = build_plan_tiles(c);
   if (rc == DE_OK) rc = build_tiles(c);
   if (rc == DE_OK) rc = batch_evaluate(c, -1);
   if (rc == DE_OK) rc = sync_stream(c);

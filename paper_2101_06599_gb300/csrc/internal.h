@@ -40,16 +40,31 @@ cudaError_t launch_gen_pipe(int xo, int obj, const PipeParams& pp, int grid, int
 struct BatchInst {
   GenParams g;
   int obj, xo, group, tiles;
+  long long row_base;        // first plan index of this instance
 };
 struct BatchTile {
   int inst, row0;
 };
+// Draws of one row, written by the plan kernel: donors, j_rand, L, the slot
+// bytes of the row and its donors (bits 0-7, 8-15, 16-23, 24-31) and the
+// parent fitness.
+struct RowPlan32 {
+  int r1, r2, r3, jrand, L;
+  uint32_t slots;
+  float fit_i;
+  int pad;
+};
 constexpr int kBatchThreadsHost = 256;
 constexpr int kBatchMaxGroup = 256;
 constexpr int kBatchMaxD4PerLane = 16;
-cudaError_t launch_batch_gen(const BatchInst* insts, const BatchTile* tiles, int ntiles, int grid, bool eval_only,
-                             cudaStream_t s);
-cudaError_t launch_batch_reset_best(DevState* states, int n, cudaStream_t s);
+// plan kernel + row kernel + close kernel (one generation of every instance)
+cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* tiles, int ntiles,
+                                    const BatchTile* ptiles, int nptiles, RowPlan32* plans, DevState* states,
+                                    int n_inst, int grid, cudaStream_t s);
+// reset best keys, evaluate the parents of the tiles' rows, close (instances
+// first_inst .. first_inst + n_inst - 1)
+cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* tiles, int ntiles, DevState* states,
+                                  int first_inst, int n_inst, int grid, cudaStream_t s);
 
 constexpr size_t kStagingHeader = 32;
 
