@@ -27,16 +27,22 @@ static int default_group(int D4) {
   return G;
 }
 
+// The device descriptor of instance k (every field set here, nowhere else).
+static BatchInst make_inst(const de_ctx* c, int k) {
+  BatchInst bi;
+  std::memset(&bi, 0, sizeof(bi));
+  bi.g = c->bp[k];
+  bi.obj = c->bobj[k];
+  bi.xo = c->bxo[k];
+  bi.group = c->bgroup[k];
+  bi.tiles = c->bt1[k] - c->bt0[k];
+  bi.row_base = c->brow_base[k];
+  return bi;
+}
+
 static int upload_insts(de_ctx* c) {
   std::vector<BatchInst> h((size_t)c->n_inst);
-  for (int k = 0; k < c->n_inst; ++k) {
-    h[k].g = c->bp[k];
-    h[k].obj = c->bobj[k];
-    h[k].xo = c->bxo[k];
-    h[k].group = c->bgroup[k];
-    h[k].tiles = c->bt1[k] - c->bt0[k];
-    h[k].row_base = c->brow_base[k];
-  }
+  for (int k = 0; k < c->n_inst; ++k) h[k] = make_inst(c, k);
   if (cudaMemcpyAsync(c->d_insts, h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, c->stream) !=
       cudaSuccess)
     return DE_ECUDA;
@@ -346,12 +352,7 @@ int de_batch_debug_step(de_ctx* c, int32_t inst, float* trial_out, float* ftrial
   if (!c->batch) return DE_ESTATE;
   if (inst < 0 || inst >= c->n_inst) return DE_EINVAL;
   const GenParams& p0 = c->bp[inst];
-  BatchInst bi;
-  bi.g = p0;
-  bi.obj = c->bobj[inst];
-  bi.xo = c->bxo[inst];
-  bi.group = c->bgroup[inst];
-  bi.tiles = c->bt1[inst] - c->bt0[inst];
+  BatchInst bi = make_inst(c, inst);
   float* dtrial = trial_out ? (float*)ctx_alloc(c, (size_t)p0.N * p0.pitch * sizeof(float)) : nullptr;
   float* dft = ftrial_out ? (float*)ctx_alloc(c, (size_t)p0.N * sizeof(float)) : nullptr;
   uint8_t* dacc = accept_out ? (uint8_t*)ctx_alloc(c, (size_t)p0.N) : nullptr;
