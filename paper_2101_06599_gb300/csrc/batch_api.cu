@@ -5,8 +5,9 @@
 // buffers (N x pitch floats), fitness, slot bytes and NEC thresholds, plus
 // one DevState per instance (contiguous, so the totals are one copy).
 // Tiles: instance k is cut into ceil(N_k / R_k) tiles of R_k = 256 / G_k
-// rows; the tile list is ordered by tile cost (R_k D_k, descending), a
-// longest-processing-time schedule for the grid-stride walk. A second list
+// rows; the tile list is grouped by (objective, crossover) and ordered by
+// tile cost (R_k D_k, descending) within a group, a longest-processing-time
+// schedule for the grid-stride walk. A second list
 // of 256-row tiles drives the plan kernel; plans (32 bytes per row of every
 // instance) live in one buffer indexed by the instance's first row.
 #include <algorithm>
@@ -52,7 +53,11 @@ static int upload_insts(de_ctx* c) {
 static int build_tiles(de_ctx* c) {
   std::vector<int> order((size_t)c->n_inst);
   std::iota(order.begin(), order.end(), 0);
+  // grouped by (objective, crossover) so that one specialisation of the row
+  // code runs at a time; longest tiles first within a group
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ca = c->bobj[a] * 3 + c->bxo[a], cb = c->bobj[b] * 3 + c->bxo[b];
+    if (ca != cb) return ca < cb;
     return (double)(kBatchThreadsHost / c->bgroup[a]) * c->bp[a].D >
            (double)(kBatchThreadsHost / c->bgroup[b]) * c->bp[b].D;
   });

@@ -9,8 +9,9 @@
 //     independent, so the serial draw work of one row never delays another.
 //  2. batch_gen_kernel: the host cuts every instance into tiles of
 //     R = 256 / G rows, G threads per row (G a power of two, 4..256, per
-//     instance); the grid walks the tile list (longest first) with a grid
-//     stride. A row's group reads its plan, then issues the parent loads and
+//     instance); the grid walks the tile list with a grid stride. The list is
+//     grouped by (objective, crossover), longest tiles first within a group,
+//     and each tile calls the row code specialised for its group. A row's group reads its plan, then issues the parent loads and
 //     the donor loads of the masked genes together (one memory round trip),
 //     applies Eq. (1) with clipping, reduces the FP32 fitness over the group,
 //     selects (strict '<') and stores accepted rows to the other slot buffer.
@@ -29,24 +30,6 @@ namespace de {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchVmax = 16;
 constexpr int kBatchTableCap = 4096;
-
-__device__ __forceinline__ void accum_gene_rt(int obj, Acc& s, float x, int j, const GenParams& p) {
-  switch (obj) {
-    case kSphere: accum_gene<kSphere>(s, x, j, p); break;
-    case kRastrigin: accum_gene<kRastrigin>(s, x, j, p); break;
-    case kAckley: accum_gene<kAckley>(s, x, j, p); break;
-    case kGriewank: accum_gene<kGriewank>(s, x, j, p); break;
-    default: accum_gene<kElliptic>(s, x, j, p); break;
-  }
-}
-
-__device__ __forceinline__ float finalize_rt(int obj, const Acc& s, const GenParams& p) {
-  switch (obj) {
-    case kAckley: return finalize_fitness<kAckley>(s, p);
-    case kGriewank: return finalize_fitness<kGriewank>(s, p);
-    default: return s.a;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // 1. plans
@@ -109,203 +92,237 @@ batch_plan_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restri
 // ---------------------------------------------------------------------------
 // 2. rows
 // ---------------------------------------------------------------------------
+struct BatchSmem {
+  float first[kBatchVmax][kBatchThreads / 32];
+  float red[4][kBatchThreads / 32];
+  int accept[kBatchThreads / 4];
+};
+
+// The rows of one tile, specialised for one objective and crossover. Kept
+// out of line so that each specialisation is its own compact code: the tile
+// list is grouped by (objective, crossover), so the SMs run one
+// specialisation at a time and it stays in the instruction cache.
+template <int OBJ, int XO>
+__device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, const RowPlan32* __restrict__ plans,
+                                        int eval_only, BatchSmem& sm) {
+  const GenParams& p = I.g;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int G = I.group;
+  const int gi = t / G, gl = t - gi * G;          // row within the tile, lane within the row's group
+  const int i = tl.row0 + gi;
+  const bool active = i < p.N;
+  const long long gen = p.st->gen;
+  const uint32_t g = (uint32_t)gen;
+  const int D = p.D, D4 = p.D4;
+  const float F = p.F, lo = p.lo, hi = p.hi;
+
+  RowPlan32 pl{};
+  if (active) {
+    if (eval_only) pl.slots = p.slots[(size_t)(gen & 1) * p.N + i];
+    else pl = plans[I.row_base + i];
+  }
+  const int si = (int)(pl.slots & 0xFFu);
+  const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)(active ? i : 0) * p.pitch);
+  const float4* d1 = reinterpret_cast<const float4*>(((pl.slots >> 8) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch);
+  const float4* d2 = reinterpret_cast<const float4*>(((pl.slots >> 16) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r2 * p.pitch);
+  const float4* d3 = reinterpret_cast<const float4*>(((pl.slots >> 24) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r3 * p.pitch);
+
+  // parent row and the donor genes of masked slots, all loads in flight together
+  float4 x[kBatchVmax];
+  unsigned mk[kBatchVmax];
+#pragma unroll
+  for (int k = 0; k < kBatchVmax; ++k) {
+    const int q = gl + k * G;
+    const bool in = active && q < D4;
+    x[k] = in ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    unsigned m = 0u;
+    if (in && !eval_only) {
+      const int j0 = 4 * q;
+      if constexpr (XO == kBin) {
+        const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
+        m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == pl.jrand) ? 1u : 0u;
+        m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == pl.jrand) ? 2u : 0u;
+        m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == pl.jrand) ? 4u : 0u;
+        m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == pl.jrand) ? 8u : 0u;
+      } else {
+        int dd = j0 - pl.jrand;
+        if (dd < 0) dd += D;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int de = dd + e;
+          if (de >= D) de -= D;
+          m |= (de < pl.L) ? (1u << e) : 0u;
+        }
+      }
+      m &= (1u << min(4, D - j0)) - 1u;
+    }
+    mk[k] = m;
+  }
+  int cnt = 0;
+#pragma unroll
+  for (int k = 0; k < kBatchVmax; ++k) {
+    if (mk[k]) {
+      const int q = gl + k * G;
+      const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
+      const unsigned m = mk[k];
+      if (m & 1u) x[k].x = clip_box(mutate(a1.x, a2.x, a3.x, F), lo, hi);
+      if (m & 2u) x[k].y = clip_box(mutate(a1.y, a2.y, a3.y, F), lo, hi);
+      if (m & 4u) x[k].z = clip_box(mutate(a1.z, a2.z, a3.z, F), lo, hi);
+      if (m & 8u) x[k].w = clip_box(mutate(a1.w, a2.w, a3.w, F), lo, hi);
+      cnt += __popc(m);
+    }
+  }
+
+  // fitness of the trial (or the parent), reduced over the group
+  Acc s{0.0f, 0.0f, 0.0f};
+  const int W = min(G, 32);                        // shuffle width
+  if constexpr (OBJ == kRosenbrock) {
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kBatchVmax; ++k) sm.first[k][warp] = x[k].x;
+    }
+    __syncthreads();
+    const int gw0 = (gi * G) >> 5;                 // first warp of this group (G >= 32)
+    const int gwn = (G + 31) >> 5;                 // warps per group
+#pragma unroll
+    for (int k = 0; k < kBatchVmax; ++k) {
+      float nb = __shfl_down_sync(0xFFFFFFFFu, x[k].x, 1, W);
+      const float next0 = __shfl_sync(0xFFFFFFFFu, (k + 1 < kBatchVmax) ? x[k + 1].x : 0.0f, 0, W);
+      if ((gl & (W - 1)) == W - 1) {
+        if (G <= 32) nb = next0;                   // group lane 0, next slot
+        else if (warp + 1 < gw0 + gwn) nb = sm.first[k][warp + 1];
+        else nb = (k + 1 < kBatchVmax) ? sm.first[k + 1][gw0] : 0.0f;
+      }
+      const int q = gl + k * G;
+      if (active && q < D4) {
+        const int j0 = 4 * q;
+        if (j0 + 1 < D) accum_pair(s, x[k].x, x[k].y);
+        if (j0 + 2 < D) accum_pair(s, x[k].y, x[k].z);
+        if (j0 + 3 < D) accum_pair(s, x[k].z, x[k].w);
+        if (j0 + 4 < D) accum_pair(s, x[k].w, nb);
+      }
+    }
+  } else {
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < kBatchVmax; ++k) {
+        const int q = gl + k * G;
+        if (q < D4) {
+          const int j0 = 4 * q;
+          accum_gene<OBJ>(s, x[k].x, j0, p);
+          if (j0 + 1 < D) accum_gene<OBJ>(s, x[k].y, j0 + 1, p);
+          if (j0 + 2 < D) accum_gene<OBJ>(s, x[k].z, j0 + 2, p);
+          if (j0 + 3 < D) accum_gene<OBJ>(s, x[k].w, j0 + 3, p);
+        }
+      }
+    }
+  }
+  constexpr int NS = ObjTraits<OBJ>::kSums;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (o < W) {
+      s.a += __shfl_xor_sync(0xFFFFFFFFu, s.a, o, W);
+      if (NS > 1) s.b += __shfl_xor_sync(0xFFFFFFFFu, s.b, o, W);
+      if (NS > 2) s.c += __shfl_xor_sync(0xFFFFFFFFu, s.c, o, W);
+      if (XO == kBin) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o, W);
+    }
+  }
+  if (G > 32) {
+    if (lane == 0) {
+      sm.red[0][warp] = s.a;
+      sm.red[1][warp] = s.b;
+      sm.red[2][warp] = s.c;
+      sm.red[3][warp] = __int_as_float(cnt);
+    }
+    __syncthreads();
+    if (gl == 0) {
+      const int gw0 = (gi * G) >> 5, gwn = G >> 5;
+      Acc r{0.0f, 0.0f, 0.0f};
+      int c = 0;
+      for (int w = 0; w < gwn; ++w) {
+        r.a += sm.red[0][gw0 + w];
+        r.b += sm.red[1][gw0 + w];
+        r.c += sm.red[2][gw0 + w];
+        c += __float_as_int(sm.red[3][gw0 + w]);
+      }
+      s = r;
+      cnt = c;
+    }
+  }
+
+  // decision by the group leader
+  if (active && gl == 0) {
+    float f = finalize_fitness<OBJ>(s, p);
+    if (f != f) f = __int_as_float(0x7F800000);
+    if (eval_only) {
+      p.fit[i] = f;
+      atomicMin(&p.st->best_key, best_key_of(f, i));
+      sm.accept[gi] = 0;
+    } else {
+      const int acc = (f < pl.fit_i) ? 1 : 0;
+      sm.accept[gi] = acc;
+      p.slots[(size_t)((gen + 1) & 1) * p.N + i] = (uint8_t)(acc ? 1 - si : si);
+      const int Lrow = (XO == kBin) ? cnt : pl.L;
+      if (acc) {
+        p.fit[i] = f;
+        atomicMin(&p.st->best_key, best_key_of(f, i));
+        atomicAdd(&p.st->accepts, 1ull);
+      }
+      atomicAdd(&p.st->masked, (unsigned long long)Lrow);
+      if (p.dbg_ftrial) p.dbg_ftrial[i] = f;
+      if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)acc;
+      if (p.dbg_draws) {
+        int* o = p.dbg_draws + 5 * (size_t)i;
+        o[0] = pl.r1; o[1] = pl.r2; o[2] = pl.r3; o[3] = pl.jrand; o[4] = Lrow;
+      }
+    }
+  }
+  __syncthreads();
+  if (active && !eval_only) {
+    if (sm.accept[gi]) {
+      float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
+#pragma unroll
+      for (int k = 0; k < kBatchVmax; ++k) {
+        const int q = gl + k * G;
+        if (q < D4) st_stream(out + q, x[k]);
+      }
+    }
+    if (p.dbg_trial) {
+      float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch);
+#pragma unroll
+      for (int k = 0; k < kBatchVmax; ++k) {
+        const int q = gl + k * G;
+        if (q < D4) o[q] = x[k];
+      }
+    }
+  }
+}
+
+template <int OBJ>
+__device__ __forceinline__ void batch_rows_xo(int xo, const BatchInst& I, const BatchTile tl,
+                                              const RowPlan32* plans, int eval_only, BatchSmem& sm) {
+  if (xo == kBin) batch_rows<OBJ, kBin>(I, tl, plans, eval_only, sm);
+  else if (xo == kExp) batch_rows<OBJ, kExp>(I, tl, plans, eval_only, sm);
+  else batch_rows<OBJ, kNec>(I, tl, plans, eval_only, sm);
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_gen_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                  const RowPlan32* __restrict__ plans, int eval_only) {
-  __shared__ float s_first[kBatchVmax][kBatchThreads / 32];
-  __shared__ float s_red[4][kBatchThreads / 32];
-  __shared__ int s_accept[kBatchThreads / 4];
-
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  __shared__ BatchSmem sm;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const BatchTile tl = tiles[tile];
     const BatchInst& I = insts[tl.inst];
-    const GenParams& p = I.g;
-    const int obj = I.obj, xo = I.xo, G = I.group;
-    const int gi = t / G, gl = t - gi * G;          // row within the tile, lane within the row's group
-    const int i = tl.row0 + gi;
-    const bool active = i < p.N;
-    const long long gen = p.st->gen;
-    const uint32_t g = (uint32_t)gen;
-
-    RowPlan32 pl{};
-    if (active) {
-      if (eval_only) pl.slots = p.slots[(size_t)(gen & 1) * p.N + i];
-      else pl = plans[I.row_base + i];
+    const int obj = I.obj, xo = I.xo;                // uniform over the CTA
+    switch (obj) {
+      case kSphere: batch_rows_xo<kSphere>(xo, I, tl, plans, eval_only, sm); break;
+      case kRastrigin: batch_rows_xo<kRastrigin>(xo, I, tl, plans, eval_only, sm); break;
+      case kAckley: batch_rows_xo<kAckley>(xo, I, tl, plans, eval_only, sm); break;
+      case kRosenbrock: batch_rows_xo<kRosenbrock>(xo, I, tl, plans, eval_only, sm); break;
+      case kGriewank: batch_rows_xo<kGriewank>(xo, I, tl, plans, eval_only, sm); break;
+      default: batch_rows_xo<kElliptic>(xo, I, tl, plans, eval_only, sm); break;
     }
-    const int si = (int)(pl.slots & 0xFFu);
-    const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)(active ? i : 0) * p.pitch);
-    const float4* d1 = reinterpret_cast<const float4*>(((pl.slots >> 8) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch);
-    const float4* d2 = reinterpret_cast<const float4*>(((pl.slots >> 16) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r2 * p.pitch);
-    const float4* d3 = reinterpret_cast<const float4*>(((pl.slots >> 24) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r3 * p.pitch);
-
-    // parent row and the donor genes of masked slots, all loads in flight together
-    float4 x[kBatchVmax];
-    unsigned mk[kBatchVmax];
-#pragma unroll
-    for (int k = 0; k < kBatchVmax; ++k) {
-      const int q = gl + k * G;
-      const bool in = active && q < p.D4;
-      x[k] = in ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      unsigned m = 0u;
-      if (in && !eval_only) {
-        const int j0 = 4 * q;
-        if (xo == kBin) {
-          const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
-          m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == pl.jrand) ? 1u : 0u;
-          m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == pl.jrand) ? 2u : 0u;
-          m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == pl.jrand) ? 4u : 0u;
-          m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == pl.jrand) ? 8u : 0u;
-        } else {
-          int dd = j0 - pl.jrand;
-          if (dd < 0) dd += p.D;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            int de = dd + e;
-            if (de >= p.D) de -= p.D;
-            m |= (de < pl.L) ? (1u << e) : 0u;
-          }
-        }
-        m &= (1u << min(4, p.D - j0)) - 1u;
-      }
-      mk[k] = m;
-    }
-    int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < kBatchVmax; ++k) {
-      if (mk[k]) {
-        const int q = gl + k * G;
-        const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
-        const unsigned m = mk[k];
-        if (m & 1u) x[k].x = clip_box(mutate(a1.x, a2.x, a3.x, p.F), p.lo, p.hi);
-        if (m & 2u) x[k].y = clip_box(mutate(a1.y, a2.y, a3.y, p.F), p.lo, p.hi);
-        if (m & 4u) x[k].z = clip_box(mutate(a1.z, a2.z, a3.z, p.F), p.lo, p.hi);
-        if (m & 8u) x[k].w = clip_box(mutate(a1.w, a2.w, a3.w, p.F), p.lo, p.hi);
-        cnt += __popc(m);
-      }
-    }
-
-    // fitness of the trial (or the parent), reduced over the group
-    Acc s{0.0f, 0.0f, 0.0f};
-    const int W = min(G, 32);                        // shuffle width
-    if (obj == kRosenbrock) {
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < kBatchVmax; ++k) s_first[k][warp] = x[k].x;
-      }
-      __syncthreads();
-      const int gw0 = (gi * G) >> 5;                 // first warp of this group (G >= 32)
-      const int gwn = (G + 31) >> 5;                 // warps per group
-#pragma unroll
-      for (int k = 0; k < kBatchVmax; ++k) {
-        float nb = __shfl_down_sync(0xFFFFFFFFu, x[k].x, 1, W);
-        const float next0 = __shfl_sync(0xFFFFFFFFu, (k + 1 < kBatchVmax) ? x[k + 1].x : 0.0f, 0, W);
-        if ((gl & (W - 1)) == W - 1) {
-          if (G <= 32) nb = next0;                   // group lane 0, next slot
-          else if (warp + 1 < gw0 + gwn) nb = s_first[k][warp + 1];
-          else nb = (k + 1 < kBatchVmax) ? s_first[k + 1][gw0] : 0.0f;
-        }
-        const int q = gl + k * G;
-        if (active && q < p.D4) {
-          const int j0 = 4 * q;
-          if (j0 + 1 < p.D) accum_pair(s, x[k].x, x[k].y);
-          if (j0 + 2 < p.D) accum_pair(s, x[k].y, x[k].z);
-          if (j0 + 3 < p.D) accum_pair(s, x[k].z, x[k].w);
-          if (j0 + 4 < p.D) accum_pair(s, x[k].w, nb);
-        }
-      }
-    } else if (active) {
-#pragma unroll
-      for (int k = 0; k < kBatchVmax; ++k) {
-        const int q = gl + k * G;
-        if (q < p.D4) {
-          const int j0 = 4 * q;
-          accum_gene_rt(obj, s, x[k].x, j0, p);
-          if (j0 + 1 < p.D) accum_gene_rt(obj, s, x[k].y, j0 + 1, p);
-          if (j0 + 2 < p.D) accum_gene_rt(obj, s, x[k].z, j0 + 2, p);
-          if (j0 + 3 < p.D) accum_gene_rt(obj, s, x[k].w, j0 + 3, p);
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (o < W) {
-        s.a += __shfl_xor_sync(0xFFFFFFFFu, s.a, o, W);
-        s.b += __shfl_xor_sync(0xFFFFFFFFu, s.b, o, W);
-        s.c += __shfl_xor_sync(0xFFFFFFFFu, s.c, o, W);
-        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o, W);
-      }
-    }
-    if (G > 32) {
-      if (lane == 0) {
-        s_red[0][warp] = s.a;
-        s_red[1][warp] = s.b;
-        s_red[2][warp] = s.c;
-        s_red[3][warp] = __int_as_float(cnt);
-      }
-      __syncthreads();
-      if (gl == 0) {
-        const int gw0 = (gi * G) >> 5, gwn = G >> 5;
-        Acc r{0.0f, 0.0f, 0.0f};
-        int c = 0;
-        for (int w = 0; w < gwn; ++w) {
-          r.a += s_red[0][gw0 + w];
-          r.b += s_red[1][gw0 + w];
-          r.c += s_red[2][gw0 + w];
-          c += __float_as_int(s_red[3][gw0 + w]);
-        }
-        s = r;
-        cnt = c;
-      }
-    }
-
-    // decision by the group leader
-    if (active && gl == 0) {
-      float f = finalize_rt(obj, s, p);
-      if (f != f) f = __int_as_float(0x7F800000);
-      if (eval_only) {
-        p.fit[i] = f;
-        atomicMin(&p.st->best_key, best_key_of(f, i));
-        s_accept[gi] = 0;
-      } else {
-        const int acc = (f < pl.fit_i) ? 1 : 0;
-        s_accept[gi] = acc;
-        p.slots[(size_t)((gen + 1) & 1) * p.N + i] = (uint8_t)(acc ? 1 - si : si);
-        const int Lrow = (xo == kBin) ? cnt : pl.L;
-        if (acc) {
-          p.fit[i] = f;
-          atomicMin(&p.st->best_key, best_key_of(f, i));
-          atomicAdd(&p.st->accepts, 1ull);
-        }
-        atomicAdd(&p.st->masked, (unsigned long long)Lrow);
-        if (p.dbg_ftrial) p.dbg_ftrial[i] = f;
-        if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)acc;
-        if (p.dbg_draws) {
-          int* o = p.dbg_draws + 5 * (size_t)i;
-          o[0] = pl.r1; o[1] = pl.r2; o[2] = pl.r3; o[3] = pl.jrand; o[4] = Lrow;
-        }
-      }
-    }
-    __syncthreads();
-    if (active && !eval_only) {
-      if (s_accept[gi]) {
-        float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
-#pragma unroll
-        for (int k = 0; k < kBatchVmax; ++k) {
-          const int q = gl + k * G;
-          if (q < p.D4) st_stream(out + q, x[k]);
-        }
-      }
-      if (p.dbg_trial) {
-        float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch);
-#pragma unroll
-        for (int k = 0; k < kBatchVmax; ++k) {
-          const int q = gl + k * G;
-          if (q < p.D4) o[q] = x[k];
-        }
-      }
-    }
-    __syncthreads();                                 // s_accept / s_first / s_red reused by the next tile
+    __syncthreads();                                 // shared scratch reused by the next tile
   }
 }
 
