@@ -28,7 +28,7 @@
 namespace de {
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchVmax = 16;
+constexpr int kBatchVmax = 8;
 constexpr int kBatchTableCap = 4096;
 
 // ---------------------------------------------------------------------------
@@ -177,11 +177,13 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   Acc s{0.0f, 0.0f, 0.0f};
   const int W = min(G, 32);                        // shuffle width
   if constexpr (OBJ == kRosenbrock) {
-    if (lane == 0) {
+    if (G > 32) {                                  // neighbours across warps go through shared memory
+      if (lane == 0) {
 #pragma unroll
-      for (int k = 0; k < kBatchVmax; ++k) sm.first[k][warp] = x[k].x;
+        for (int k = 0; k < kBatchVmax; ++k) sm.first[k][warp] = x[k].x;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const int gw0 = (gi * G) >> 5;                 // first warp of this group (G >= 32)
     const int gwn = (G + 31) >> 5;                 // warps per group
 #pragma unroll
@@ -250,17 +252,18 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     }
   }
 
-  // decision by the group leader
+  // decision by the group leader; a group of G <= 32 lies inside one warp and
+  // learns it by a shuffle, larger groups through shared memory
+  int acc = 0;
   if (active && gl == 0) {
     float f = finalize_fitness<OBJ>(s, p);
     if (f != f) f = __int_as_float(0x7F800000);
     if (eval_only) {
       p.fit[i] = f;
       atomicMin(&p.st->best_key, best_key_of(f, i));
-      sm.accept[gi] = 0;
     } else {
-      const int acc = (f < pl.fit_i) ? 1 : 0;
-      sm.accept[gi] = acc;
+      acc = (f < pl.fit_i) ? 1 : 0;
+      if (G > 32) sm.accept[gi] = acc;
       p.slots[(size_t)((gen + 1) & 1) * p.N + i] = (uint8_t)(acc ? 1 - si : si);
       const int Lrow = (XO == kBin) ? cnt : pl.L;
       if (acc) {
@@ -277,9 +280,14 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
       }
     }
   }
-  __syncthreads();
+  if (G > 32) {
+    __syncthreads();
+    acc = sm.accept[gi];
+  } else {
+    acc = __shfl_sync(0xFFFFFFFFu, acc, 0, W);
+  }
   if (active && !eval_only) {
-    if (sm.accept[gi]) {
+    if (acc) {
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
@@ -306,7 +314,7 @@ __device__ __forceinline__ void batch_rows_xo(int xo, const BatchInst& I, const 
   else batch_rows<OBJ, kNec>(I, tl, plans, eval_only, sm);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(kBatchThreads, 3)
 batch_gen_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                  const RowPlan32* __restrict__ plans, int eval_only) {
   __shared__ BatchSmem sm;
@@ -322,7 +330,10 @@ batch_gen_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restric
       case kGriewank: batch_rows_xo<kGriewank>(xo, I, tl, plans, eval_only, sm); break;
       default: batch_rows_xo<kElliptic>(xo, I, tl, plans, eval_only, sm); break;
     }
-    __syncthreads();                                 // shared scratch reused by the next tile
+    // Only tiles with groups wider than a warp use shared memory (and CTA
+    // barriers); such a tile ends with a barrier before the scratch is reused.
+    // G is uniform over the CTA, so every thread meets the same barriers.
+    if (I.group > 32) __syncthreads();
   }
 }
 
