@@ -206,7 +206,7 @@ typedef struct {
  * kernel launch: the instances are cut into tiles of 256 / G rows with G
  * threads per row (G set per instance, see de_batch_set_groups) and the
  * tiles are walked in longest-first order. Per-instance limits as de_create
- * with D <= 8192 and non-rotated objectives (Ackley constant 0.2). The
+ * with D <= 16384 and non-rotated objectives (Ackley constant 0.2). The
  * initial populations are drawn and evaluated before the call returns.
  * Single-population calls (de_best, de_get_population, de_set_population,
  * de_debug_step, de_set_kernel, ...) return DE_ESTATE on a batch; de_save
@@ -236,7 +236,7 @@ int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftri
                         uint8_t *accept_out, int32_t *draws_out);
 
 /* Tile shape per instance: threads per row G (a power of two, 4..256, with
- * ceil(ceil(D/4) / G) <= 8; 0 = the default, the smallest such G). Tuning
+ * ceil(ceil(D/4) / G) <= 16; 0 = the default, the smallest such G). Tuning
  * only: draws are unchanged, FP32 fitness rounding may change. */
 int de_batch_set_groups(de_ctx *ctx, const int32_t *groups);
 int de_batch_get_groups(de_ctx *ctx, int32_t *groups);

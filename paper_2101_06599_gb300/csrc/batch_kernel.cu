@@ -28,7 +28,7 @@
 namespace de {
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchVmax = 8;
+constexpr int kBatchVmax = 16;
 constexpr int kBatchTableCap = 4096;
 
 // ---------------------------------------------------------------------------
@@ -314,7 +314,7 @@ __device__ __forceinline__ void batch_rows_xo(int xo, const BatchInst& I, const 
   else batch_rows<OBJ, kNec>(I, tl, plans, eval_only, sm);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 3)
+__global__ void __launch_bounds__(kBatchThreads, 2)
 batch_gen_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                  const RowPlan32* __restrict__ plans, int eval_only) {
   __shared__ BatchSmem sm;

@@ -56,7 +56,7 @@ struct RowPlan32 {
 };
 constexpr int kBatchThreadsHost = 256;
 constexpr int kBatchMaxGroup = 256;
-constexpr int kBatchMaxD4PerLane = 8;
+constexpr int kBatchMaxD4PerLane = 16;
 // plan kernel + row kernel + close kernel (one generation of every instance)
 cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* tiles, int ntiles,
                                     const BatchTile* ptiles, int nptiles, RowPlan32* plans, DevState* states,
