@@ -177,13 +177,11 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   Acc s{0.0f, 0.0f, 0.0f};
   const int W = min(G, 32);                        // shuffle width
   if constexpr (OBJ == kRosenbrock) {
-    if (G > 32) {                                  // neighbours across warps go through shared memory
-      if (lane == 0) {
+    if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < kBatchVmax; ++k) sm.first[k][warp] = x[k].x;
-      }
-      __syncthreads();
+      for (int k = 0; k < kBatchVmax; ++k) sm.first[k][warp] = x[k].x;
     }
+    __syncthreads();
     const int gw0 = (gi * G) >> 5;                 // first warp of this group (G >= 32)
     const int gwn = (G + 31) >> 5;                 // warps per group
 #pragma unroll
@@ -252,18 +250,17 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     }
   }
 
-  // decision by the group leader; a group of G <= 32 lies inside one warp and
-  // learns it by a shuffle, larger groups through shared memory
-  int acc = 0;
+  // decision by the group leader
   if (active && gl == 0) {
     float f = finalize_fitness<OBJ>(s, p);
     if (f != f) f = __int_as_float(0x7F800000);
     if (eval_only) {
       p.fit[i] = f;
       atomicMin(&p.st->best_key, best_key_of(f, i));
+      sm.accept[gi] = 0;
     } else {
-      acc = (f < pl.fit_i) ? 1 : 0;
-      if (G > 32) sm.accept[gi] = acc;
+      const int acc = (f < pl.fit_i) ? 1 : 0;
+      sm.accept[gi] = acc;
       p.slots[(size_t)((gen + 1) & 1) * p.N + i] = (uint8_t)(acc ? 1 - si : si);
       const int Lrow = (XO == kBin) ? cnt : pl.L;
       if (acc) {
@@ -280,14 +277,9 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
       }
     }
   }
-  if (G > 32) {
-    __syncthreads();
-    acc = sm.accept[gi];
-  } else {
-    acc = __shfl_sync(0xFFFFFFFFu, acc, 0, W);
-  }
+  __syncthreads();
   if (active && !eval_only) {
-    if (acc) {
+    if (sm.accept[gi]) {
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
@@ -330,10 +322,7 @@ batch_gen_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restric
       case kGriewank: batch_rows_xo<kGriewank>(xo, I, tl, plans, eval_only, sm); break;
       default: batch_rows_xo<kElliptic>(xo, I, tl, plans, eval_only, sm); break;
     }
-    // Only tiles with groups wider than a warp use shared memory (and CTA
-    // barriers); such a tile ends with a barrier before the scratch is reused.
-    // G is uniform over the CTA, so every thread meets the same barriers.
-    if (I.group > 32) __syncthreads();
+    __syncthreads();                                 // shared scratch reused by the next tile
   }
 }
 
