@@ -185,6 +185,45 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         raise
 
 
+def time_batched(DE, torch, steps, warmup, seed, peak):
+    """The 512-instance workload (D log-uniform in [10, 2000], N = min(10 D,
+    4096), sphere/Rastrigin/Ackley/Rosenbrock round-robin, NEC, F = 0.5,
+    Cr = 0.9), one generation of every instance per step."""
+    from paper_2101_06599_gb300 import workloads as Wk
+    specs = [dict(N=s.N, D=s.D, obj=s.objective, bounds=Wk.BOXES[s.objective], xo="nec", CR=CR_DEF, F=F_DEF)
+             for s in Wk.batched_specs()]
+    units = float(sum(s["N"] * s["D"] for s in specs))
+    rows = float(sum(s["N"] for s in specs))
+    b = DE.Batch(specs, seed=seed + 4)
+    try:
+        b.run(warmup)
+        b.synchronize()
+        st0 = b.stats()
+        acc0 = [b.stats(k)["accepts"] for k in range(len(specs))]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(b.stream)
+        b.run(steps)
+        ev1.record(b.stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st1 = b.stats()
+        acc_genes = sum((b.stats(k)["accepts"] - acc0[k]) * specs[k]["D"] for k in range(len(specs)))
+    finally:
+        b.close()
+    d_acc = st1["accepts"] - st0["accepts"]
+    d_msk = st1["masked_genes"] - st0["masked_genes"]
+    # parent rows, donor genes of masked genes, accepted rows, per-row plans (written
+    # and read, 32 bytes each), fitness and slot bytes
+    byts = (4.0 * units * steps + 12.0 * d_msk + 4.0 * acc_genes + 64.0 * rows * steps
+            + 6.0 * rows * steps + 4.0 * d_acc)
+    gbs = byts / (ms / 1e3) / 1e9
+    return {"workload": "batched_512_instances", "instances": len(specs), "ind_dims_per_step": units,
+            "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_gen": ms / steps,
+            "hbm_gbs": gbs, "frac": gbs / peak, "launches_per_step": 3,
+            "a_acceptance": d_acc / (rows * steps), "m_masked_fraction": d_msk / (units * steps)}
+
+
 _dist = None
 
 
@@ -275,6 +314,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
     ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
     args = ap.parse_args()
@@ -350,6 +390,10 @@ def main():
                     "value": units / (ms2 / 1e3), "ms_per_gen": ms2 / K, "hbm_gbs": ach2, "frac": ach2 / peak,
                     "m": m2 / (N * D * K), "a": a2 / (N * K), "kernel": sh2}
 
+    batched = None
+    if not args.no_batched:
+        batched = time_batched(DE, torch, K, W, seed, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, timed, secs = oracle_generation_rate(N, D, "rosenbrock", "nec", 12.0)
@@ -367,7 +411,7 @@ def main():
                        "F": F_DEF, "CR": CR_DEF, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (two 0.66 GB population buffers), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
-            "clocks": clk.summary(), "variants": variants,
+            "clocks": clk.summary(), "variants": variants, "batched": batched,
         }
         print(json.dumps(line))
     if _dist is not None:
