@@ -103,6 +103,9 @@ typedef struct {
   int64_t best_gen;         /* generation at which the best value last strictly improved  */
   double best_f;            /* best fitness (FP32 value, widened)                          */
   int32_t best_index;       /* row holding it; lowest index on ties                       */
+  double incumbent_f64;     /* shifted-rotated: the best row's objective recomputed in FP64
+                               every incumbent_every generations (NaN otherwise)           */
+  int64_t incumbent_gen;    /* generation of that re-evaluation (-1 = none)                */
 } de_stats_t;
 
 typedef struct de_ctx de_ctx;

@@ -109,7 +109,7 @@ bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de
 // requested count.
 void configure_pipe(de_ctx* c) {
   c->pipe_ok = false;
-  if (c->xo == DE_XOVER_BIN || c->sm_count <= 0 || c->smem_optin <= 0) return;
+  if (c->xo == DE_XOVER_BIN || c->rotated || c->sm_count <= 0 || c->smem_optin <= 0) return;
   const int row_floats = 4 * c->D4;
   int need = 16;
   if (c->CR >= 1.0) need = c->D + 8;
@@ -155,6 +155,7 @@ void resolve_kernel(de_ctx* c) {
 
 cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
   if (c->batch) return batch_launch_generation(c, false, -1);
+  if (c->rotated) return sr_launch_generation(c, p);
   if (c->use_pipe) {
     PipeParams pp = c->pp;
     pp.g = p;
@@ -168,6 +169,7 @@ cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
 }
 
 int evaluate_population(de_ctx* c) {
+  if (c->rotated) return sr_evaluate(c);
   cudaError_t e = launch_reset_best(c->p, c->stream);
   if (e == cudaSuccess) e = launch_eval(c->obj, c->vidx, c->p, c->block, c->stream);
   if (e == cudaSuccess) e = launch_close_eval(c->p, c->stream);
@@ -238,7 +240,8 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   if (!valid_problem(N, D, F, CR, (int)xo, (int)obj, b)) return DE_EINVAL;
   if (is_rotated(obj)) {
     if (!prm || !prm->shift || !prm->rotation) return DE_EINVAL;
-    return DE_EUNSUPPORTED;
+    if (prm->prec != DE_PREC_FP32 && prm->prec != DE_PREC_BF16) return DE_EUNSUPPORTED;
+    if (prm->prec == DE_PREC_BF16 && !sr_tc_supported(D)) return DE_EUNSUPPORTED;
   }
   double ackley_b = 0.2;
   if (prm && prm->ackley_b != 0.0) {
@@ -305,6 +308,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   p.ackley_b = (float)ackley_b;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
 
+  c->rotated = is_rotated(obj);
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) {
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -319,6 +323,13 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   std::memset(&s0, 0, sizeof(s0));
   s0.best_key = ~0ULL;
   s0.best_f = INFINITY;
+  s0.incumbent_gen = -1;
+  int src = DE_OK;
+  if (is_rotated(obj)) src = sr_setup(c, prm);
+  if (src != DE_OK) {
+    de_destroy(c);
+    return src;
+  }
   cudaError_t e = cudaMemsetAsync(pop0, 0, pop_bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(pop1, 0, pop_bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, 2 * (size_t)N, c->stream);
@@ -432,6 +443,8 @@ int de_stats(de_ctx* c, de_stats_t* out) {
   out->best_gen = s.best_gen;
   out->best_f = (double)s.best_f;
   out->best_index = (int32_t)(uint32_t)(s.best_key & 0xFFFFFFFFull);
+  out->incumbent_f64 = c->rotated ? s.incumbent_f64 : NAN;
+  out->incumbent_gen = c->rotated ? s.incumbent_gen : -1;
   return DE_OK;
 }
 
@@ -460,6 +473,8 @@ int de_set_population(de_ctx* c, const float* pop, const float* fit) {
   int rc;
   if (fit) {
     e = cudaMemcpyAsync(c->p.fit, fit, (size_t)c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->rotated)
+      e = cudaMemsetAsync(c->sp.fit_err, 0, (size_t)c->N * sizeof(float), c->stream);
     if (e == cudaSuccess) e = launch_reset_best(c->p, c->stream);
     if (e == cudaSuccess) e = launch_best_from_fit(c->p, c->stream);
     if (e == cudaSuccess) e = launch_close_eval(c->p, c->stream);
@@ -537,6 +552,8 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->p.fit, in + sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float),
                         (size_t)c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && c->rotated)
+    e = cudaMemsetAsync(c->sp.fit_err, 0, (size_t)c->N * sizeof(float), c->stream);
   if (e != cudaSuccess) return DE_ECUDA;
   const int rc = sync_stream(c);
   if (rc == DE_OK) c->host_gen = s.gen;

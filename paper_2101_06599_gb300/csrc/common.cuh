@@ -43,6 +43,8 @@ struct DevState {
   unsigned int error;            // sticky device error code (0 = none)
   float best_f;                  // best fitness at the end of the last generation
   float pad_[3];
+  double incumbent_f64;          // shifted-rotated: FP64 objective of the best row
+  long long incumbent_gen;       // generation of that re-evaluation (-1 = none)
 };
 
 struct GenParams {

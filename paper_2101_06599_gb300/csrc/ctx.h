@@ -8,6 +8,7 @@
 #include "../../include/de.h"
 #include "gen_pipe.cuh"
 #include "internal.h"
+#include "sr_common.cuh"
 
 using namespace de;
 
@@ -64,6 +65,12 @@ struct de_ctx {
   std::vector<long long> brow_base;
   de::DevState* d_states = nullptr;
   int ntiles = 0, batch_grid = 0, max_pitch = 0;
+  // shifted-rotated objectives (sr_api.cu)
+  bool rotated = false;
+  de::SrParams sp{};
+  de::SrBound sbound{};
+  int incumbent_every = 50;
+  int tc_ok = 0;                     // tcgen05 product available for this D
 };
 
 
@@ -83,4 +90,8 @@ bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de
 // Batched contexts (batch_api.cu).
 cudaError_t batch_launch_generation(de_ctx* c, bool with_debug_of_inst, int inst);
 int batch_stats(de_ctx* c, de_stats_t* out);
+// Shifted-rotated objectives (sr_api.cu).
+int sr_setup(de_ctx* c, const de_objparams* prm);
+cudaError_t sr_launch_generation(de_ctx* c, const GenParams& p);
+int sr_evaluate(de_ctx* c);
 }  // namespace de_host

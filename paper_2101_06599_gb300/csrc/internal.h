@@ -66,6 +66,23 @@ cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* til
 cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* tiles, int ntiles, DevState* states,
                                   int first_inst, int n_inst, int grid, cudaStream_t s);
 
+// Shifted-rotated objectives (sr_kernels.cu, sr_tc.cu); SrParams and
+// SrBound in sr_common.cuh.
+struct SrParams;
+struct SrBound;
+cudaError_t launch_sr_trial(int xo, int vidx, const SrParams& sp, int block, cudaStream_t s);
+cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s);
+cudaError_t launch_sr_select(const SrParams& sp, const SrBound& b, cudaStream_t s);
+cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s);
+cudaError_t launch_sr_close(const SrParams& sp, cudaStream_t s);
+cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s);
+cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, cudaStream_t s);
+cudaError_t launch_sr_incumbent(const SrParams& sp, int every, cudaStream_t s);
+// tcgen05 BF16 product (split operands) with the fitness epilogue; requires
+// D % 256 == 0. sr_tc_supported tells whether this build and device have it.
+cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s);
+bool sr_tc_supported(int D);
+
 constexpr size_t kStagingHeader = 32;
 
 }  // namespace de

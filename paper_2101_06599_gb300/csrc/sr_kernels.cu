@@ -1,0 +1,467 @@
+// sr_kernels.cu — generation of the shifted-rotated objectives.
+//
+// One generation = sr_trial_kernel (draws, crossover, mutation, clipping as
+// in the separable path; the trial row is written to the row's other slot
+// buffer, so acceptance is a slot flip; a = u - o and |a|^2, and for the BF16
+// path the split operands bf16(a), bf16(a - bf16(a))), then the product
+// Z = A R^T with a fused g(z) epilogue (this file: FP32 SIMT; sr_tc.cu:
+// tcgen05), then sr_select_kernel (strict '<' decisions, or interval
+// decisions with a per-row error bound on the BF16 path: rows whose interval
+// straddles the parent's go to an FP32 re-evaluation with this file's GEMM
+// and sr_resolve_kernel), then sr_close_kernel.
+//
+// The FP32 GEMM accumulates every z_ik in one fixed order (j ascending, one
+// FMA per term, one thread per element) and reduces g(z) over each 64-column
+// tile in one fixed order, so a row's value does not depend on which other
+// rows share its tile: re-evaluating a row reproduces the FP32 path bit for
+// bit.
+#include "draws.cuh"
+#include "gen_kernel.cuh"
+#include "internal.h"
+#include "sr_common.cuh"
+
+#include <cuda_bf16.h>
+
+namespace de {
+
+// ---------------------------------------------------------------------------
+// trials
+// ---------------------------------------------------------------------------
+template <int XO, int V>
+__global__ void __launch_bounds__(kMaxThreads) sr_trial_kernel(const __grid_constant__ SrParams sp) {
+  const GenParams& p = sp.g;
+  __shared__ RowShared sh;
+  __shared__ float red[4][32];
+  const int i = blockIdx.x;
+  const int t = threadIdx.x, T = blockDim.x;
+  const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
+  const long long gen = p.st->gen;
+  const uint32_t g = (uint32_t)gen;
+  const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
+  const int si = slot_in[i];
+  const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)i * p.pitch);
+
+  float4 x[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const int q = t + k * T;
+    x[k] = (q < p.D4) ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  if (t == 0) {
+    RowDraws d;
+    draw_donors(p, g, i, d);
+    if constexpr (XO == kNec) d.L = nec_length(p, g, i);
+    else if constexpr (XO == kExp) d.L = exp_walk_length(p, g, i);
+    else d.L = 0;
+    sh.r1 = d.r1; sh.r2 = d.r2; sh.r3 = d.r3; sh.jrand = d.jrand; sh.L = d.L;
+    sh.d1 = reinterpret_cast<const float4*>((slot_in[d.r1] ? p.pop1 : p.pop0) + (size_t)d.r1 * p.pitch);
+    sh.d2 = reinterpret_cast<const float4*>((slot_in[d.r2] ? p.pop1 : p.pop0) + (size_t)d.r2 * p.pitch);
+    sh.d3 = reinterpret_cast<const float4*>((slot_in[d.r3] ? p.pop1 : p.pop0) + (size_t)d.r3 * p.pitch);
+  }
+  __syncthreads();
+  const int jrand = sh.jrand, L = sh.L;
+  int cnt = 0;
+  float nrm = 0.0f;
+  float4* trow = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const int q = t + k * T;
+    if (q < p.D4) {
+      const int j0 = 4 * q;
+      unsigned m = 0u;
+      if constexpr (XO == kBin) {
+        const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
+        m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == jrand) ? 1u : 0u;
+        m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == jrand) ? 2u : 0u;
+        m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == jrand) ? 4u : 0u;
+        m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == jrand) ? 8u : 0u;
+      } else {
+        int dd = j0 - jrand;
+        if (dd < 0) dd += p.D;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int de = dd + e;
+          if (de >= p.D) de -= p.D;
+          m |= (de < L) ? (1u << e) : 0u;
+        }
+      }
+      m &= (1u << min(4, p.D - j0)) - 1u;
+      if (m) {
+        const float4 a1 = ld_ro(sh.d1 + q), a2 = ld_ro(sh.d2 + q), a3 = ld_ro(sh.d3 + q);
+        if (m & 1u) x[k].x = clip_box(mutate(a1.x, a2.x, a3.x, p.F), p.lo, p.hi);
+        if (m & 2u) x[k].y = clip_box(mutate(a1.y, a2.y, a3.y, p.F), p.lo, p.hi);
+        if (m & 4u) x[k].z = clip_box(mutate(a1.z, a2.z, a3.z, p.F), p.lo, p.hi);
+        if (m & 8u) x[k].w = clip_box(mutate(a1.w, a2.w, a3.w, p.F), p.lo, p.hi);
+      }
+      if constexpr (XO == kBin) cnt += __popc(m);
+      st_stream(trow + q, x[k]);
+      if (p.dbg_trial) reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch)[q] = x[k];
+      // a = u - o, its norm, and the split BF16 operands
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = j0 + e;
+        if (j < p.D) {
+          const float a = __fsub_rn(lane_of(x[k], e), sp.shift[j]);
+          nrm = fmaf(a, a, nrm);
+          if (sp.prec != 0) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(a);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(hi)));
+            sp.a_hi[(size_t)i * p.D + j] = __bfloat16_as_ushort(hi);
+            sp.a_lo[(size_t)i * p.D + j] = __bfloat16_as_ushort(lo);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, o);
+    cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = nrm;
+    red[1][warp] = __int_as_float(cnt);
+  }
+  __syncthreads();
+  if (t == 0) {
+    float n2 = 0.0f;
+    int c = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      n2 += red[0][w];
+      c += __float_as_int(red[1][w]);
+    }
+    sp.norm2[i] = n2;
+    const int Lrow = (XO == kBin) ? c : L;
+    atomicAdd(&p.st->masked, (unsigned long long)Lrow);
+    if (p.dbg_draws) {
+      int* o = p.dbg_draws + 5 * (size_t)i;
+      o[0] = sh.r1; o[1] = sh.r2; o[2] = sh.r3; o[3] = sh.jrand; o[4] = Lrow;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 product with the fitness epilogue
+// mode 0: all rows, trial rows (other slot); 1: all rows, parent rows;
+// 2: the ambiguous entries (row << 1 | parent flag), partials to part2_*.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sr_gemm_fp32_kernel(const __grid_constant__ SrParams sp, int mode) {
+  const GenParams& p = sp.g;
+  __shared__ __align__(16) float As[kSrKStep][kSrTile + 4];
+  __shared__ __align__(16) float Bs[kSrKStep][kSrTile + 4];
+  __shared__ const float* rowp[kSrTile];
+
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int n0 = blockIdx.x * kSrTile;            // output column tile
+  const int r0 = blockIdx.y * kSrTile;            // row tile (rows or entries)
+  const long long gen = p.st->gen;
+  const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
+  const int nrows = (mode == 2) ? (int)*sp.amb_count : p.N;
+  if (r0 >= nrows) return;
+
+  if (t < kSrTile) {
+    const int e = r0 + t;
+    const float* rp = nullptr;
+    if (e < nrows) {
+      int r = e, parent = (mode == 1);
+      if (mode == 2) {
+        r = sp.amb[e] >> 1;
+        parent = sp.amb[e] & 1;
+      }
+      const int s = slot_in[r];
+      const int buf = parent ? s : 1 - s;
+      rp = (buf ? p.pop1 : p.pop0) + (size_t)r * p.pitch;
+    }
+    rowp[t] = rp;
+  }
+  __syncthreads();
+
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+
+  const int lr = t >> 2, lc = (t & 3) * 8;        // loader: row lr, 8 consecutive k from lc
+  for (int k0 = 0; k0 < p.D; k0 += kSrKStep) {
+    {
+      const float* rp = rowp[lr];
+      float va[8], vb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = k0 + lc + u;
+        va[u] = (rp && j < p.D) ? __fsub_rn(rp[j], sp.shift[j]) : 0.0f;
+        const int n = n0 + lr;
+        vb[u] = (n < p.D && j < p.D) ? sp.rot[(size_t)n * p.D + j] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        As[lc + u][lr] = va[u];
+        Bs[lc + u][lr] = vb[u];
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kSrKStep; ++kk) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float ar[4] = {av.x, av.y, av.z, av.w};
+      const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+
+  // epilogue: g(z) and w|z| over this thread's 4 columns, then over the tile's 64
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float sg = 0.0f, sw = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int n = n0 + tx * 4 + b;
+      if (n < p.D) {
+        const float w = sr_weight(sp.obj, n, p.ell_k);
+        sg += sr_g(sp.obj, acc[a][b], w);
+        sw = fmaf(w, fabsf(acc[a][b]), sw);
+      }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      sg += __shfl_xor_sync(0xFFFFFFFFu, sg, o);
+      sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+    }
+    const int e = r0 + ty * 4 + a;
+    if (tx == 0 && e < nrows) {
+      float* pg = (mode == 2) ? sp.part2_g : sp.part_g;
+      float* pw = (mode == 2) ? sp.part2_w : sp.part_w;
+      pg[(size_t)e * gridDim.x + blockIdx.x] = sg;   // gridDim.x = nct2 (= nct on the FP32 path)
+      pw[(size_t)e * gridDim.x + blockIdx.x] = sw;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// decisions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sr_row_value(const float* pg, int nct) {
+  float f = 0.0f;
+  for (int c = 0; c < nct; ++c) f += pg[c];
+  return (f != f) ? __int_as_float(0x7F800000) : f;
+}
+
+// Bound on |f_BF16 - f_FP32path| of one row from |a|_2 and sum_k w_k |z_k|:
+// |dz_k| <= delta = c |a|_2 for every k; Rastrigin |dg| <= delta (2|z| + 20 pi
+// + 3 delta); elliptic |dg_k| <= w_k delta (2|z_k| + delta); plus the
+// reductions' relative error.
+__device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, float f, int D, const SrBound& b) {
+  const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f;
+  float e;
+  if (obj == kSrElliptic) e = delta * (2.0f * sumw + delta * b.sum_w);
+  else e = delta * (2.0f * sumw + (float)D * (20.0f * 3.14159274f + 3.0f * delta));
+  return (e + b.rel * fabsf(f)) * 1.001f;
+}
+
+__global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bnd) {
+  const GenParams& p = sp.g;
+  const long long gen = p.st->gen;
+  const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
+  uint8_t* slot_out = p.slots + (size_t)((gen + 1) & 1) * p.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += gridDim.x * blockDim.x) {
+    const int si = slot_in[i];
+    const float f = sr_row_value(sp.part_g + (size_t)i * sp.nct, sp.nct);
+    float bu = 0.0f;
+    if (sp.prec != 0) {
+      float sw = 0.0f;
+      for (int c = 0; c < sp.nct; ++c) sw += sp.part_w[(size_t)i * sp.nct + c];
+      bu = sr_bound(sp.obj, sp.norm2[i], sw, f, p.D, bnd);
+    }
+    const float fx = p.fit[i], bx = sp.fit_err[i];
+    int decision;                                    // 1 accept, 0 reject, 2 ambiguous
+    if (bu == 0.0f && bx == 0.0f) decision = (f < fx) ? 1 : 0;
+    else if (f + bu < fx - bx) decision = 1;
+    else if (f - bu >= fx + bx) decision = 0;
+    else decision = 2;
+    if (decision == 1) {
+      slot_out[i] = (uint8_t)(1 - si);
+      p.fit[i] = f;
+      sp.fit_err[i] = bu;
+      atomicMin(&p.st->best_key, best_key_of(f, i));
+      atomicAdd(&p.st->accepts, 1ull);
+    } else {
+      slot_out[i] = (uint8_t)si;
+    }
+    if (decision == 2) {
+      const unsigned k = atomicAdd(sp.amb_count, bx > 0.0f ? 2u : 1u);
+      sp.amb[k] = i << 1;                            // the trial
+      if (bx > 0.0f) sp.amb[k + 1] = (i << 1) | 1;   // and the parent, when its value is inexact
+      atomicAdd(&p.st->reselected, 1ull);
+    }
+    if (p.dbg_ftrial) p.dbg_ftrial[i] = f;
+    if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)(decision == 1);
+  }
+}
+
+// Ambiguous rows: decide with FP32-path values of the trial (and the parent).
+__global__ void sr_resolve_kernel(const __grid_constant__ SrParams sp) {
+  const GenParams& p = sp.g;
+  const long long gen = p.st->gen;
+  const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
+  uint8_t* slot_out = p.slots + (size_t)((gen + 1) & 1) * p.N;
+  const unsigned n = *sp.amb_count;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    if (sp.amb[e] & 1) continue;                     // parents are read by their trial's entry
+    const int i = sp.amb[e] >> 1;
+    const float fu = sr_row_value(sp.part2_g + (size_t)e * sp.nct2, sp.nct2);
+    float fx = p.fit[i];
+    if (e + 1 < n && sp.amb[e + 1] == ((i << 1) | 1)) {
+      fx = sr_row_value(sp.part2_g + (size_t)(e + 1) * sp.nct2, sp.nct2);
+      p.fit[i] = fx;                                 // the parent's exact FP32-path value
+      sp.fit_err[i] = 0.0f;
+    }
+    const int si = slot_in[i];
+    const int acc = (fu < fx) ? 1 : 0;
+    if (acc) {
+      slot_out[i] = (uint8_t)(1 - si);
+      p.fit[i] = fu;
+      sp.fit_err[i] = 0.0f;
+      atomicMin(&p.st->best_key, best_key_of(fu, i));
+      atomicAdd(&p.st->accepts, 1ull);
+    }
+    if (p.dbg_ftrial) p.dbg_ftrial[i] = fu;
+    if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)acc;
+  }
+}
+
+// Close the generation (one thread); clears the ambiguous list for the next.
+__global__ void sr_close_kernel(DevState* st, unsigned* amb_count) {
+  const float bf = from_ordered_bits((uint32_t)(st->best_key >> 32));
+  if (bf < st->best_f) {
+    st->best_f = bf;
+    st->best_gen = st->gen + 1;
+  }
+  st->gen = st->gen + 1;
+  *amb_count = 0u;
+}
+
+// Initial evaluation (FP32 path): fit = sum of partials, fit_err = 0, best key.
+__global__ void sr_store_eval_kernel(const __grid_constant__ SrParams sp) {
+  const GenParams& p = sp.g;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += gridDim.x * blockDim.x) {
+    const float f = sr_row_value(sp.part_g + (size_t)i * sp.nct, sp.nct);
+    p.fit[i] = f;
+    sp.fit_err[i] = 0.0f;
+    atomicMin(&p.st->best_key, best_key_of(f, i));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int XO>
+static cudaError_t sr_trial_xo(int vidx, const SrParams& sp, int block, cudaStream_t s) {
+  const dim3 grid((unsigned)sp.g.N), blk((unsigned)block);
+  switch (vidx) {
+    case 0: sr_trial_kernel<XO, 1><<<grid, blk, 0, s>>>(sp); break;
+    case 1: sr_trial_kernel<XO, 2><<<grid, blk, 0, s>>>(sp); break;
+    case 2: sr_trial_kernel<XO, 4><<<grid, blk, 0, s>>>(sp); break;
+    case 3: sr_trial_kernel<XO, 8><<<grid, blk, 0, s>>>(sp); break;
+    case 4: sr_trial_kernel<XO, 16><<<grid, blk, 0, s>>>(sp); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sr_trial(int xo, int vidx, const SrParams& sp, int block, cudaStream_t s) {
+  if (xo == kBin) return sr_trial_xo<kBin>(vidx, sp, block, s);
+  if (xo == kExp) return sr_trial_xo<kExp>(vidx, sp, block, s);
+  return sr_trial_xo<kNec>(vidx, sp, block, s);
+}
+
+cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
+  const dim3 grid((unsigned)sp.nct2, (unsigned)((max_rows + kSrTile - 1) / kSrTile));
+  sr_gemm_fp32_kernel<<<grid, 256, 0, s>>>(sp, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sr_select(const SrParams& sp, const SrBound& b, cudaStream_t s) {
+  sr_select_kernel<<<(sp.g.N + 255) / 256, 256, 0, s>>>(sp, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s) {
+  sr_resolve_kernel<<<(2 * sp.g.N + 255) / 256, 256, 0, s>>>(sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sr_close(const SrParams& sp, cudaStream_t s) {
+  sr_close_kernel<<<1, 1, 0, s>>>(sp.g.st, sp.amb_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s) {
+  sr_store_eval_kernel<<<(sp.g.N + 255) / 256, 256, 0, s>>>(sp);
+  return cudaGetLastError();
+}
+
+}  // namespace de
+
+namespace de {
+
+// R -> bf16(R), bf16(R - bf16(R)).
+__global__ void sr_split_kernel(const float* rot, uint16_t* hi, uint16_t* lo, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const float r = rot[k];
+    const __nv_bfloat16 h = __float2bfloat16_rn(r);
+    hi[k] = __bfloat16_as_ushort(h);
+    lo[k] = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(r, __bfloat162float(h))));
+  }
+}
+
+cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, cudaStream_t s) {
+  sr_split_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(rot, hi, lo, n);
+  return cudaGetLastError();
+}
+
+// The incumbent in FP64 (the only FP64 arithmetic on the GPU): every `every`
+// generations, after the generation closed, the best row's objective is
+// recomputed as z = R (x - o) and sum g(z) in FP64 and kept in the state.
+__global__ void sr_incumbent_kernel(const __grid_constant__ SrParams sp, int every) {
+  const GenParams& p = sp.g;
+  const long long gen = p.st->gen;
+  if (every <= 0 || gen % every != 0) return;
+  __shared__ double red[32];
+  const int idx = (int)(uint32_t)(p.st->best_key & 0xFFFFFFFFull);
+  if (idx < 0 || idx >= p.N) return;
+  const int si = p.slots[(size_t)(gen & 1) * p.N + idx];
+  const float* x = (si ? p.pop1 : p.pop0) + (size_t)idx * p.pitch;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < p.D; k += blockDim.x) {
+    double z = 0.0;
+    for (int j = 0; j < p.D; ++j) z += (double)sp.rot[(size_t)k * p.D + j] * ((double)x[j] - (double)sp.shift[j]);
+    if (sp.obj == kSrElliptic) {
+      const double c = (p.D > 1) ? exp2((double)k * (6.0 * 3.321928094887362 / (double)(p.D - 1))) : 1.0;
+      acc += c * z * z;
+    } else {
+      acc += z * z - 10.0 * cos(2.0 * 3.141592653589793 * z) + 10.0;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f += red[w];
+    p.st->incumbent_f64 = f;
+    p.st->incumbent_gen = gen;
+  }
+}
+
+cudaError_t launch_sr_incumbent(const SrParams& sp, int every, cudaStream_t s) {
+  sr_incumbent_kernel<<<1, 1024, 0, s>>>(sp, every);
+  return cudaGetLastError();
+}
+
+}  // namespace de

@@ -40,7 +40,7 @@ class de_objparams(C.Structure):
 class de_stats_t(C.Structure):
     _fields_ = [("generation", C.c_int64), ("accepts", C.c_uint64), ("masked_genes", C.c_uint64),
                 ("reselected", C.c_uint64), ("best_gen", C.c_int64), ("best_f", C.c_double),
-                ("best_index", C.c_int32)]
+                ("best_index", C.c_int32), ("incumbent_f64", C.c_double), ("incumbent_gen", C.c_int64)]
 
 
 class de_instance_spec(C.Structure):
