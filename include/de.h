@@ -104,7 +104,7 @@ typedef struct {
   double best_f;            /* best fitness (FP32 value, widened)                          */
   int32_t best_index;       /* row holding it; lowest index on ties                       */
   double incumbent_f64;     /* shifted-rotated: the best row's objective recomputed in FP64
-                               every incumbent_every generations (NaN otherwise)           */
+                               every incumbent_every generations (0 when incumbent_gen is -1) */
   int64_t incumbent_gen;    /* generation of that re-evaluation (-1 = none)                */
 } de_stats_t;
 

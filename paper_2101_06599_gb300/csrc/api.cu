@@ -443,7 +443,7 @@ int de_stats(de_ctx* c, de_stats_t* out) {
   out->best_gen = s.best_gen;
   out->best_f = (double)s.best_f;
   out->best_index = (int32_t)(uint32_t)(s.best_key & 0xFFFFFFFFull);
-  out->incumbent_f64 = c->rotated ? s.incumbent_f64 : NAN;
+  out->incumbent_f64 = c->rotated ? s.incumbent_f64 : 0.0;
   out->incumbent_gen = c->rotated ? s.incumbent_gen : -1;
   return DE_OK;
 }

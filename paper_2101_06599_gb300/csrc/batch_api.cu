@@ -123,6 +123,7 @@ int batch_stats(de_ctx* c, de_stats_t* out) {
   std::memset(out, 0, sizeof(*out));
   out->best_f = INFINITY;
   out->best_index = -1;
+  out->incumbent_gen = -1;
   out->generation = h.empty() ? 0 : h[0].gen;
   for (int k = 0; k < c->n_inst; ++k) {
     if (h[k].error) return (int)h[k].error;
@@ -309,6 +310,8 @@ int de_batch_stats(de_ctx* c, int32_t inst, de_stats_t* out) {
   out->best_gen = s.best_gen;
   out->best_f = (double)s.best_f;
   out->best_index = (int32_t)(uint32_t)(s.best_key & 0xFFFFFFFFull);
+  out->incumbent_f64 = 0.0;
+  out->incumbent_gen = -1;
   return DE_OK;
 }
 
