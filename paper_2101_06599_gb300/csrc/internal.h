@@ -81,6 +81,7 @@ cudaError_t launch_sr_incumbent(const SrParams& sp, int every, cudaStream_t s);
 // tcgen05 BF16 product (split operands) with the fitness epilogue; requires
 // D % 256 == 0. sr_tc_supported tells whether this build and device have it.
 cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s);
+cudaError_t prepare_sr_tc();
 bool sr_tc_supported(int D);
 
 constexpr size_t kStagingHeader = 32;

@@ -74,6 +74,8 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
     sp.rot_hi = hi;
     sp.rot_lo = lo;
     if (launch_sr_split_rotation(rot, hi, lo, (size_t)D * D, c->stream) != cudaSuccess) return DE_ECUDA;
+    if (prepare_sr_tc() != cudaSuccess) return DE_ECUDA;
+    sp.nct = D / 256;                    // one partial per 256-column tile of the tensor-core product
   }
   c->sbound = make_bound(D, c->obj, (double)c->p.ell_k);
   return sync_stream(c);                 // host shift / rotation consumed

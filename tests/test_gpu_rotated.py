@@ -103,3 +103,57 @@ def test_rotated_identity_matches_plain_objective_shift():
         assert np.all(np.abs(fit - ref) <= 1e-5 * np.maximum(1, np.abs(ref)))
     finally:
         opt.close()
+
+
+# ---- the tensor-core path: split BF16 operands, interval decisions, FP32 re-evaluation ---------
+@pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
+@pytest.mark.parametrize("N,D,xo", [(256, 256, "nec"), (300, 512, "bin"), (128, 1024, "exp")])
+def test_rotated_bf16_selections_equal_fp32_path(obj, N, D, xo):
+    """Same seed and population on the FP32 path and the BF16 tensor-core path:
+    identical trials and identical selections generation after generation."""
+    a, o, R = make(N, D, xo, obj, prec="fp32", seed=5)
+    b, _, _ = make(N, D, xo, obj, prec="bf16", seed=5)
+    try:
+        lo, hi = W.BOXES[obj]
+        pop = W.population(N, D, lo, hi, 55)
+        a.set_population(pop)
+        b.set_population(pop)
+        reselected = 0
+        for g in range(4):
+            ta, fa, acca, da = a.debug_step()
+            tb, fb, accb, db = b.debug_step()
+            assert np.array_equal(da, db)
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            assert np.array_equal(acca, accb), "generation %d: selections differ" % g
+            # BF16 values of decided rows are close to the FP32 path's; re-evaluated rows equal it
+            rel = np.abs(fb.astype(np.float64) - fa) / np.maximum(1.0, np.abs(fa))
+            assert rel.max() < 1e-3, rel.max()
+            pa, ffa = a.population()
+            pb, ffb = b.population()
+            assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        st = b.stats()
+        assert st["generation"] == 4 and st["reselected"] >= 0
+        print("rows re-evaluated in FP32 over 4 generations:", st["reselected"], "of", 4 * N)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_rotated_bf16_against_oracle():
+    N, D, obj, xo = 200, 256, "sr_rastrigin", "nec"
+    opt, o, R = make(N, D, xo, obj, prec="bf16", seed=9)
+    try:
+        lo, hi = W.BOXES[obj]
+        pop = W.population(N, D, lo, hi, 77)
+        opt.set_population(pop)
+        fit64 = O.evaluate(obj, pop, shift=o, rot=R)
+        g = opt.stats()["generation"]
+        trial, ft, acc, draws = opt.debug_step()
+        s = O.step(pop, fit64, 0.5, 0.9, xo, obj, lo, hi, 9, g, shift=o, rot=R)
+        assert np.array_equal(draws, s.draws)
+        assert np.array_equal(trial.view(np.uint32), s.trial.view(np.uint32))
+        assert np.all(np.abs(ft - s.ftrial) <= 1e-3 * np.maximum(1, np.abs(s.ftrial)))
+        amb = np.abs(s.ftrial - fit64) <= tol(s.ftrial) + tol(fit64)
+        assert np.array_equal(acc[~amb], s.accept[~amb])
+    finally:
+        opt.close()
