@@ -346,11 +346,12 @@ __global__ void sr_close_kernel(DevState* st, unsigned* amb_count) {
   *amb_count = 0u;
 }
 
-// Initial evaluation (FP32 path): fit = sum of partials, fit_err = 0, best key.
+// Initial evaluation (always the FP32 product, whose partials have nct2
+// columns): fit = sum of partials, fit_err = 0, best key.
 __global__ void sr_store_eval_kernel(const __grid_constant__ SrParams sp) {
   const GenParams& p = sp.g;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += gridDim.x * blockDim.x) {
-    const float f = sr_row_value(sp.part_g + (size_t)i * sp.nct, sp.nct);
+    const float f = sr_row_value(sp.part_g + (size_t)i * sp.nct2, sp.nct2);
     p.fit[i] = f;
     sp.fit_err[i] = 0.0f;
     atomicMin(&p.st->best_key, best_key_of(f, i));
