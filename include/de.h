@@ -78,6 +78,16 @@ typedef enum {
 /* Precision of the z = R (x - o) product of the shifted-rotated objectives. */
 typedef enum { DE_PREC_FP32 = 0, DE_PREC_TF32 = 1, DE_PREC_BF16 = 2 } de_precision;
 
+/* Error bound that decides which BF16-path selections are certain (the rest
+ * are re-evaluated with the FP32 product, so that decisions match the FP32
+ * path). PROBABILISTIC: margin_sigmas standard deviations of |f_BF16 -
+ * f_FP32| under the standard model of independent, zero-mean rounding errors
+ * (Hoeffding's inequality), with the accumulation's partial sums taken as at
+ * most 4 |x - o|_2 / sqrt(D) (rotations with delocalised rows, such as a
+ * random orthogonal R). WORST_CASE: the deterministic bound, valid for any R,
+ * which at D ~ 1000 sends almost every row to the FP32 re-evaluation. */
+typedef enum { DE_BOUND_PROBABILISTIC = 0, DE_BOUND_WORST_CASE = 1 } de_bound_kind;
+
 /* Search box, the same for every dimension (Section 4 gives one interval
  * per function). Requires lo < hi, both finite. Trial genes are clipped to
  * [lo, hi] (bound repair; the paper names none). */
@@ -91,6 +101,10 @@ typedef struct {
   de_precision prec;        /* shifted-rotated objectives: product precision                */
   int32_t incumbent_every;  /* shifted-rotated: FP64 re-evaluation of the best every K
                                generations (0 selects 50)                                  */
+  de_bound_kind bound;      /* BF16 product: which error bound decides certain selections  */
+  double margin_sigmas;     /* PROBABILISTIC bound: margin in standard deviations (0 selects
+                               8; the model's failure probability per decision is at most
+                               2 exp(-m^2 / 2))                                             */
 } de_objparams;
 
 /* Counters kept on the device and read by de_stats. */

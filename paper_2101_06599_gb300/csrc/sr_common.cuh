@@ -34,13 +34,28 @@ struct SrParams {
   unsigned* amb_count;     // number of entries in amb
   float* part2_g;          // 2N x nct: partial sums of the re-evaluated entries
   float* part2_w;
+  double* inc_part;        // D: FP64 g(z_k) of the incumbent re-evaluation
+  unsigned* inc_count;     // CTAs of the incumbent re-evaluation done (last one sums)
 };
 
-// Bound constants of the BF16 path (sr_select_kernel).
+// Bound constants of the BF16 path (sr_select_kernel). For a row with a =
+// u - o, |a|_2 = n and FP32 value f, H bounds |g'(z)|_2: Rastrigin
+// 2 n + 20 pi sqrt(D) (|g'(z)| <= 2|z| + 20 pi, |z|_2 = n), elliptic
+// 2 sqrt(w_max |f|) (sum w^2 z^2 <= w_max sum w z^2).
 struct SrBound {
-  float delta_per_norm;   // per-element |dz| bound per unit |u - o|_2
+  int mode;               // 0 probabilistic, 1 worst case
+  // worst case: |dz_k| <= delta_per_norm * n for every k
+  float delta_per_norm;
   float rel;              // relative bound of the reductions of sum g
   float sum_w;            // sum of the elliptic weights
+  // probabilistic: lambda * sqrt(s_rep^2 + s_acc^2 + s_eval^2) + quad
+  float lambda;           // margin in standard deviations
+  float rep_c;            // s_rep = rep_c * H  (operand-split residuals, sqrt(3) 2^-16 max|a_j|)
+  float acc_c;            // s_acc = acc_c * n * H (accumulation roundings of both products)
+  float eval_c;           // s_eval = eval_c * |f| (g evaluation and the sums over k)
+  float quad_a, quad_b;   // second-order term quad_a + quad_b * n^2
+  float hconst;           // Rastrigin: 20 pi sqrt(D)
+  float wmax;             // elliptic: the largest weight
 };
 
 // The elliptic weight of column k: 10^(6k/(D-1)) = 2^(k * ell_k).

@@ -252,16 +252,30 @@ __device__ __forceinline__ float sr_row_value(const float* pg, int nct) {
   return (f != f) ? __int_as_float(0x7F800000) : f;
 }
 
-// Bound on |f_BF16 - f_FP32path| of one row from |a|_2 and sum_k w_k |z_k|:
-// |dz_k| <= delta = c |a|_2 for every k; Rastrigin |dg| <= delta (2|z| + 20 pi
-// + 3 delta); elliptic |dg_k| <= w_k delta (2|z_k| + delta); plus the
+// Bound on |f_BF16 - f_FP32path| of one row from n^2 = |a|_2^2, the row's
+// sum_k w_k |z_k| and its value f.
+// Worst case: |dz_k| <= delta = c n for every k; Rastrigin |dg| <= delta (2|z|
+// + 20 pi + 3 delta); elliptic |dg_k| <= w_k delta (2|z_k| + delta); plus the
 // reductions' relative error.
+// Probabilistic: the first-order change sum_k g'(z_k) dz_k is a sum of
+// independent zero-mean terms (operand-split residuals, accumulation
+// roundings) whose bounds give the standard deviations; the g evaluations and
+// the sums over k add theirs; second-order terms are bounded by the mean of
+// |dz|_2^2 with a factor 2.
 __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, float f, int D, const SrBound& b) {
-  const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f;
-  float e;
-  if (obj == kSrElliptic) e = delta * (2.0f * sumw + delta * b.sum_w);
-  else e = delta * (2.0f * sumw + (float)D * (20.0f * 3.14159274f + 3.0f * delta));
-  return (e + b.rel * fabsf(f)) * 1.001f;
+  if (b.mode == 1) {
+    const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f;
+    float e;
+    if (obj == kSrElliptic) e = delta * (2.0f * sumw + delta * b.sum_w);
+    else e = delta * (2.0f * sumw + (float)D * (20.0f * 3.14159274f + 3.0f * delta));
+    return (e + b.rel * fabsf(f)) * 1.001f;
+  }
+  const float n = sqrtf(norm2) * 1.0001f;
+  const float af = fabsf(f);
+  const float H = (obj == kSrElliptic) ? 2.0f * sqrtf(b.wmax * af * 1.0001f) : 2.0002f * n + b.hconst;
+  const float s_rep = b.rep_c * H, s_acc = b.acc_c * n * H, s_ev = b.eval_c * af;
+  const float sig = sqrtf(s_rep * s_rep + s_acc * s_acc + s_ev * s_ev);
+  return (b.lambda * sig + b.quad_a + b.quad_b * norm2) * 1.001f;
 }
 
 __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bnd) {
@@ -275,7 +289,8 @@ __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bn
     float bu = 0.0f;
     if (sp.prec != 0) {
       float sw = 0.0f;
-      for (int c = 0; c < sp.nct; ++c) sw += sp.part_w[(size_t)i * sp.nct + c];
+      if (bnd.mode == 1)
+        for (int c = 0; c < sp.nct; ++c) sw += sp.part_w[(size_t)i * sp.nct + c];
       bu = sr_bound(sp.obj, sp.norm2[i], sw, f, p.D, bnd);
     }
     const float fx = p.fit[i], bx = sp.fit_err[i];
@@ -429,39 +444,61 @@ cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* l
 // The incumbent in FP64 (the only FP64 arithmetic on the GPU): every `every`
 // generations, after the generation closed, the best row's objective is
 // recomputed as z = R (x - o) and sum g(z) in FP64 and kept in the state.
-__global__ void sr_incumbent_kernel(const __grid_constant__ SrParams sp, int every) {
+// One warp per z_k (coalesced reads of row k of R, lanes over j, a fixed
+// shuffle tree), g(z_k) to inc_part[k]; the last CTA to finish sums
+// inc_part in a fixed order, so the value does not depend on scheduling.
+constexpr int kIncWarps = 8;
+
+__global__ void __launch_bounds__(kIncWarps * 32) sr_incumbent_kernel(const __grid_constant__ SrParams sp, int every) {
   const GenParams& p = sp.g;
   const long long gen = p.st->gen;
   if (every <= 0 || gen % every != 0) return;
-  __shared__ double red[32];
   const int idx = (int)(uint32_t)(p.st->best_key & 0xFFFFFFFFull);
-  if (idx < 0 || idx >= p.N) return;
+  if (idx < 0 || idx >= p.N) return;                // uniform across the grid: no CTA counts
   const int si = p.slots[(size_t)(gen & 1) * p.N + idx];
   const float* x = (si ? p.pop1 : p.pop0) + (size_t)idx * p.pitch;
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < p.D; k += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * kIncWarps + warp;
+  if (k < p.D) {
+    const float* r = sp.rot + (size_t)k * p.D;
     double z = 0.0;
-    for (int j = 0; j < p.D; ++j) z += (double)sp.rot[(size_t)k * p.D + j] * ((double)x[j] - (double)sp.shift[j]);
-    if (sp.obj == kSrElliptic) {
-      const double c = (p.D > 1) ? exp2((double)k * (6.0 * 3.321928094887362 / (double)(p.D - 1))) : 1.0;
-      acc += c * z * z;
-    } else {
-      acc += z * z - 10.0 * cos(2.0 * 3.141592653589793 * z) + 10.0;
+    for (int j = lane; j < p.D; j += 32) z = fma((double)r[j], (double)x[j] - (double)sp.shift[j], z);
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, o);
+    if (lane == 0) {
+      double gk;
+      if (sp.obj == kSrElliptic) {
+        const double c = (p.D > 1) ? exp2((double)k * (6.0 * 3.321928094887362 / (double)(p.D - 1))) : 1.0;
+        gk = c * z * z;
+      } else {
+        gk = z * z - 10.0 * cos(2.0 * 3.141592653589793 * z) + 10.0;
+      }
+      sp.inc_part[k] = gk;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __shared__ unsigned ticket;
+  __shared__ double red[kIncWarps * 32];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(sp.inc_count, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < p.D; q += blockDim.x) acc += __ldcg(sp.inc_part + q);
+  red[threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double f = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f += red[w];
+    for (int w = 0; w < (int)blockDim.x; ++w) f += red[w];
     p.st->incumbent_f64 = f;
     p.st->incumbent_gen = gen;
+    *sp.inc_count = 0u;
   }
 }
 
 cudaError_t launch_sr_incumbent(const SrParams& sp, int every, cudaStream_t s) {
-  sr_incumbent_kernel<<<1, 1024, 0, s>>>(sp, every);
+  const unsigned grid = (unsigned)((sp.g.D + kIncWarps - 1) / kIncWarps);
+  sr_incumbent_kernel<<<grid, kIncWarps * 32, 0, s>>>(sp, every);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ XOVER = {"bin": 0, "exp": 1, "nec": 2}
 OBJECTIVE = {"sphere": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "griewank": 4,
              "elliptic": 5, "sr_rastrigin": 6, "sr_elliptic": 7}
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
+BOUND = {"probabilistic": 0, "worst_case": 1}
 
 
 class DEError(RuntimeError):
@@ -34,7 +35,8 @@ class de_bounds(C.Structure):
 
 class de_objparams(C.Structure):
     _fields_ = [("ackley_b", C.c_double), ("shift", C.c_void_p), ("rotation", C.c_void_p),
-                ("prec", C.c_int), ("incumbent_every", C.c_int32)]
+                ("prec", C.c_int), ("incumbent_every", C.c_int32), ("bound", C.c_int),
+                ("margin_sigmas", C.c_double)]
 
 
 class de_stats_t(C.Structure):
@@ -190,7 +192,9 @@ def de_create(N, D, F, CR, xo, obj, bounds, seed, params=None, stream=None):
                           shift.ctypes.data if shift is not None else None,
                           rot.ctypes.data if rot is not None else None,
                           PRECISION.get(params.get("prec", "fp32"), 0),
-                          int(params.get("incumbent_every", 0)))
+                          int(params.get("incumbent_every", 0)),
+                          BOUND[params.get("bound", "probabilistic")],
+                          float(params.get("margin_sigmas", 0.0)))
     xo_i = XOVER[xo] if isinstance(xo, str) else int(xo)
     obj_i = OBJECTIVE[obj] if isinstance(obj, str) else int(obj)
     rc = L.de_create(C.byref(h), int(N), int(D), float(F), float(CR), xo_i, obj_i,
