@@ -240,10 +240,10 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   if (!valid_problem(N, D, F, CR, (int)xo, (int)obj, b)) return DE_EINVAL;
   if (is_rotated(obj)) {
     if (!prm || !prm->shift || !prm->rotation) return DE_EINVAL;
-    if (prm->prec != DE_PREC_FP32 && prm->prec != DE_PREC_BF16) return DE_EUNSUPPORTED;
-    if (prm->prec == DE_PREC_BF16 && !sr_tc_supported(D)) return DE_EUNSUPPORTED;
     if (prm->bound != DE_BOUND_PROBABILISTIC && prm->bound != DE_BOUND_WORST_CASE) return DE_EINVAL;
     if (!std::isfinite(prm->margin_sigmas) || prm->margin_sigmas < 0.0) return DE_EINVAL;
+    if (prm->prec != DE_PREC_FP32 && prm->prec != DE_PREC_BF16) return DE_EUNSUPPORTED;
+    if (prm->prec == DE_PREC_BF16 && !sr_tc_supported(D)) return DE_EUNSUPPORTED;
   }
   double ackley_b = 0.2;
   if (prm && prm->ackley_b != 0.0) {

@@ -31,8 +31,13 @@ namespace de_host {
 // |g'|_2 c_rw |a|_2 sqrt(3 u_tc^2 + u^2) when the partial sums stay within
 // c_rw |a|_2 / sqrt(D), c_rw = 4; the g evaluations (<= 12 roundings each)
 // and the sums of D values and nct partials on both paths at most
-// u |f| (sqrt(2 (D + nct)) + 12) because every g is >= 0. The second-order
-// term is bounded by max|g''| / 2 times twice the mean of |dz|_2^2.
+// u |f| (sqrt(2 (D + nct)) + 12) because every g is >= 0. The tensor cores'
+// accumulator truncates: 3D / 16 MMA steps (K = 16 each) round each z_k
+// toward zero by at most 2^-23 |z_k| (partial sums taken no larger than
+// |z_k|), a bias of at most (3D/16) 2^-23 sum_k |g'(z_k)| |z_k|, which is at
+// most n (2 n + 20 pi sqrt(D)) for Rastrigin and 2 |f| for the elliptic
+// function. The second-order term is bounded by max|g''| / 2 times twice the
+// mean of |dz|_2^2.
 static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas, double amax, int nct) {
   SrBound b{};
   const double u = std::ldexp(1.0, -24), utc = std::ldexp(1.0, -23);
@@ -59,6 +64,7 @@ static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas,
   b.quad_a = (float)(g2half * 2.0 * D * 3.0 * std::ldexp(1.0, -32) * amax * amax);
   b.quad_b = (float)(g2half * 2.0 * D * acc2 * c_rw * c_rw);
   b.hconst = (float)(20.0 * pi * std::sqrt((double)D));
+  b.bias_c = (float)((3.0 * D / 16.0) * utc * 1.001);
   b.wmax = (float)((obj == DE_OBJ_SR_ELLIPTIC) ? std::exp2((double)(D - 1) * ell_k) * 1.0001 : 0.0);
   return b;
 }

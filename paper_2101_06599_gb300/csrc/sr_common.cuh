@@ -48,12 +48,13 @@ struct SrBound {
   float delta_per_norm;
   float rel;              // relative bound of the reductions of sum g
   float sum_w;            // sum of the elliptic weights
-  // probabilistic: lambda * sqrt(s_rep^2 + s_acc^2 + s_eval^2) + quad
+  // probabilistic: lambda * sqrt(s_rep^2 + s_acc^2 + s_eval^2) + bias + quad
   float lambda;           // margin in standard deviations
   float rep_c;            // s_rep = rep_c * H  (operand-split residuals, sqrt(3) 2^-16 max|a_j|)
   float acc_c;            // s_acc = acc_c * n * H (accumulation roundings of both products)
   float eval_c;           // s_eval = eval_c * |f| (g evaluation and the sums over k)
   float quad_a, quad_b;   // second-order term quad_a + quad_b * n^2
+  float bias_c;           // truncation bias: bias_c * sum_k |g'(z_k)| |z_k| (n H Rastrigin, 2|f| elliptic)
   float hconst;           // Rastrigin: 20 pi sqrt(D)
   float wmax;             // elliptic: the largest weight
 };

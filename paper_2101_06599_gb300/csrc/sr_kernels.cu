@@ -260,8 +260,10 @@ __device__ __forceinline__ float sr_row_value(const float* pg, int nct) {
 // Probabilistic: the first-order change sum_k g'(z_k) dz_k is a sum of
 // independent zero-mean terms (operand-split residuals, accumulation
 // roundings) whose bounds give the standard deviations; the g evaluations and
-// the sums over k add theirs; second-order terms are bounded by the mean of
-// |dz|_2^2 with a factor 2.
+// the sums over k add theirs. The tensor cores' FP32 accumulator rounds
+// toward zero, which shrinks every |z_k| a little: one rounding of at most
+// 2^-23 |z_k| per MMA step bounds that bias. Second-order terms are bounded
+// by the mean of |dz|_2^2 with a factor 2.
 __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, float f, int D, const SrBound& b) {
   if (b.mode == 1) {
     const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f;
@@ -275,7 +277,8 @@ __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, floa
   const float H = (obj == kSrElliptic) ? 2.0f * sqrtf(b.wmax * af * 1.0001f) : 2.0002f * n + b.hconst;
   const float s_rep = b.rep_c * H, s_acc = b.acc_c * n * H, s_ev = b.eval_c * af;
   const float sig = sqrtf(s_rep * s_rep + s_acc * s_acc + s_ev * s_ev);
-  return (b.lambda * sig + b.quad_a + b.quad_b * norm2) * 1.001f;
+  const float bias = b.bias_c * ((obj == kSrElliptic) ? 2.0f * af : n * H);
+  return (b.lambda * sig + bias + b.quad_a + b.quad_b * norm2) * 1.001f;
 }
 
 __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bnd) {

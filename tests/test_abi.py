@@ -67,6 +67,23 @@ def test_rotated_objective_needs_shift_and_rotation(lib):
     assert e.value.code == DE.DE_EINVAL
 
 
+@pytest.mark.parametrize("extra", [{"bound": 7}, {"margin_sigmas": -1.0}, {"margin_sigmas": float("nan")}])
+def test_rotated_bound_parameters_are_validated(lib, extra):
+    import numpy as np
+    D = 8
+    params = {"shift": np.zeros(D, np.float32), "rotation": np.eye(D, dtype=np.float32), "prec": "fp32"}
+    params.update(extra)
+    if "bound" in extra:
+        DE.BOUND[7] = 7                      # an out-of-range enum value, passed through unchanged
+        params["bound"] = 7
+    try:
+        with pytest.raises(DE.DEError) as e:
+            DE.de_create(16, D, 0.5, 0.9, "nec", "sr_rastrigin", (-100.0, 100.0), 1, params=params)
+        assert e.value.code == DE.DE_EINVAL
+    finally:
+        DE.BOUND.pop(7, None)
+
+
 def test_null_context_calls_are_rejected(lib):
     assert lib.de_step(None) == DE.DE_EINVAL
     assert lib.de_run(None, 3) == DE.DE_EINVAL

@@ -28,11 +28,12 @@ def _gpu():
     DE.load_library()
 
 
-def make(N, D, xo, obj, prec="fp32", CR=0.9, F=0.5, seed=1, every=0):
+def make(N, D, xo, obj, prec="fp32", CR=0.9, F=0.5, seed=1, every=0, **extra):
     o = W.shift_vector(D, seed=2)
     R = W.rotation(D, seed=3)
-    opt = DE.Optimizer(N, D, F=F, CR=CR, xo=xo, obj=obj, bounds=W.BOXES[obj], seed=seed,
-                       params={"shift": o, "rotation": R, "prec": prec, "incumbent_every": every})
+    params = {"shift": o, "rotation": R, "prec": prec, "incumbent_every": every}
+    params.update(extra)
+    opt = DE.Optimizer(N, D, F=F, CR=CR, xo=xo, obj=obj, bounds=W.BOXES[obj], seed=seed, params=params)
     return opt, o, R
 
 
@@ -107,12 +108,13 @@ def test_rotated_identity_matches_plain_objective_shift():
 
 # ---- the tensor-core path: split BF16 operands, interval decisions, FP32 re-evaluation ---------
 @pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
-@pytest.mark.parametrize("N,D,xo", [(256, 256, "nec"), (300, 512, "bin"), (128, 1024, "exp")])
-def test_rotated_bf16_selections_equal_fp32_path(obj, N, D, xo):
+@pytest.mark.parametrize("N,D,xo,bound", [(256, 256, "nec", "probabilistic"), (300, 512, "bin", "probabilistic"),
+                                          (128, 1024, "exp", "probabilistic"), (128, 512, "nec", "worst_case")])
+def test_rotated_bf16_selections_equal_fp32_path(obj, N, D, xo, bound):
     """Same seed and population on the FP32 path and the BF16 tensor-core path:
     identical trials and identical selections generation after generation."""
     a, o, R = make(N, D, xo, obj, prec="fp32", seed=5)
-    b, _, _ = make(N, D, xo, obj, prec="bf16", seed=5)
+    b, _, _ = make(N, D, xo, obj, prec="bf16", seed=5, bound=bound)
     try:
         lo, hi = W.BOXES[obj]
         pop = W.population(N, D, lo, hi, 55)
@@ -157,3 +159,98 @@ def test_rotated_bf16_against_oracle():
         assert np.array_equal(acc[~amb], s.accept[~amb])
     finally:
         opt.close()
+
+
+# ---- the error bound that decides which BF16 selections are certain ---------------------------
+U, UTC = 2.0 ** -24, 2.0 ** -23
+
+
+def bf16_bound(obj, D, o, box, trial, f, lam=8.0):
+    """The probabilistic bound on |f_BF16 - f_FP32| of each row, written out
+    from its derivation: Hoeffding deviations of the operand-split residuals,
+    of the accumulation roundings and of the g evaluations, the tensor cores'
+    truncation bias, and a second-order term."""
+    lo, hi = box
+    o64 = o.astype(np.float64)
+    amax = max(np.max(np.abs(lo - o64)), np.max(np.abs(hi - o64))) * (1 + 2.0 ** -22)
+    a = (trial - o[None, :]).astype(np.float32).astype(np.float64)
+    n2 = (a * a).sum(1)
+    n = np.sqrt(n2)
+    af = np.abs(f.astype(np.float64))
+    if obj == "sr_elliptic":
+        wmax = 10.0 ** 6
+        H = 2 * np.sqrt(wmax * af)
+        bias = (3 * D / 16) * UTC * 2 * af
+        g2half = wmax
+    else:
+        H = 2 * n + 20 * np.pi * np.sqrt(D)
+        bias = (3 * D / 16) * UTC * n * H
+        g2half = 1 + 20 * np.pi ** 2
+    s_rep = np.sqrt(3) * 1.005 * 2.0 ** -16 * amax * H
+    s_acc = 4 * np.sqrt(3 * UTC ** 2 + U ** 2) * n * H
+    s_ev = U * (np.sqrt(2 * (D + D // 256)) + 12) * af
+    quad = g2half * 2 * D * (3 * 2.0 ** -32 * amax ** 2 + (3 * UTC ** 2 + U ** 2) * 16 * n2)
+    return lam * np.sqrt(s_rep ** 2 + s_acc ** 2 + s_ev ** 2) + bias + quad
+
+
+@pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
+@pytest.mark.parametrize("D", [256, 1024, 2048])
+def test_rotated_bf16_error_within_bound(obj, D):
+    """Raw BF16-path values (almost no margin, so nearly every row is decided
+    on them) against the FP32 path's values on the same parents and trials,
+    at the start and after 100 generations: every row's difference stays well
+    inside the bound the selection uses."""
+    N = 1024
+    a, o, R = make(N, D, "nec", obj, prec="fp32", seed=11)
+    b, _, _ = make(N, D, "nec", obj, prec="bf16", seed=11, margin_sigmas=1e-6)
+    try:
+        done = 0
+        for G0 in (0, 100):
+            a.run(G0 - done)
+            b.run(G0 - done)
+            done = G0
+            pop, _ = a.population()
+            a.set_population(pop)
+            b.set_population(pop)
+            ta, fa, _, _ = a.debug_step()
+            tb, fb, _, _ = b.debug_step()
+            done += 1
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            B = bf16_bound(obj, D, o, W.BOXES[obj], tb, fb)
+            r = np.abs(fb.astype(np.float64) - fa) / B
+            print("D=%d %s gen %d: max |f_bf16 - f_fp32| / bound = %.3f, mean signed (f_bf16 - f_fp32) / bound = %.3f"
+                  % (D, obj, G0, r.max(), float(np.mean((fb.astype(np.float64) - fa) / B))))
+            assert r.max() <= 0.25, r.max()
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
+def test_rotated_bf16_lockstep_full_size(obj):
+    """The shifted-rotated workload at its full size (N = 4096, D = 1024):
+    the BF16 path with its default bound makes the FP32 path's selections in
+    every one of 30 generations, re-evaluating a small share of rows."""
+    N, D, G = 4096, 1024, 30
+    a, o, R = make(N, D, "nec", obj, prec="fp32", seed=1, every=10)
+    b, _, _ = make(N, D, "nec", obj, prec="bf16", seed=1, every=10)
+    try:
+        for g in range(G):
+            ta, fa, acca, _ = a.debug_step()
+            tb, fb, accb, _ = b.debug_step()
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32)), g
+            assert np.array_equal(acca, accb), "generation %d: selections differ" % g
+        sa, sb = a.stats(), b.stats()
+        assert sa["accepts"] == sb["accepts"]
+        assert sb["incumbent_gen"] == 30 and sa["incumbent_gen"] == 30
+        pa, _ = a.population()
+        pb, _ = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        x, f, idx, _ = b.best()
+        ref = O.evaluate(obj, x, shift=o, rot=R)
+        assert sb["incumbent_f64"] == pytest.approx(ref, rel=1e-12)
+        print("%s: rows re-evaluated in FP32: %.2f%%" % (obj, 100.0 * sb["reselected"] / (N * G)))
+        assert sb["reselected"] < 0.2 * N * G
+    finally:
+        a.close()
+        b.close()
