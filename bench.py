@@ -224,6 +224,77 @@ def time_batched(DE, torch, steps, warmup, seed, peak):
             "a_acceptance": d_acc / (rows * steps), "m_masked_fraction": d_msk / (units * steps)}
 
 
+def time_rotated(DE, torch, steps, warmup):
+    """Shifted-rotated Rastrigin and elliptic (N = 4096, D = 1024, box
+    [-100, 100], o ~ U[-80, 80] seed 2, Gaussian-QR rotation seed 3, NEC,
+    F = 0.5, Cr = 0.9): the FP32-product path against the BF16 tensor-core
+    path with FP32 re-evaluation of uncertain selections; both runs start from
+    the same population, so equal accept counts mean equal selections."""
+    from paper_2101_06599_gb300 import workloads as Wk
+    N, D = 4096, 1024
+    o = Wk.shift_vector(D, seed=2)
+    R = Wk.rotation(D, seed=3)
+    out = {"workload": "shifted_rotated_N4096_D1024", "N": N, "D": D,
+           "gemm_flop_per_gen": 2.0 * N * D * D}
+    for obj in ("sr_rastrigin", "sr_elliptic"):
+        r = {}
+        for prec in ("fp32", "bf16"):
+            opt = DE.Optimizer(N, D, F=F_DEF, CR=CR_DEF, xo="nec", obj=obj, bounds=Wk.BOXES[obj], seed=SEED,
+                               params={"shift": o, "rotation": R, "prec": prec, "incumbent_every": 50})
+            try:
+                opt.run(warmup)
+                opt.synchronize()
+                st0 = opt.stats()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(opt.stream)
+                opt.run(steps)
+                ev1.record(opt.stream)
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+                st1 = opt.stats()
+            finally:
+                opt.close()
+            r[prec] = {"ms_per_gen": ms / steps, "value": N * D * steps / (ms / 1e3),
+                       "accepts": st1["accepts"] - st0["accepts"],
+                       "reselected_frac": (st1["reselected"] - st0["reselected"]) / (N * steps)}
+        r["speedup_bf16_over_fp32"] = r["fp32"]["ms_per_gen"] / r["bf16"]["ms_per_gen"]
+        r["same_selections"] = r["fp32"]["accepts"] == r["bf16"]["accepts"]
+        out[obj] = r
+    return out
+
+
+def time_small_configs(DE, torch, warmup):
+    """The small configurations: sphere N = 100, D = 30 for 200 generations
+    (launch-bound, one graph of 200 generations) and Rastrigin N = 1024,
+    D = 1000 (a 4 MB population that stays in L2) for 1000 generations at
+    Cr in {0.1, 0.5, 0.9} with each crossover."""
+    out = {}
+    cases = [("sphere_N100_D30", 100, 30, "sphere", (-100.0, 100.0), [0.9], 200),
+             ("rastrigin_N1024_D1000", 1024, 1000, "rastrigin", (-5.12, 5.12), [0.1, 0.5, 0.9], 1000)]
+    for name, N, D, obj, box, crs, G in cases:
+        res = {}
+        for cr in crs:
+            for xo in ("bin", "exp", "nec"):
+                opt = DE.Optimizer(N, D, F=F_DEF, CR=cr, xo=xo, obj=obj, bounds=box, seed=SEED)
+                try:
+                    opt.run(G)                      # builds and warms the graph of G generations
+                    opt.synchronize()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(opt.stream)
+                    opt.run(G)
+                    ev1.record(opt.stream)
+                    ev1.synchronize()
+                    ms = ev0.elapsed_time(ev1)
+                    best = opt.best()[1]
+                finally:
+                    opt.close()
+                res["%s_cr%g" % (xo, cr)] = {"ms_per_gen": ms / G, "value": N * D * G / (ms / 1e3),
+                                             "best_f": best}
+        out[name] = {"generations": G, "results": res}
+    return out
+
+
 _dist = None
 
 
@@ -315,6 +386,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-rotated", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--only", choices=["rotated", "small", "batched"],
+                    help="run one side workload alone (for profiling); prints its own JSON line")
     ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
     ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
     args = ap.parse_args()
@@ -337,6 +412,19 @@ def main():
     DE.load_library()
     N, D, K, W = args.N, args.D, args.steps, args.warmup
     seed = SEED + rank
+
+    if args.only:
+        if args.only == "rotated":
+            res = time_rotated(DE, torch, K, W)
+        elif args.only == "small":
+            res = time_small_configs(DE, torch, W)
+        else:
+            res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0])
+        if rank == 0:
+            print(json.dumps({"only": args.only, "steps": K, "warmup": W, "result": res}))
+        if _dist is not None:
+            _dist.destroy_process_group()
+        return 0
 
     # headline: NEC on Rosenbrock, clocks sampled across the ramp and the timed region
     with ClockSampler(local) as clk:
@@ -394,6 +482,14 @@ def main():
     if not args.no_batched:
         batched = time_batched(DE, torch, K, W, seed, peak)
 
+    rotated = None
+    if not args.no_rotated:
+        rotated = time_rotated(DE, torch, K, W)
+
+    small = None
+    if not args.no_small:
+        small = time_small_configs(DE, torch, W)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, timed, secs = oracle_generation_rate(N, D, "rosenbrock", "nec", 12.0)
@@ -411,7 +507,8 @@ def main():
                        "F": F_DEF, "CR": CR_DEF, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (two 0.66 GB population buffers), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
-            "clocks": clk.summary(), "variants": variants, "batched": batched,
+            "clocks": clk.summary(), "variants": variants, "batched": batched, "rotated": rotated,
+            "small_configs": small,
         }
         print(json.dumps(line))
     if _dist is not None:
