@@ -144,101 +144,224 @@ __global__ void __launch_bounds__(kMaxThreads) sr_trial_kernel(const __grid_cons
 // FP32 product with the fitness epilogue
 // mode 0: all rows, trial rows (other slot); 1: all rows, parent rows;
 // 2: the ambiguous entries (row << 1 | parent flag), partials to part2_*.
+//
+// Every z_ik is one FMA chain over j ascending (zero padding past D adds
+// fma(0, 0, acc) = acc), and every 64-column partial sums g over the column
+// tile the same way in both kernels below: each of 16 lanes adds its 4
+// consecutive columns in order, then an xor tree over the 16 lanes
+// (offsets 8, 4, 2, 1). So a row's partials do not depend on the kernel, the
+// tile or the other rows: the re-evaluation kernel reproduces the all-rows
+// kernel bit for bit.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) sr_gemm_fp32_kernel(const __grid_constant__ SrParams sp, int mode) {
+__device__ __forceinline__ const float* sr_row_ptr(const SrParams& sp, int mode, int e, const uint8_t* slot_in) {
   const GenParams& p = sp.g;
-  __shared__ __align__(16) float As[kSrKStep][kSrTile + 4];
-  __shared__ __align__(16) float Bs[kSrKStep][kSrTile + 4];
-  __shared__ const float* rowp[kSrTile];
+  int r = e, parent = (mode == 1);
+  if (mode == 2) {
+    r = sp.amb[e] >> 1;
+    parent = sp.amb[e] & 1;
+  }
+  const int s = slot_in[r];
+  const int buf = parent ? s : 1 - s;
+  return (buf ? p.pop1 : p.pop0) + (size_t)r * p.pitch;
+}
+
+// One row's 4 columns of a 64-column tile, reduced over the tile's 16 lanes
+// (all 32 lanes of the warp call it; lanes 16..31 reduce their own tile row).
+__device__ __forceinline__ void sr_tile_reduce(const SrParams& sp, const float z[4], int c0, float& sg, float& sw) {
+  const GenParams& p = sp.g;
+  sg = 0.0f;
+  sw = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int n = c0 + b;
+    if (n < p.D) {
+      const float w = sr_weight(sp.obj, n, p.ell_k);
+      sg += sr_g(sp.obj, z[b], w);
+      sw = fmaf(w, fabsf(z[b]), sw);
+    }
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    sg += __shfl_xor_sync(0xFFFFFFFFu, sg, o);
+    sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+  }
+}
+
+// All rows (modes 0 and 1): 128 x 128 output tile, 256 threads, 8 rows x
+// (2 x 4) columns per thread (columns tx*4.. and 64 + tx*4.. so that each
+// 64-column half keeps the lane layout above), K in steps of 16 through a
+// double-buffered shared-memory stage with the next step prefetched into
+// registers. VEC: D % 4 == 0, 16-byte loads of x, o and R.
+constexpr int kGbM = 128, kGbN = 128, kGbK = 16, kGbLd = kGbM + 4;
+
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_constant__ SrParams sp, int mode) {
+  const GenParams& p = sp.g;
+  __shared__ __align__(16) float As[2][kGbK][kGbLd];
+  __shared__ __align__(16) float Bs[2][kGbK][kGbLd];
+  __shared__ const float* rowp[kGbM];
 
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int n0 = blockIdx.x * kSrTile;            // output column tile
-  const int r0 = blockIdx.y * kSrTile;            // row tile (rows or entries)
+  const int n0 = blockIdx.x * kGbN, r0 = blockIdx.y * kGbM;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
-  const int nrows = (mode == 2) ? (int)*sp.amb_count : p.N;
-  if (r0 >= nrows) return;
-
-  if (t < kSrTile) {
-    const int e = r0 + t;
-    const float* rp = nullptr;
-    if (e < nrows) {
-      int r = e, parent = (mode == 1);
-      if (mode == 2) {
-        r = sp.amb[e] >> 1;
-        parent = sp.amb[e] & 1;
-      }
-      const int s = slot_in[r];
-      const int buf = parent ? s : 1 - s;
-      rp = (buf ? p.pop1 : p.pop0) + (size_t)r * p.pitch;
-    }
-    rowp[t] = rp;
-  }
+  if (t < kGbM) rowp[t] = (r0 + t < p.N) ? sr_row_ptr(sp, mode, r0 + t, slot_in) : nullptr;
   __syncthreads();
 
-  float acc[4][4];
+  // loader: row / column lm of the tile, 8 consecutive k from lk
+  const int lm = t & (kGbM - 1), lk = (t >> 7) * 8;
+  const float* xa = rowp[lm];
+  const float* rb = (n0 + lm < p.D) ? sp.rot + (size_t)(n0 + lm) * p.D : nullptr;
+  float va[8], vb[8];
+  auto load = [&](int k0) {
+    const int j0 = k0 + lk;
+    if constexpr (VEC) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+      for (int h = 0; h < 2; ++h) {
+        const int j = j0 + 4 * h;
+        float4 x4 = make_float4(0.f, 0.f, 0.f, 0.f), r4 = x4;
+        if (j < p.D) {
+          const float4 o4 = *reinterpret_cast<const float4*>(sp.shift + j);
+          if (xa) {
+            x4 = *reinterpret_cast<const float4*>(xa + j);
+            x4 = make_float4(__fsub_rn(x4.x, o4.x), __fsub_rn(x4.y, o4.y), __fsub_rn(x4.z, o4.z), __fsub_rn(x4.w, o4.w));
+          }
+          if (rb) r4 = *reinterpret_cast<const float4*>(rb + j);
+        }
+        va[4 * h + 0] = x4.x; va[4 * h + 1] = x4.y; va[4 * h + 2] = x4.z; va[4 * h + 3] = x4.w;
+        vb[4 * h + 0] = r4.x; vb[4 * h + 1] = r4.y; vb[4 * h + 2] = r4.z; vb[4 * h + 3] = r4.w;
+      }
+    } else {
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        va[u] = (xa && j < p.D) ? __fsub_rn(xa[j], sp.shift[j]) : 0.0f;
+        vb[u] = (rb && j < p.D) ? rb[j] : 0.0f;
+      }
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      As[buf][lk + u][lm] = va[u];
+      Bs[buf][lk + u][lm] = vb[u];
+    }
+  };
 
-  const int lr = t >> 2, lc = (t & 3) * 8;        // loader: row lr, 8 consecutive k from lc
-  for (int k0 = 0; k0 < p.D; k0 += kSrKStep) {
-    {
-      const float* rp = rowp[lr];
-      float va[8], vb[8];
+  float acc[8][8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = k0 + lc + u;
-        va[u] = (rp && j < p.D) ? __fsub_rn(rp[j], sp.shift[j]) : 0.0f;
-        const int n = n0 + lr;
-        vb[u] = (n < p.D && j < p.D) ? sp.rot[(size_t)n * p.D + j] : 0.0f;
-      }
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        As[lc + u][lr] = va[u];
-        Bs[lc + u][lr] = vb[u];
-      }
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < p.D; k0 += kGbK) {
+    const bool more = k0 + kGbK < p.D;
+    if (more) load(k0 + kGbK);
+#pragma unroll
+    for (int kk = 0; kk < kGbK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kSrKStep; ++kk) {
-      const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float ar[4] = {av.x, av.y, av.z, av.w};
-      const float br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
-    }
-    __syncthreads();
+    buf ^= 1;
   }
 
-  // epilogue: g(z) and w|z| over this thread's 4 columns, then over the tile's 64
+  float* pg = sp.part_g;
+  float* pw = sp.part_w;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    float sg = 0.0f, sw = 0.0f;
+  for (int a = 0; a < 8; ++a) {
+    const int e = r0 + ty * 8 + a;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int n = n0 + tx * 4 + b;
-      if (n < p.D) {
-        const float w = sr_weight(sp.obj, n, p.ell_k);
-        sg += sr_g(sp.obj, acc[a][b], w);
-        sw = fmaf(w, fabsf(acc[a][b]), sw);
+    for (int h = 0; h < 2; ++h) {
+      const float z[4] = {acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]};
+      const int c0 = n0 + 64 * h;
+      float sg, sw;
+      sr_tile_reduce(sp, z, c0 + tx * 4, sg, sw);
+      if (tx == 0 && e < p.N && c0 < p.D) {
+        pg[(size_t)e * sp.nct2 + (c0 >> 6)] = sg;
+        pw[(size_t)e * sp.nct2 + (c0 >> 6)] = sw;
       }
     }
+  }
+}
+
+// The ambiguous entries (mode 2): 16 entries x 64 columns per tile, 64
+// threads (4 rows x 4 columns each), K in steps of 32; a fixed grid walks
+// the entry tiles, so a short list uses many CTAs and an empty one none.
+constexpr int kGsM = 16, kGsK = 32, kGsThreads = 64;
+
+__global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
+  const GenParams& p = sp.g;
+  __shared__ __align__(16) float As[kGsK][kGsM + 4];
+  __shared__ __align__(16) float Bs[kGsK][kSrTile + 4];
+  __shared__ const float* rowp[kGsM];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int n0 = blockIdx.x * kSrTile;
+  const long long gen = p.st->gen;
+  const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
+  const int nrows = (int)*sp.amb_count;
+  for (int r0 = blockIdx.y * kGsM; r0 < nrows; r0 += gridDim.y * kGsM) {
+    __syncthreads();                                // rowp and the stages are reused
+    if (t < kGsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
+    __syncthreads();
+    float acc[4][4];
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      sg += __shfl_xor_sync(0xFFFFFFFFu, sg, o);
-      sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    for (int k0 = 0; k0 < p.D; k0 += kGsK) {
+      {
+        const int lr = t >> 2, lc = (t & 3) * 8;    // A: 16 rows x 32 k, 8 each
+        const float* rp = rowp[lr];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = k0 + lc + u;
+          As[lc + u][lr] = (rp && j < p.D) ? __fsub_rn(rp[j], sp.shift[j]) : 0.0f;
+        }
+        const int n = n0 + t;                       // B: 64 columns x 32 k, one column each
+        const float* rb = (n < p.D) ? sp.rot + (size_t)n * p.D : nullptr;
+#pragma unroll 8
+        for (int u = 0; u < kGsK; ++u) {
+          const int j = k0 + u;
+          Bs[u][t] = (rb && j < p.D) ? rb[j] : 0.0f;
+        }
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < kGsK; ++kk) {
+        const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        const float ar[4] = {av.x, av.y, av.z, av.w};
+        const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+      }
+      __syncthreads();
     }
-    const int e = r0 + ty * 4 + a;
-    if (tx == 0 && e < nrows) {
-      float* pg = (mode == 2) ? sp.part2_g : sp.part_g;
-      float* pw = (mode == 2) ? sp.part2_w : sp.part_w;
-      pg[(size_t)e * gridDim.x + blockIdx.x] = sg;   // gridDim.x = nct2 (= nct on the FP32 path)
-      pw[(size_t)e * gridDim.x + blockIdx.x] = sw;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int e = r0 + ty * 4 + a;
+      float sg, sw;
+      sr_tile_reduce(sp, acc[a], n0 + tx * 4, sg, sw);
+      if (tx == 0 && e < nrows) {
+        sp.part2_g[(size_t)e * sp.nct2 + blockIdx.x] = sg;
+        sp.part2_w[(size_t)e * sp.nct2 + blockIdx.x] = sw;
+      }
     }
   }
 }
@@ -400,8 +523,15 @@ cudaError_t launch_sr_trial(int xo, int vidx, const SrParams& sp, int block, cud
 }
 
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
-  const dim3 grid((unsigned)sp.nct2, (unsigned)((max_rows + kSrTile - 1) / kSrTile));
-  sr_gemm_fp32_kernel<<<grid, 256, 0, s>>>(sp, mode);
+  if (mode == 2) {
+    const int tiles = (max_rows + kGsM - 1) / kGsM;
+    const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 64)));
+    sr_gemm_fp32_list_kernel<<<grid, kGsThreads, 0, s>>>(sp);
+    return cudaGetLastError();
+  }
+  const dim3 grid((unsigned)((sp.g.D + kGbN - 1) / kGbN), (unsigned)((max_rows + kGbM - 1) / kGbM));
+  if (sp.g.D % 4 == 0) sr_gemm_fp32_kernel<true><<<grid, 256, 0, s>>>(sp, mode);
+  else sr_gemm_fp32_kernel<false><<<grid, 256, 0, s>>>(sp, mode);
   return cudaGetLastError();
 }
 
