@@ -298,69 +298,122 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
   }
 }
 
-// The ambiguous entries (mode 2): 16 entries x 64 columns per tile, 64
-// threads (4 rows x 4 columns each), K in steps of 32; a fixed grid walks
-// the entry tiles, so a short list uses many CTAs and an empty one none.
-constexpr int kGsM = 16, kGsK = 32, kGsThreads = 64;
+// The ambiguous entries (mode 2): 16 entries x 128 columns per tile, 128
+// threads, 2 rows x (2 x 4) columns each (the column layout of the kernel
+// above), K in steps of 16, double-buffered with register prefetch; a fixed
+// grid walks the entry tiles, so a short list still spreads over the SMs.
+constexpr int kGsM = 16, kGsThreads = 128, kGsLdA = kGsM + 4;
 
+template <bool VEC>
 __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
   const GenParams& p = sp.g;
-  __shared__ __align__(16) float As[kGsK][kGsM + 4];
-  __shared__ __align__(16) float Bs[kGsK][kSrTile + 4];
+  __shared__ __align__(16) float As[2][kGbK][kGsLdA];
+  __shared__ __align__(16) float Bs[2][kGbK][kGbLd];
   __shared__ const float* rowp[kGsM];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int n0 = blockIdx.x * kSrTile;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows 2 ty, 2 ty + 1
+  const int n0 = blockIdx.x * kGbN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
+  // loaders: A, threads 0..63: row q >> 2, k (q & 3) * 4; B, 4 per thread:
+  // column q >> 2, k (q & 3) * 4 for q = t + 128 i
   for (int r0 = blockIdx.y * kGsM; r0 < nrows; r0 += gridDim.y * kGsM) {
     __syncthreads();                                // rowp and the stages are reused
     if (t < kGsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
     __syncthreads();
-    float acc[4][4];
+    const float* xa = (t < 64) ? rowp[t >> 2] : nullptr;
+    float va[4], vb[4][4];
+    auto load = [&](int k0) {
+      const int jk = k0 + (t & 3) * 4;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int u = 0; u < 4; ++u) va[u] = 0.0f;
+      if (xa) {
+        if constexpr (VEC) {
+          if (jk < p.D) {
+            const float4 x4 = *reinterpret_cast<const float4*>(xa + jk);
+            const float4 o4 = *reinterpret_cast<const float4*>(sp.shift + jk);
+            va[0] = __fsub_rn(x4.x, o4.x); va[1] = __fsub_rn(x4.y, o4.y);
+            va[2] = __fsub_rn(x4.z, o4.z); va[3] = __fsub_rn(x4.w, o4.w);
+          }
+        } else {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-    for (int k0 = 0; k0 < p.D; k0 += kGsK) {
-      {
-        const int lr = t >> 2, lc = (t & 3) * 8;    // A: 16 rows x 32 k, 8 each
-        const float* rp = rowp[lr];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int j = k0 + lc + u;
-          As[lc + u][lr] = (rp && j < p.D) ? __fsub_rn(rp[j], sp.shift[j]) : 0.0f;
-        }
-        const int n = n0 + t;                       // B: 64 columns x 32 k, one column each
-        const float* rb = (n < p.D) ? sp.rot + (size_t)n * p.D : nullptr;
-#pragma unroll 8
-        for (int u = 0; u < kGsK; ++u) {
-          const int j = k0 + u;
-          Bs[u][t] = (rb && j < p.D) ? rb[j] : 0.0f;
+          for (int u = 0; u < 4; ++u)
+            if (jk + u < p.D) va[u] = __fsub_rn(xa[jk + u], sp.shift[jk + u]);
         }
       }
-      __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < kGsK; ++kk) {
-        const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-        const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-        const float ar[4] = {av.x, av.y, av.z, av.w};
-        const float br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 4; ++i) {
+        const int n = n0 + ((t + kGsThreads * i) >> 2);
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+        for (int u = 0; u < 4; ++u) vb[i][u] = 0.0f;
+        if (n < p.D) {
+          const float* rb = sp.rot + (size_t)n * p.D;
+          if constexpr (VEC) {
+            if (jk < p.D) {
+              const float4 r4 = *reinterpret_cast<const float4*>(rb + jk);
+              vb[i][0] = r4.x; vb[i][1] = r4.y; vb[i][2] = r4.z; vb[i][3] = r4.w;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (jk + u < p.D) vb[i][u] = rb[jk + u];
+          }
+        }
       }
+    };
+    auto store = [&](int buf) {
+      const int kc = (t & 3) * 4;
+      if (t < 64) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) As[buf][kc + u][t >> 2] = va[u];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Bs[buf][kc + u][(t + kGsThreads * i) >> 2] = vb[i][u];
+    };
+
+    float acc[2][8];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < p.D; k0 += kGbK) {
+      const bool more = k0 + kGbK < p.D;
+      if (more) load(k0 + kGbK);
+#pragma unroll
+      for (int kk = 0; kk < kGbK; ++kk) {
+        const float2 av = *reinterpret_cast<const float2*>(&As[buf][kk][ty * 2]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+        const float ar[2] = {av.x, av.y};
+        const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+      }
+      if (more) store(buf ^ 1);
       __syncthreads();
+      buf ^= 1;
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int e = r0 + ty * 4 + a;
-      float sg, sw;
-      sr_tile_reduce(sp, acc[a], n0 + tx * 4, sg, sw);
-      if (tx == 0 && e < nrows) {
-        sp.part2_g[(size_t)e * sp.nct2 + blockIdx.x] = sg;
-        sp.part2_w[(size_t)e * sp.nct2 + blockIdx.x] = sw;
+    for (int a = 0; a < 2; ++a) {
+      const int e = r0 + ty * 2 + a;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float z[4] = {acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]};
+        const int c0 = n0 + 64 * h;
+        float sg, sw;
+        sr_tile_reduce(sp, z, c0 + tx * 4, sg, sw);
+        if (tx == 0 && e < nrows && c0 < p.D) {
+          sp.part2_g[(size_t)e * sp.nct2 + (c0 >> 6)] = sg;
+          sp.part2_w[(size_t)e * sp.nct2 + (c0 >> 6)] = sw;
+        }
       }
     }
   }
@@ -523,13 +576,15 @@ cudaError_t launch_sr_trial(int xo, int vidx, const SrParams& sp, int block, cud
 }
 
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
+  const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
   if (mode == 2) {
     const int tiles = (max_rows + kGsM - 1) / kGsM;
-    const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 64)));
-    sr_gemm_fp32_list_kernel<<<grid, kGsThreads, 0, s>>>(sp);
+    const dim3 grid(gx, (unsigned)std::max(1, std::min(tiles, 128)));
+    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true><<<grid, kGsThreads, 0, s>>>(sp);
+    else sr_gemm_fp32_list_kernel<false><<<grid, kGsThreads, 0, s>>>(sp);
     return cudaGetLastError();
   }
-  const dim3 grid((unsigned)((sp.g.D + kGbN - 1) / kGbN), (unsigned)((max_rows + kGbM - 1) / kGbM));
+  const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
   if (sp.g.D % 4 == 0) sr_gemm_fp32_kernel<true><<<grid, 256, 0, s>>>(sp, mode);
   else sr_gemm_fp32_kernel<false><<<grid, 256, 0, s>>>(sp, mode);
   return cudaGetLastError();
