@@ -74,10 +74,9 @@ cudaError_t launch_sr_trial(int xo, int vidx, const SrParams& sp, int block, cud
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s);
 cudaError_t launch_sr_select(const SrParams& sp, const SrBound& b, cudaStream_t s);
 cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s);
-cudaError_t launch_sr_close(const SrParams& sp, cudaStream_t s);
 cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s);
 cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, cudaStream_t s);
-cudaError_t launch_sr_incumbent(const SrParams& sp, int every, cudaStream_t s);
+cudaError_t launch_sr_finish(const SrParams& sp, int every, bool close, cudaStream_t s);
 // tcgen05 BF16 product (split operands) with the fitness epilogue; requires
 // D % 256 == 0. sr_tc_supported tells whether this build and device have it.
 cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s);

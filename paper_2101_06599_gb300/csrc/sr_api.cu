@@ -136,8 +136,7 @@ cudaError_t sr_launch_generation(de_ctx* c, const GenParams& p) {
     e = launch_sr_gemm_fp32(sp, 2, 2 * c->N, c->stream);
     if (e == cudaSuccess) e = launch_sr_resolve(sp, c->stream);
   }
-  if (e == cudaSuccess) e = launch_sr_close(sp, c->stream);
-  if (e == cudaSuccess) e = launch_sr_incumbent(sp, c->incumbent_every, c->stream);
+  if (e == cudaSuccess) e = launch_sr_finish(sp, c->incumbent_every, true, c->stream);
   return e;
 }
 
@@ -148,7 +147,7 @@ int sr_evaluate(de_ctx* c) {
   if (e == cudaSuccess) e = launch_sr_gemm_fp32(sp, 1, c->N, c->stream);
   if (e == cudaSuccess) e = launch_sr_store_eval(sp, c->stream);
   if (e == cudaSuccess) e = launch_close_eval(c->p, c->stream);
-  if (e == cudaSuccess) e = launch_sr_incumbent(sp, 1, c->stream);
+  if (e == cudaSuccess) e = launch_sr_finish(sp, 1, false, c->stream);
   return cuda_status(e);
 }
 

@@ -8,7 +8,8 @@
 // tcgen05), then sr_select_kernel (strict '<' decisions, or interval
 // decisions with a per-row error bound on the BF16 path: rows whose interval
 // straddles the parent's go to an FP32 re-evaluation with this file's GEMM
-// and sr_resolve_kernel), then sr_close_kernel.
+// and sr_resolve_kernel), then sr_finish_kernel (FP64 incumbent when due, and
+// the close of the generation).
 //
 // The FP32 GEMM accumulates every z_ik in one fixed order (j ascending, one
 // FMA per term, one thread per element) and reduces g(z) over each 64-column
@@ -25,118 +26,136 @@
 namespace de {
 
 // ---------------------------------------------------------------------------
-// trials
+// trials: one warp per row, 8 rows per CTA. The warp issues its first parent
+// loads, lane 0 draws the donors and L (Philox, slot lookups) and broadcasts
+// them, then the lanes stream the row 4 genes at a time: crossover mask,
+// mutation and clip of masked genes, the trial into the other slot, a = u - o
+// with |a|^2, and on the BF16 path the split operands as packed 8-byte
+// stores. Mask counts go to the state with one atomic per CTA.
 // ---------------------------------------------------------------------------
-template <int XO, int V>
-__global__ void __launch_bounds__(kMaxThreads) sr_trial_kernel(const __grid_constant__ SrParams sp) {
+constexpr int kTrialWarps = 8, kTrialUnroll = 4;
+
+template <int XO>
+__global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid_constant__ SrParams sp) {
   const GenParams& p = sp.g;
-  __shared__ RowShared sh;
-  __shared__ float red[4][32];
-  const int i = blockIdx.x;
-  const int t = threadIdx.x, T = blockDim.x;
-  const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
+  __shared__ int wcnt[kTrialWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * kTrialWarps + warp;
   const long long gen = p.st->gen;
   const uint32_t g = (uint32_t)gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
-  const int si = slot_in[i];
-  const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)i * p.pitch);
-
-  float4 x[V];
+  int Lrow = 0;
+  if (i < p.N) {                                   // warp-uniform
+    const int si = slot_in[i];
+    const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)i * p.pitch);
+    float4* trow = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
+    float4 x[kTrialUnroll];
 #pragma unroll
-  for (int k = 0; k < V; ++k) {
-    const int q = t + k * T;
-    x[k] = (q < p.D4) ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  }
-  if (t == 0) {
-    RowDraws d;
-    draw_donors(p, g, i, d);
-    if constexpr (XO == kNec) d.L = nec_length(p, g, i);
-    else if constexpr (XO == kExp) d.L = exp_walk_length(p, g, i);
-    else d.L = 0;
-    sh.r1 = d.r1; sh.r2 = d.r2; sh.r3 = d.r3; sh.jrand = d.jrand; sh.L = d.L;
-    sh.d1 = reinterpret_cast<const float4*>((slot_in[d.r1] ? p.pop1 : p.pop0) + (size_t)d.r1 * p.pitch);
-    sh.d2 = reinterpret_cast<const float4*>((slot_in[d.r2] ? p.pop1 : p.pop0) + (size_t)d.r2 * p.pitch);
-    sh.d3 = reinterpret_cast<const float4*>((slot_in[d.r3] ? p.pop1 : p.pop0) + (size_t)d.r3 * p.pitch);
-  }
-  __syncthreads();
-  const int jrand = sh.jrand, L = sh.L;
-  int cnt = 0;
-  float nrm = 0.0f;
-  float4* trow = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
+    for (int u = 0; u < kTrialUnroll; ++u) {
+      const int q = lane + 32 * u;
+      x[u] = (q < p.D4) ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    RowDraws d{};
+    unsigned long long pd1 = 0, pd2 = 0, pd3 = 0;
+    if (lane == 0) {
+      draw_donors(p, g, i, d);
+      if constexpr (XO == kNec) d.L = nec_length(p, g, i);
+      else if constexpr (XO == kExp) d.L = exp_walk_length(p, g, i);
+      else d.L = 0;
+      pd1 = (unsigned long long)((slot_in[d.r1] ? p.pop1 : p.pop0) + (size_t)d.r1 * p.pitch);
+      pd2 = (unsigned long long)((slot_in[d.r2] ? p.pop1 : p.pop0) + (size_t)d.r2 * p.pitch);
+      pd3 = (unsigned long long)((slot_in[d.r3] ? p.pop1 : p.pop0) + (size_t)d.r3 * p.pitch);
+    }
+    const int jrand = __shfl_sync(0xFFFFFFFFu, d.jrand, 0);
+    const int L = __shfl_sync(0xFFFFFFFFu, d.L, 0);
+    const float4* d1 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd1, 0));
+    const float4* d2 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd2, 0));
+    const float4* d3 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd3, 0));
+    int cnt = 0;
+    float nrm = 0.0f;
+    for (int q0 = 0; q0 < p.D4; q0 += 32 * kTrialUnroll) {
+      if (q0 > 0) {
 #pragma unroll
-  for (int k = 0; k < V; ++k) {
-    const int q = t + k * T;
-    if (q < p.D4) {
-      const int j0 = 4 * q;
-      unsigned m = 0u;
-      if constexpr (XO == kBin) {
-        const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
-        m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == jrand) ? 1u : 0u;
-        m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == jrand) ? 2u : 0u;
-        m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == jrand) ? 4u : 0u;
-        m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == jrand) ? 8u : 0u;
-      } else {
-        int dd = j0 - jrand;
-        if (dd < 0) dd += p.D;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int de = dd + e;
-          if (de >= p.D) de -= p.D;
-          m |= (de < L) ? (1u << e) : 0u;
+        for (int u = 0; u < kTrialUnroll; ++u) {
+          const int q = q0 + lane + 32 * u;
+          x[u] = (q < p.D4) ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
       }
-      m &= (1u << min(4, p.D - j0)) - 1u;
-      if (m) {
-        const float4 a1 = ld_ro(sh.d1 + q), a2 = ld_ro(sh.d2 + q), a3 = ld_ro(sh.d3 + q);
-        if (m & 1u) x[k].x = clip_box(mutate(a1.x, a2.x, a3.x, p.F), p.lo, p.hi);
-        if (m & 2u) x[k].y = clip_box(mutate(a1.y, a2.y, a3.y, p.F), p.lo, p.hi);
-        if (m & 4u) x[k].z = clip_box(mutate(a1.z, a2.z, a3.z, p.F), p.lo, p.hi);
-        if (m & 8u) x[k].w = clip_box(mutate(a1.w, a2.w, a3.w, p.F), p.lo, p.hi);
-      }
-      if constexpr (XO == kBin) cnt += __popc(m);
-      st_stream(trow + q, x[k]);
-      if (p.dbg_trial) reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch)[q] = x[k];
-      // a = u - o, its norm, and the split BF16 operands
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int j = j0 + e;
-        if (j < p.D) {
-          const float a = __fsub_rn(lane_of(x[k], e), sp.shift[j]);
-          nrm = fmaf(a, a, nrm);
-          if (sp.prec != 0) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(a);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(a, __bfloat162float(hi)));
-            sp.a_hi[(size_t)i * p.D + j] = __bfloat16_as_ushort(hi);
-            sp.a_lo[(size_t)i * p.D + j] = __bfloat16_as_ushort(lo);
+      for (int u = 0; u < kTrialUnroll; ++u) {
+        const int q = q0 + lane + 32 * u;
+        if (q >= p.D4) continue;
+        const int j0 = 4 * q;
+        unsigned m = 0u;
+        if constexpr (XO == kBin) {
+          const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
+          m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == jrand) ? 1u : 0u;
+          m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == jrand) ? 2u : 0u;
+          m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == jrand) ? 4u : 0u;
+          m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == jrand) ? 8u : 0u;
+        } else {
+          int dd = j0 - jrand;
+          if (dd < 0) dd += p.D;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            int de = dd + e;
+            if (de >= p.D) de -= p.D;
+            m |= (de < L) ? (1u << e) : 0u;
           }
         }
+        m &= (1u << min(4, p.D - j0)) - 1u;
+        float4 v = x[u];
+        if (m) {
+          const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
+          if (m & 1u) v.x = clip_box(mutate(a1.x, a2.x, a3.x, p.F), p.lo, p.hi);
+          if (m & 2u) v.y = clip_box(mutate(a1.y, a2.y, a3.y, p.F), p.lo, p.hi);
+          if (m & 4u) v.z = clip_box(mutate(a1.z, a2.z, a3.z, p.F), p.lo, p.hi);
+          if (m & 8u) v.w = clip_box(mutate(a1.w, a2.w, a3.w, p.F), p.lo, p.hi);
+        }
+        if constexpr (XO == kBin) cnt += __popc(m);
+        st_stream(trow + q, v);
+        if (p.dbg_trial) reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch)[q] = v;
+        float a[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = j0 + e;
+          a[e] = (j < p.D) ? __fsub_rn(lane_of(v, e), sp.shift[j]) : 0.0f;
+          nrm = fmaf(a[e], a[e], nrm);
+        }
+        if (sp.prec != 0) {                        // D % 256 == 0 on this path: 8-byte aligned
+          uint32_t h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(a[e]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(a[e], __bfloat162float(hi)));
+            h[e] = __bfloat16_as_ushort(hi);
+            l[e] = __bfloat16_as_ushort(lo);
+          }
+          *reinterpret_cast<uint2*>(sp.a_hi + (size_t)i * p.D + j0) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+          *reinterpret_cast<uint2*>(sp.a_lo + (size_t)i * p.D + j0) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, o);
+      cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    }
+    Lrow = (XO == kBin) ? cnt : L;
+    if (lane == 0) {
+      sp.norm2[i] = nrm;
+      if (p.dbg_draws) {
+        int* o = p.dbg_draws + 5 * (size_t)i;
+        o[0] = d.r1; o[1] = d.r2; o[2] = d.r3; o[3] = d.jrand; o[4] = Lrow;
       }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, o);
-    cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-  }
-  if (lane == 0) {
-    red[0][warp] = nrm;
-    red[1][warp] = __int_as_float(cnt);
-  }
+  if (lane == 0) wcnt[warp] = Lrow;
   __syncthreads();
-  if (t == 0) {
-    float n2 = 0.0f;
-    int c = 0;
-    for (int w = 0; w < nwarps; ++w) {
-      n2 += red[0][w];
-      c += __float_as_int(red[1][w]);
-    }
-    sp.norm2[i] = n2;
-    const int Lrow = (XO == kBin) ? c : L;
-    atomicAdd(&p.st->masked, (unsigned long long)Lrow);
-    if (p.dbg_draws) {
-      int* o = p.dbg_draws + 5 * (size_t)i;
-      o[0] = sh.r1; o[1] = sh.r2; o[2] = sh.r3; o[3] = sh.jrand; o[4] = Lrow;
-    }
+  if (threadIdx.x == 0) {
+    unsigned long long c = 0;
+    for (int w = 0; w < kTrialWarps; ++w) c += (unsigned long long)wcnt[w];
+    atomicAdd(&p.st->masked, c);
   }
 }
 
@@ -529,17 +548,6 @@ __global__ void sr_resolve_kernel(const __grid_constant__ SrParams sp) {
   }
 }
 
-// Close the generation (one thread); clears the ambiguous list for the next.
-__global__ void sr_close_kernel(DevState* st, unsigned* amb_count) {
-  const float bf = from_ordered_bits((uint32_t)(st->best_key >> 32));
-  if (bf < st->best_f) {
-    st->best_f = bf;
-    st->best_gen = st->gen + 1;
-  }
-  st->gen = st->gen + 1;
-  *amb_count = 0u;
-}
-
 // Initial evaluation (always the FP32 product, whose partials have nct2
 // columns): fit = sum of partials, fit_err = 0, best key.
 __global__ void sr_store_eval_kernel(const __grid_constant__ SrParams sp) {
@@ -555,24 +563,12 @@ __global__ void sr_store_eval_kernel(const __grid_constant__ SrParams sp) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int XO>
-static cudaError_t sr_trial_xo(int vidx, const SrParams& sp, int block, cudaStream_t s) {
-  const dim3 grid((unsigned)sp.g.N), blk((unsigned)block);
-  switch (vidx) {
-    case 0: sr_trial_kernel<XO, 1><<<grid, blk, 0, s>>>(sp); break;
-    case 1: sr_trial_kernel<XO, 2><<<grid, blk, 0, s>>>(sp); break;
-    case 2: sr_trial_kernel<XO, 4><<<grid, blk, 0, s>>>(sp); break;
-    case 3: sr_trial_kernel<XO, 8><<<grid, blk, 0, s>>>(sp); break;
-    case 4: sr_trial_kernel<XO, 16><<<grid, blk, 0, s>>>(sp); break;
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_sr_trial(int xo, int /*vidx*/, const SrParams& sp, int /*block*/, cudaStream_t s) {
+  const unsigned grid = (unsigned)((sp.g.N + kTrialWarps - 1) / kTrialWarps);
+  if (xo == kBin) sr_trial_kernel<kBin><<<grid, kTrialWarps * 32, 0, s>>>(sp);
+  else if (xo == kExp) sr_trial_kernel<kExp><<<grid, kTrialWarps * 32, 0, s>>>(sp);
+  else sr_trial_kernel<kNec><<<grid, kTrialWarps * 32, 0, s>>>(sp);
   return cudaGetLastError();
-}
-
-cudaError_t launch_sr_trial(int xo, int vidx, const SrParams& sp, int block, cudaStream_t s) {
-  if (xo == kBin) return sr_trial_xo<kBin>(vidx, sp, block, s);
-  if (xo == kExp) return sr_trial_xo<kExp>(vidx, sp, block, s);
-  return sr_trial_xo<kNec>(vidx, sp, block, s);
 }
 
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
@@ -600,11 +596,6 @@ cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sr_close(const SrParams& sp, cudaStream_t s) {
-  sr_close_kernel<<<1, 1, 0, s>>>(sp.g.st, sp.amb_count);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s) {
   sr_store_eval_kernel<<<(sp.g.N + 255) / 256, 256, 0, s>>>(sp);
   return cudaGetLastError();
@@ -629,38 +620,47 @@ cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* l
   return cudaGetLastError();
 }
 
-// The incumbent in FP64 (the only FP64 arithmetic on the GPU): every `every`
-// generations, after the generation closed, the best row's objective is
-// recomputed as z = R (x - o) and sum g(z) in FP64 and kept in the state.
-// One warp per z_k (coalesced reads of row k of R, lanes over j, a fixed
-// shuffle tree), g(z_k) to inc_part[k]; the last CTA to finish sums
-// inc_part in a fixed order, so the value does not depend on scheduling.
+// The incumbent in FP64 (the only FP64 arithmetic on the GPU), fused with
+// the close of the generation. Generation g' = g + 1 when closing (g itself
+// for the initial evaluation); every `every` generations the best row's
+// objective is recomputed as z = R (x - o) and sum g(z) in FP64: one warp per
+// z_k (coalesced reads of row k of R, lanes over j, a fixed shuffle tree),
+// g(z_k) to inc_part[k]. The last CTA to finish (a ticket) sums inc_part in a
+// fixed order, so the value does not depend on scheduling, and then closes
+// the generation: best value and generation, the counter, the ambiguous list.
+// Every CTA reads the state before it takes its ticket, and only the last
+// one writes it.
 constexpr int kIncWarps = 8;
 
-__global__ void __launch_bounds__(kIncWarps * 32) sr_incumbent_kernel(const __grid_constant__ SrParams sp, int every) {
+__global__ void __launch_bounds__(kIncWarps * 32) sr_finish_kernel(const __grid_constant__ SrParams sp, int every,
+                                                                  int close) {
   const GenParams& p = sp.g;
   const long long gen = p.st->gen;
-  if (every <= 0 || gen % every != 0) return;
+  const long long gnext = close ? gen + 1 : gen;
+  const bool due = every > 0 && gnext % every == 0;
+  if (!due && !close) return;                       // uniform across the grid
   const int idx = (int)(uint32_t)(p.st->best_key & 0xFFFFFFFFull);
-  if (idx < 0 || idx >= p.N) return;                // uniform across the grid: no CTA counts
-  const int si = p.slots[(size_t)(gen & 1) * p.N + idx];
-  const float* x = (si ? p.pop1 : p.pop0) + (size_t)idx * p.pitch;
+  const bool have = due && idx >= 0 && idx < p.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k = blockIdx.x * kIncWarps + warp;
-  if (k < p.D) {
-    const float* r = sp.rot + (size_t)k * p.D;
-    double z = 0.0;
-    for (int j = lane; j < p.D; j += 32) z = fma((double)r[j], (double)x[j] - (double)sp.shift[j], z);
-    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, o);
-    if (lane == 0) {
-      double gk;
-      if (sp.obj == kSrElliptic) {
-        const double c = (p.D > 1) ? exp2((double)k * (6.0 * 3.321928094887362 / (double)(p.D - 1))) : 1.0;
-        gk = c * z * z;
-      } else {
-        gk = z * z - 10.0 * cos(2.0 * 3.141592653589793 * z) + 10.0;
+  if (have) {
+    const int si = p.slots[(size_t)(gnext & 1) * p.N + idx];
+    const float* x = (si ? p.pop1 : p.pop0) + (size_t)idx * p.pitch;
+    const int k = blockIdx.x * kIncWarps + warp;
+    if (k < p.D) {
+      const float* r = sp.rot + (size_t)k * p.D;
+      double z = 0.0;
+      for (int j = lane; j < p.D; j += 32) z = fma((double)r[j], (double)x[j] - (double)sp.shift[j], z);
+      for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, o);
+      if (lane == 0) {
+        double gk;
+        if (sp.obj == kSrElliptic) {
+          const double c = (p.D > 1) ? exp2((double)k * (6.0 * 3.321928094887362 / (double)(p.D - 1))) : 1.0;
+          gk = c * z * z;
+        } else {
+          gk = z * z - 10.0 * cos(2.0 * 3.141592653589793 * z) + 10.0;
+        }
+        sp.inc_part[k] = gk;
       }
-      sp.inc_part[k] = gk;
     }
   }
   __shared__ unsigned ticket;
@@ -671,22 +671,36 @@ __global__ void __launch_bounds__(kIncWarps * 32) sr_incumbent_kernel(const __gr
   __syncthreads();
   if (ticket != gridDim.x - 1) return;
   __threadfence();
-  double acc = 0.0;
-  for (int q = threadIdx.x; q < p.D; q += blockDim.x) acc += __ldcg(sp.inc_part + q);
-  red[threadIdx.x] = acc;
-  __syncthreads();
+  if (have) {
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < p.D; q += blockDim.x) acc += __ldcg(sp.inc_part + q);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double f = 0.0;
-    for (int w = 0; w < (int)blockDim.x; ++w) f += red[w];
-    p.st->incumbent_f64 = f;
-    p.st->incumbent_gen = gen;
+    if (have) {
+      double f = 0.0;
+      for (int w = 0; w < (int)blockDim.x; ++w) f += red[w];
+      p.st->incumbent_f64 = f;
+      p.st->incumbent_gen = gnext;
+    }
+    if (close) {
+      DevState* st = p.st;
+      const float bf = from_ordered_bits((uint32_t)(st->best_key >> 32));
+      if (bf < st->best_f) {
+        st->best_f = bf;
+        st->best_gen = gnext;
+      }
+      st->gen = gnext;
+      *sp.amb_count = 0u;
+    }
     *sp.inc_count = 0u;
   }
 }
 
-cudaError_t launch_sr_incumbent(const SrParams& sp, int every, cudaStream_t s) {
+cudaError_t launch_sr_finish(const SrParams& sp, int every, bool close, cudaStream_t s) {
   const unsigned grid = (unsigned)((sp.g.D + kIncWarps - 1) / kIncWarps);
-  sr_incumbent_kernel<<<grid, kIncWarps * 32, 0, s>>>(sp, every);
+  sr_finish_kernel<<<grid, kIncWarps * 32, 0, s>>>(sp, every, close ? 1 : 0);
   return cudaGetLastError();
 }
 
