@@ -317,31 +317,32 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
   }
 }
 
-// The ambiguous entries (mode 2): 16 entries x 128 columns per tile, 128
-// threads, 2 rows x (2 x 4) columns each (the column layout of the kernel
-// above), K in steps of 16, double-buffered with register prefetch; a fixed
-// grid walks the entry tiles, so a short list still spreads over the SMs.
-constexpr int kGsM = 16, kGsThreads = 128, kGsLdA = kGsM + 4;
+// The ambiguous entries (mode 2): 16 entries x 64 columns per tile, 128
+// threads, 2 rows x 4 columns each (16 lanes x 4 columns cover the 64-column
+// tile as in the kernel above), K in steps of 16, double-buffered with
+// register prefetch; a fixed grid walks the entry tiles. A list of a few
+// hundred entries is a small product: narrow tiles keep enough warps per SM.
+constexpr int kGsM = 16, kGsN = 64, kGsThreads = 128, kGsLdA = kGsM + 4, kGsLdB = kGsN + 4;
 
 template <bool VEC>
 __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
   const GenParams& p = sp.g;
   __shared__ __align__(16) float As[2][kGbK][kGsLdA];
-  __shared__ __align__(16) float Bs[2][kGbK][kGbLd];
+  __shared__ __align__(16) float Bs[2][kGbK][kGsLdB];
   __shared__ const float* rowp[kGsM];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows 2 ty, 2 ty + 1
-  const int n0 = blockIdx.x * kGbN;
+  const int n0 = blockIdx.x * kGsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
-  // loaders: A, threads 0..63: row q >> 2, k (q & 3) * 4; B, 4 per thread:
+  // loaders: A, threads 0..63: row t >> 2, k (t & 3) * 4; B, 2 per thread:
   // column q >> 2, k (q & 3) * 4 for q = t + 128 i
   for (int r0 = blockIdx.y * kGsM; r0 < nrows; r0 += gridDim.y * kGsM) {
     __syncthreads();                                // rowp and the stages are reused
     if (t < kGsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
     __syncthreads();
     const float* xa = (t < 64) ? rowp[t >> 2] : nullptr;
-    float va[4], vb[4][4];
+    float va[4], vb[2][4];
     auto load = [&](int k0) {
       const int jk = k0 + (t & 3) * 4;
 #pragma unroll
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < 2; ++i) {
         const int n = n0 + ((t + kGsThreads * i) >> 2);
 #pragma unroll
         for (int u = 0; u < 4; ++u) vb[i][u] = 0.0f;
@@ -387,16 +388,16 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
         for (int u = 0; u < 4; ++u) As[buf][kc + u][t >> 2] = va[u];
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int u = 0; u < 4; ++u) Bs[buf][kc + u][(t + kGsThreads * i) >> 2] = vb[i][u];
     };
 
-    float acc[2][8];
+    float acc[2][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
     load(0);
     store(0);
     __syncthreads();
@@ -407,14 +408,13 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
 #pragma unroll
       for (int kk = 0; kk < kGbK; ++kk) {
         const float2 av = *reinterpret_cast<const float2*>(&As[buf][kk][ty * 2]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
         const float ar[2] = {av.x, av.y};
-        const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
       }
       if (more) store(buf ^ 1);
       __syncthreads();
@@ -423,16 +423,11 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
       const int e = r0 + ty * 2 + a;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float z[4] = {acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]};
-        const int c0 = n0 + 64 * h;
-        float sg, sw;
-        sr_tile_reduce(sp, z, c0 + tx * 4, sg, sw);
-        if (tx == 0 && e < nrows && c0 < p.D) {
-          sp.part2_g[(size_t)e * sp.nct2 + (c0 >> 6)] = sg;
-          sp.part2_w[(size_t)e * sp.nct2 + (c0 >> 6)] = sw;
-        }
+      float sg, sw;
+      sr_tile_reduce(sp, acc[a], n0 + tx * 4, sg, sw);
+      if (tx == 0 && e < nrows) {
+        sp.part2_g[(size_t)e * sp.nct2 + blockIdx.x] = sg;
+        sp.part2_w[(size_t)e * sp.nct2 + blockIdx.x] = sw;
       }
     }
   }
@@ -575,7 +570,7 @@ cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cuda
   const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
   if (mode == 2) {
     const int tiles = (max_rows + kGsM - 1) / kGsM;
-    const dim3 grid(gx, (unsigned)std::max(1, std::min(tiles, 128)));
+    const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 128)));
     if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true><<<grid, kGsThreads, 0, s>>>(sp);
     else sr_gemm_fp32_list_kernel<false><<<grid, kGsThreads, 0, s>>>(sp);
     return cudaGetLastError();
