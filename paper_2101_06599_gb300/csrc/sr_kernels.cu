@@ -319,51 +319,60 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 
 // The ambiguous entries (mode 2): 16 entries x 64 columns per tile, 128
 // threads, 2 rows x 4 columns each (16 lanes x 4 columns cover the 64-column
-// tile as in the kernel above), K in steps of 16, double-buffered with
+// tile as in the kernel above), K in steps of 64, double-buffered with
 // register prefetch; a fixed grid walks the entry tiles. A list of a few
-// hundred entries is a small product: narrow tiles keep enough warps per SM.
-constexpr int kGsM = 16, kGsN = 64, kGsThreads = 128, kGsLdA = kGsM + 4, kGsLdB = kGsN + 4;
+// hundred entries is a small product: narrow tiles keep enough warps per SM,
+// and long K steps cover the load latency with few warps.
+constexpr int kGsM = 16, kGsN = 64, kGsK = 64, kGsThreads = 128, kGsLdA = kGsM + 4, kGsLdB = kGsN + 4;
 
 template <bool VEC>
 __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
   const GenParams& p = sp.g;
-  __shared__ __align__(16) float As[2][kGbK][kGsLdA];
-  __shared__ __align__(16) float Bs[2][kGbK][kGsLdB];
+  __shared__ __align__(16) float As[2][kGsK][kGsLdA];
+  __shared__ __align__(16) float Bs[2][kGsK][kGsLdB];
   __shared__ const float* rowp[kGsM];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows 2 ty, 2 ty + 1
   const int n0 = blockIdx.x * kGsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
-  // loaders: A, threads 0..63: row t >> 2, k (t & 3) * 4; B, 2 per thread:
-  // column q >> 2, k (q & 3) * 4 for q = t + 128 i
+  // loaders, one 16-byte chunk (4 k) per item: A, 16 rows x 16 chunks, items
+  // q = t + 128 i (i < 2): row q & 15, chunk q >> 4; B, 64 columns x 16
+  // chunks, items q = t + 128 i (i < 8): column q & 63, chunk q >> 6 (a warp
+  // stores consecutive rows / columns of one chunk: no bank conflicts)
   for (int r0 = blockIdx.y * kGsM; r0 < nrows; r0 += gridDim.y * kGsM) {
     __syncthreads();                                // rowp and the stages are reused
     if (t < kGsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
     __syncthreads();
-    const float* xa = (t < 64) ? rowp[t >> 2] : nullptr;
-    float va[4], vb[2][4];
+    float va[2][4], vb[8][4];
     auto load = [&](int k0) {
-      const int jk = k0 + (t & 3) * 4;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) va[u] = 0.0f;
-      if (xa) {
-        if constexpr (VEC) {
-          if (jk < p.D) {
-            const float4 x4 = *reinterpret_cast<const float4*>(xa + jk);
-            const float4 o4 = *reinterpret_cast<const float4*>(sp.shift + jk);
-            va[0] = __fsub_rn(x4.x, o4.x); va[1] = __fsub_rn(x4.y, o4.y);
-            va[2] = __fsub_rn(x4.z, o4.z); va[3] = __fsub_rn(x4.w, o4.w);
+      for (int i = 0; i < 2; ++i) {
+        const int q = t + kGsThreads * i;
+        const float* xa = rowp[q & 15];
+        const int jk = k0 + (q >> 4) * 4;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) va[i][u] = 0.0f;
+        if (xa) {
+          if constexpr (VEC) {
+            if (jk < p.D) {
+              const float4 x4 = *reinterpret_cast<const float4*>(xa + jk);
+              const float4 o4 = *reinterpret_cast<const float4*>(sp.shift + jk);
+              va[i][0] = __fsub_rn(x4.x, o4.x); va[i][1] = __fsub_rn(x4.y, o4.y);
+              va[i][2] = __fsub_rn(x4.z, o4.z); va[i][3] = __fsub_rn(x4.w, o4.w);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (jk + u < p.D) va[i][u] = __fsub_rn(xa[jk + u], sp.shift[jk + u]);
           }
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (jk + u < p.D) va[u] = __fsub_rn(xa[jk + u], sp.shift[jk + u]);
         }
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int n = n0 + ((t + kGsThreads * i) >> 2);
+      for (int i = 0; i < 8; ++i) {
+        const int q = t + kGsThreads * i;
+        const int n = n0 + (q & 63);
+        const int jk = k0 + (q >> 6) * 4;
 #pragma unroll
         for (int u = 0; u < 4; ++u) vb[i][u] = 0.0f;
         if (n < p.D) {
@@ -382,15 +391,18 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
       }
     };
     auto store = [&](int buf) {
-      const int kc = (t & 3) * 4;
-      if (t < 64) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) As[buf][kc + u][t >> 2] = va[u];
+      for (int i = 0; i < 2; ++i) {
+        const int q = t + kGsThreads * i;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) As[buf][(q >> 4) * 4 + u][q & 15] = va[i][u];
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 8; ++i) {
+        const int q = t + kGsThreads * i;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) Bs[buf][kc + u][(t + kGsThreads * i) >> 2] = vb[i][u];
+        for (int u = 0; u < 4; ++u) Bs[buf][(q >> 6) * 4 + u][q & 63] = vb[i][u];
+      }
     };
 
     float acc[2][4];
@@ -402,11 +414,11 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
     store(0);
     __syncthreads();
     int buf = 0;
-    for (int k0 = 0; k0 < p.D; k0 += kGbK) {
-      const bool more = k0 + kGbK < p.D;
-      if (more) load(k0 + kGbK);
-#pragma unroll
-      for (int kk = 0; kk < kGbK; ++kk) {
+    for (int k0 = 0; k0 < p.D; k0 += kGsK) {
+      const bool more = k0 + kGsK < p.D;
+      if (more) load(k0 + kGsK);
+#pragma unroll 16
+      for (int kk = 0; kk < kGsK; ++kk) {
         const float2 av = *reinterpret_cast<const float2*>(&As[buf][kk][ty * 2]);
         const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
         const float ar[2] = {av.x, av.y};
