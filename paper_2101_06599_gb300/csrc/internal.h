@@ -76,6 +76,7 @@ cudaError_t launch_sr_select(const SrParams& sp, const SrBound& b, cudaStream_t 
 cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s);
 cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s);
 cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, cudaStream_t s);
+cudaError_t launch_sr_transpose(const float* rot, float* rot_t, int D, cudaStream_t s);
 cudaError_t launch_sr_finish(const SrParams& sp, int every, bool close, cudaStream_t s);
 // tcgen05 BF16 product (split operands) with the fitness epilogue; requires
 // D % 256 == 0. sr_tc_supported tells whether this build and device have it.

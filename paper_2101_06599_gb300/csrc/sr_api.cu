@@ -102,6 +102,12 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.fit_err, 0, (size_t)N * sizeof(float), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.amb_count, 0, sizeof(unsigned), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.inc_count, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) {
+    float* rot_t = (float*)ctx_alloc(c, (size_t)D * D * sizeof(float));
+    if (!rot_t) return DE_ENOMEM;
+    sp.rot_t = rot_t;
+    e = launch_sr_transpose(rot, rot_t, D, c->stream);
+  }
   if (e != cudaSuccess) return DE_ECUDA;
   if (sp.prec == 2) {
     uint16_t* hi = (uint16_t*)ctx_alloc(c, (size_t)D * D * sizeof(uint16_t));

@@ -24,6 +24,7 @@ struct SrParams {
   const float* rot;        // R, D x D FP32 row-major (z_k = sum_j R[k][j] a_j)
   const uint16_t* rot_hi;  // bf16(R), D x D
   const uint16_t* rot_lo;  // bf16(R - bf16(R)), D x D
+  const float* rot_t;      // R transposed (j-major, rot_t[j D + k] = R[k][j]), D x D
   uint16_t* a_hi;          // bf16(u - o), N x D (BF16 path)
   uint16_t* a_lo;          // bf16((u - o) - bf16(u - o)), N x D
   float* part_g;           // N x nct: sum of g(z) over the column tile
@@ -66,6 +67,21 @@ __device__ __forceinline__ float sr_weight(int obj, int k, float ell_k) {
 
 __device__ __forceinline__ float sr_g(int obj, float z, float w) {
   return obj == kSrElliptic ? w * z * z : fmaf(z, z, 20.0f * sin2pi(z));
+}
+
+// Asynchronous global -> shared copies (LDGSTS) of 16 or 4 bytes; src_bytes = 0
+// fills the destination with zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ uint32_t sr_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 }  // namespace de

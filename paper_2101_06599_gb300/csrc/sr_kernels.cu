@@ -319,108 +319,109 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 
 // The ambiguous entries (mode 2): 16 entries x 64 columns per tile, 128
 // threads, 2 rows x 4 columns each (16 lanes x 4 columns cover the 64-column
-// tile as in the kernel above), K in steps of 64, double-buffered with
-// register prefetch; a fixed grid walks the entry tiles. A list of a few
-// hundred entries is a small product: narrow tiles keep enough warps per SM,
-// and long K steps cover the load latency with few warps.
-constexpr int kGsM = 16, kGsN = 64, kGsK = 64, kGsThreads = 128, kGsLdA = kGsM + 4, kGsLdB = kGsN + 4;
+// tile as in the kernel above). K in steps of 32 through a 4-stage ring of
+// asynchronous copies: the entries' rows and o as they are, R from its
+// transposed copy (contiguous 64-column rows of R^T); each stage's a = x - o
+// is formed in shared memory in K-major order before use. A fixed grid walks
+// the entry tiles, so a short list still spreads over the SMs.
+constexpr int kLsM = 16, kLsN = 64, kLsK = 32, kLsStages = 4, kLsThreads = 128;
+constexpr int kLsLdA = kLsK + 4, kLsLdB = kLsN + 4, kLsLdT = kLsM + 4;
 
 template <bool VEC>
-__global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
+__global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
   const GenParams& p = sp.g;
-  __shared__ __align__(16) float As[2][kGsK][kGsLdA];
-  __shared__ __align__(16) float Bs[2][kGsK][kGsLdB];
-  __shared__ const float* rowp[kGsM];
+  __shared__ __align__(16) float Araw[kLsStages][kLsM][kLsLdA];
+  __shared__ __align__(16) float Osh[kLsStages][kLsK];
+  __shared__ __align__(16) float Bsh[kLsStages][kLsK][kLsLdB];
+  __shared__ __align__(16) float At[kLsK][kLsLdT];
+  __shared__ const float* rowp[kLsM];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows 2 ty, 2 ty + 1
-  const int n0 = blockIdx.x * kGsN;
+  const int n0 = blockIdx.x * kLsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
-  // loaders, one 16-byte chunk (4 k) per item: A, 16 rows x 16 chunks, items
-  // q = t + 128 i (i < 2): row q & 15, chunk q >> 4; B, 64 columns x 16
-  // chunks, items q = t + 128 i (i < 8): column q & 63, chunk q >> 6 (a warp
-  // stores consecutive rows / columns of one chunk: no bank conflicts)
-  for (int r0 = blockIdx.y * kGsM; r0 < nrows; r0 += gridDim.y * kGsM) {
-    __syncthreads();                                // rowp and the stages are reused
-    if (t < kGsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
-    __syncthreads();
-    float va[2][4], vb[8][4];
-    auto load = [&](int k0) {
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int q = t + kGsThreads * i;
-        const float* xa = rowp[q & 15];
-        const int jk = k0 + (q >> 4) * 4;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) va[i][u] = 0.0f;
-        if (xa) {
-          if constexpr (VEC) {
-            if (jk < p.D) {
-              const float4 x4 = *reinterpret_cast<const float4*>(xa + jk);
-              const float4 o4 = *reinterpret_cast<const float4*>(sp.shift + jk);
-              va[i][0] = __fsub_rn(x4.x, o4.x); va[i][1] = __fsub_rn(x4.y, o4.y);
-              va[i][2] = __fsub_rn(x4.z, o4.z); va[i][3] = __fsub_rn(x4.w, o4.w);
-            }
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (jk + u < p.D) va[i][u] = __fsub_rn(xa[jk + u], sp.shift[jk + u]);
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int q = t + kGsThreads * i;
-        const int n = n0 + (q & 63);
-        const int jk = k0 + (q >> 6) * 4;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) vb[i][u] = 0.0f;
-        if (n < p.D) {
-          const float* rb = sp.rot + (size_t)n * p.D;
-          if constexpr (VEC) {
-            if (jk < p.D) {
-              const float4 r4 = *reinterpret_cast<const float4*>(rb + jk);
-              vb[i][0] = r4.x; vb[i][1] = r4.y; vb[i][2] = r4.z; vb[i][3] = r4.w;
-            }
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (jk + u < p.D) vb[i][u] = rb[jk + u];
-          }
-        }
-      }
-    };
-    auto store = [&](int buf) {
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int q = t + kGsThreads * i;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) As[buf][(q >> 4) * 4 + u][q & 15] = va[i][u];
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int q = t + kGsThreads * i;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) Bs[buf][(q >> 6) * 4 + u][q & 63] = vb[i][u];
-      }
-    };
+  const int KS = (p.D + kLsK - 1) / kLsK;
 
+  // one stage: A 16 rows x 8 chunks (row t >> 3, chunk t & 7), o 8 chunks
+  // (threads 0..7), B 32 rows of R^T x 16 chunks (q = t + 128 i: row q >> 4,
+  // chunk q & 15); out-of-range pieces are zero-filled
+  auto issue = [&](int step) {
+    const int st = step % kLsStages, k0 = step * kLsK;
+    {
+      const int m = t >> 3, c = (t & 7) * 4, j = k0 + c;
+      const float* xa = rowp[m];
+      if constexpr (VEC) {
+        const bool ok = xa && j < p.D;
+        cp_async16(sr_smem_u32(&Araw[st][m][c]), ok ? xa + j : sp.shift, ok ? 16u : 0u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool ok = xa && j + u < p.D;
+          cp_async4(sr_smem_u32(&Araw[st][m][c + u]), ok ? xa + j + u : sp.shift, ok ? 4u : 0u);
+        }
+      }
+    }
+    if (t < kLsK / 4) {
+      const int c = t * 4, j = k0 + c;
+      if constexpr (VEC) {
+        const bool ok = j < p.D;
+        cp_async16(sr_smem_u32(&Osh[st][c]), ok ? sp.shift + j : sp.shift, ok ? 16u : 0u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool ok = j + u < p.D;
+          cp_async4(sr_smem_u32(&Osh[st][c + u]), ok ? sp.shift + j + u : sp.shift, ok ? 4u : 0u);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < (kLsK * kLsN / 4) / kLsThreads; ++i) {
+      const int q = t + kLsThreads * i;
+      const int kr = q >> 4, c = (q & 15) * 4, j = k0 + kr, n = n0 + c;
+      if constexpr (VEC) {
+        const bool ok = j < p.D && n < p.D;
+        cp_async16(sr_smem_u32(&Bsh[st][kr][c]), ok ? sp.rot_t + (size_t)j * p.D + n : sp.rot_t, ok ? 16u : 0u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool ok = j < p.D && n + u < p.D;
+          cp_async4(sr_smem_u32(&Bsh[st][kr][c + u]), ok ? sp.rot_t + (size_t)j * p.D + n + u : sp.rot_t,
+                    ok ? 4u : 0u);
+        }
+      }
+    }
+  };
+
+  for (int r0 = blockIdx.y * kLsM; r0 < nrows; r0 += gridDim.y * kLsM) {
+    __syncthreads();                                // rowp and the stages are reused
+    if (t < kLsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
+    __syncthreads();
+#pragma unroll
+    for (int s0 = 0; s0 < kLsStages - 1; ++s0) {
+      if (s0 < KS) issue(s0);
+      cp_async_commit();
+    }
     float acc[2][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-    load(0);
-    store(0);
-    __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < p.D; k0 += kGsK) {
-      const bool more = k0 + kGsK < p.D;
-      if (more) load(k0 + kGsK);
-#pragma unroll 16
-      for (int kk = 0; kk < kGsK; ++kk) {
-        const float2 av = *reinterpret_cast<const float2*>(&As[buf][kk][ty * 2]);
-        const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+    for (int step = 0; step < KS; ++step) {
+      cp_async_wait<kLsStages - 2>();
+      __syncthreads();                              // this stage landed; the previous step is done
+      if (step + kLsStages - 1 < KS) issue(step + kLsStages - 1);
+      cp_async_commit();
+      const int st = step % kLsStages;
+#pragma unroll
+      for (int i = 0; i < kLsM * kLsK / kLsThreads; ++i) {   // a = x - o, K-major
+        const int e = t + kLsThreads * i, m = e & 15, k = e >> 4;
+        At[k][m] = __fsub_rn(Araw[st][m][k], Osh[st][k]);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < kLsK; ++kk) {
+        const float2 av = *reinterpret_cast<const float2*>(&At[kk][ty * 2]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bsh[st][kk][tx * 4]);
         const float ar[2] = {av.x, av.y};
         const float br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
@@ -428,10 +429,8 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
 #pragma unroll
           for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
       }
-      if (more) store(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
     }
+    cp_async_wait<0>();
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
       const int e = r0 + ty * 2 + a;
@@ -443,6 +442,27 @@ __global__ void __launch_bounds__(kGsThreads) sr_gemm_fp32_list_kernel(const __g
       }
     }
   }
+}
+
+// R^T for the list kernel's contiguous B tiles (once, at set-up).
+__global__ void sr_transpose_kernel(const float* __restrict__ rot, float* __restrict__ rot_t, int D) {
+  __shared__ float tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = by + r, j = bx + threadIdx.x;
+    tile[r][threadIdx.x] = (k < D && j < D) ? rot[(size_t)k * D + j] : 0.0f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = bx + r, k = by + threadIdx.x;
+    if (j < D && k < D) rot_t[(size_t)j * D + k] = tile[threadIdx.x][r];
+  }
+}
+
+cudaError_t launch_sr_transpose(const float* rot, float* rot_t, int D, cudaStream_t s) {
+  const dim3 grid((unsigned)((D + 31) / 32), (unsigned)((D + 31) / 32)), blk(32, 8);
+  sr_transpose_kernel<<<grid, blk, 0, s>>>(rot, rot_t, D);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -581,10 +601,10 @@ cudaError_t launch_sr_trial(int xo, int /*vidx*/, const SrParams& sp, int /*bloc
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
   const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
   if (mode == 2) {
-    const int tiles = (max_rows + kGsM - 1) / kGsM;
+    const int tiles = (max_rows + kLsM - 1) / kLsM;
     const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 128)));
-    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true><<<grid, kGsThreads, 0, s>>>(sp);
-    else sr_gemm_fp32_list_kernel<false><<<grid, kGsThreads, 0, s>>>(sp);
+    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true><<<grid, kLsThreads, 0, s>>>(sp);
+    else sr_gemm_fp32_list_kernel<false><<<grid, kLsThreads, 0, s>>>(sp);
     return cudaGetLastError();
   }
   const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
