@@ -90,6 +90,42 @@ def test_shifted_rotated_at_shift_and_axes():
         assert O.evaluate("sr_elliptic", x, shift=zero, rot=R) == pytest.approx(ref, rel=1e-5)
 
 
+def test_shifted_rotated_at_rotated_integer_points():
+    """x = o + R^T n with n an integer vector gives z = n, so the rotated
+    Rastrigin is sum n_k^2 (every cosine is 1) and the rotated elliptic is
+    sum 10^(6k/(D-1)) n_k^2: pins the direction of the rotation, the sign of
+    the shift and the index of each weight."""
+    D = 12
+    o = W.shift_vector(D, seed=2).astype(np.float64)
+    R = W.rotation(D, seed=3, dtype=np.float64)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        n = rng.integers(-5, 6, size=D).astype(np.float64)
+        x = o + R.T @ n
+        w = 10.0 ** (6.0 * np.arange(D) / (D - 1))
+        x32 = x.astype(np.float32)                 # the oracle takes FP32 inputs: z = n + O(1e-5)
+        f_r = O.evaluate("sr_rastrigin", x32, shift=o.astype(np.float32), rot=R.astype(np.float32))
+        f_e = O.evaluate("sr_elliptic", x32, shift=o.astype(np.float32), rot=R.astype(np.float32))
+        assert f_r == pytest.approx((n * n).sum(), rel=1e-3, abs=1e-2)
+        assert f_e == pytest.approx((w * n * n).sum(), rel=1e-4, abs=1e-2)
+
+
+def test_shifted_rotated_with_a_permutation():
+    """R a permutation matrix: z_k = x_pi(k) - o_pi(k), so the elliptic weight
+    of row k applies to gene pi(k)."""
+    D = 9
+    pi = np.array([3, 0, 8, 1, 5, 2, 7, 4, 6])
+    P = np.zeros((D, D), np.float32)
+    P[np.arange(D), pi] = 1.0
+    o = W.shift_vector(D, seed=2)
+    x = W.population(2, D, -100, 100, seed=4)
+    w = 10.0 ** (6.0 * np.arange(D) / (D - 1))
+    for row in x:
+        a = row.astype(np.float64) - o.astype(np.float64)
+        ref = (w * a[pi] ** 2).sum()
+        assert O.evaluate("sr_elliptic", row, shift=o, rot=P) == pytest.approx(ref, rel=1e-12)
+
+
 def test_rosenbrock_pair_order():
     # f(x0, x1) = 100 (x0^2 - x1)^2 + (1 - x0)^2: (2, 0) -> 1601, (0, 2) -> 401
     assert O.evaluate("rosenbrock", np.array([2.0, 0.0], np.float32)) == 1601.0
