@@ -172,7 +172,10 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         st1 = opt.stats()
         d_acc = st1["accepts"] - st0["accepts"]
         d_msk = st1["masked_genes"] - st0["masked_genes"]
-        if opt.kernel() == 2:
+        if opt.kernel() == 3:
+            shape = "gen_stream_kernel<%s, %s>: one warp per row, 8 rows per CTA, chunks of 512 genes, " \
+                    "winning trials recomputed and stored" % (xo.upper(), obj)
+        elif opt.kernel() == 2:
             nc, stages, span, cps = opt.pipeline()
             shape = "gen_pipe_kernel<%s, %s>: %d CTA/SM, 1 producer warp + %d consumers, %d stages, " \
                     "donor spans of %d floats" % (xo.upper(), obj, cps, nc, stages, span)

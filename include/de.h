@@ -274,8 +274,11 @@ int de_get_launch(de_ctx *ctx, int32_t *threads, int32_t *vec4);
  * CTA per SM, a producer warp streams parent rows and the masked donor spans
  * into a shared-memory ring with bulk TMA copies; classic exponential and NEC
  * only; DE_EUNSUPPORTED for binomial or when a stage does not fit in shared
- * memory). Automatic picks 2 for exp / NEC when D >= 2048 and a stage fits.
- * Draws and trials are the same under both kernels. */
+ * memory), 3 = streaming kernel (one warp per row, the row in chunks, the
+ * trial recomputed and stored only when it wins; every crossover, every D).
+ * Automatic picks 2 for exp / NEC and 3 for binomial when D >= 2048. Draws,
+ * trials and selections are the same under every kernel; FP32 fitness
+ * rounding differs by summation order. The rotated objectives ignore it. */
 int de_set_kernel(de_ctx *ctx, int32_t kind);
 /* The kernel in use: 1 or 2. */
 int de_get_kernel(de_ctx *ctx, int32_t *kind);

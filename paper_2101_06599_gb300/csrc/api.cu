@@ -148,9 +148,18 @@ void configure_pipe(de_ctx* c) {
 }
 
 void resolve_kernel(de_ctx* c) {
-  if (c->kernel_req == 2) c->use_pipe = c->pipe_ok;
-  else if (c->kernel_req == 1) c->use_pipe = false;
-  else c->use_pipe = c->pipe_ok && c->D >= 2048;
+  c->use_stream = false;
+  if (c->kernel_req == 3) {
+    c->use_pipe = false;
+    c->use_stream = true;
+  } else if (c->kernel_req == 2) {
+    c->use_pipe = c->pipe_ok;
+  } else if (c->kernel_req == 1) {
+    c->use_pipe = false;
+  } else {
+    c->use_pipe = c->pipe_ok && c->D >= 2048;
+    c->use_stream = c->xo == DE_XOVER_BIN && c->D >= 2048;
+  }
 }
 
 cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
@@ -161,6 +170,7 @@ cudaError_t launch_generation(de_ctx* c, const GenParams& p) {
     pp.g = p;
     return launch_gen_pipe(c->xo, c->obj, pp, c->pipe_grid, c->pipe_block, c->pipe_smem, c->stream);
   }
+  if (c->use_stream) return launch_gen_stream(c->xo, c->obj, p, c->stream);
   switch (c->xo) {
     case DE_XOVER_BIN: return launch_gen_bin(c->obj, c->vidx, p, c->block, c->stream);
     case DE_XOVER_EXP: return launch_gen_exp(c->obj, c->vidx, p, c->block, c->stream);
@@ -614,7 +624,7 @@ int de_set_launch(de_ctx* c, int32_t threads, int32_t vec4) {
 }
 
 int de_set_kernel(de_ctx* c, int32_t kind) {
-  if (!c || kind < 0 || kind > 2) return DE_EINVAL;
+  if (!c || kind < 0 || kind > 3) return DE_EINVAL;
   if (c->batch) return DE_ESTATE;
   if (kind == 2 && !c->pipe_ok) return DE_EUNSUPPORTED;
   c->kernel_req = kind;
@@ -626,7 +636,7 @@ int de_set_kernel(de_ctx* c, int32_t kind) {
 int de_get_kernel(de_ctx* c, int32_t* kind) {
   if (!c || !kind) return DE_EINVAL;
   if (c->batch) return DE_ESTATE;
-  *kind = c->use_pipe ? 2 : 1;
+  *kind = c->use_pipe ? 2 : (c->use_stream ? 3 : 1);
   return DE_OK;
 }
 

@@ -33,6 +33,7 @@ struct de_ctx {
   // kernel choice: 0 = automatic, 1 = row per CTA, 2 = pipelined (exp / NEC)
   int kernel_req = 0;
   bool use_pipe = false;
+  bool use_stream = false;         // streaming warp-per-row kernel (gen_stream.cuh)
   bool pipe_ok = false;
   PipeParams pp{};
   int pipe_grid = 0, pipe_block = 32 + 256;

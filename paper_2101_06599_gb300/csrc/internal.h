@@ -9,6 +9,7 @@ namespace de {
 // Generation kernels, one translation unit per crossover. vidx indexes
 // kVecChoices (float4 slots per thread: 1, 2, 4, 8, 16).
 cudaError_t launch_gen_bin(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
+cudaError_t launch_gen_stream(int xo, int obj, const GenParams& p, cudaStream_t s);
 cudaError_t launch_gen_exp(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
 cudaError_t launch_gen_nec(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
 

@@ -327,9 +327,70 @@ def test_automatic_kernel_choice_at_large_rows(D):
     for xo in ("exp", "nec", "bin"):
         opt, lo, hi = make(64, D, xo, "rosenbrock", seed=1)
         try:
-            assert opt.kernel() == (1 if xo == "bin" else 2)
+            assert opt.kernel() == (3 if xo == "bin" else 2)
             if xo != "bin":
                 nc, stages, span, cps = opt.pipeline()
                 assert stages >= 2 and cps in (1, 2) and nc == 256
         finally:
             opt.close()
+
+
+# ---- the streaming kernel (one warp per row, chunks of 512 genes) ----------------------------
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+@pytest.mark.parametrize("obj", ["sphere", "rastrigin", "ackley", "rosenbrock", "griewank", "elliptic"])
+@pytest.mark.parametrize("N,D,CR", [(37, 29, 0.9), (64, 1000, 0.5), (20, 4097, 0.9), (48, 513, 0.1),
+                                    (9, 9999, 0.9)])
+def test_stream_kernel_parity(xo, obj, N, D, CR):
+    F, seed = 0.5, 17
+    opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
+    try:
+        opt.set_kernel(3)
+        assert opt.kernel() == 3
+        one_step_parity(opt, lo, hi, xo, obj, F, CR, seed)
+    finally:
+        opt.close()
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+@pytest.mark.parametrize("N,D,CR", [(4, 1, 0.9), (500, 3, 0.0), (33, 130, 1.0), (17, 2048, 0.9)])
+def test_stream_kernel_edges(xo, N, D, CR):
+    F, seed, obj = 0.7, 23, "rosenbrock"
+    opt, lo, hi = make(N, D, xo, obj, CR=CR, F=F, seed=seed)
+    try:
+        opt.set_kernel(3)
+        s, acc, _ = one_step_parity(opt, lo, hi, xo, obj, F, CR, seed)
+        if xo != "bin" and CR == 0.0:
+            assert np.all(s.L == 1)
+        if CR == 1.0:
+            assert np.all(s.L == D)                # every gene crosses (binomial: the mask popcount)
+    finally:
+        opt.close()
+
+
+def test_stream_matches_row_kernel_over_generations():
+    """Binomial, Ackley, 8 generations: the two kernels draw, cross and mutate
+    identically; their FP32 sums differ only in order."""
+    N, D, obj = 600, 3000, "ackley"
+    a, lo, hi = make(N, D, "bin", obj, CR=0.9, seed=4)
+    b, _, _ = make(N, D, "bin", obj, CR=0.9, seed=4)
+    try:
+        a.set_kernel(1)
+        assert b.kernel() == 3                     # chosen automatically for binomial at D >= 2048
+        for g in range(8):
+            ta, fa, acca, da = a.debug_step()
+            tb, fb, accb, db = b.debug_step()
+            assert np.array_equal(da, db)
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            assert np.allclose(fa, fb, rtol=2 * RTOL, atol=2 * RTOL)
+            pa, ffa = a.population()
+            pb, ffb = b.population()
+            if not np.array_equal(pa.view(np.uint32), pb.view(np.uint32)):
+                b.set_population(pa, ffa)
+        b.run(5)
+        st = b.stats()
+        assert st["generation"] == 13
+        pop, fit = b.population()
+        assert np.all(np.abs(fit - O.evaluate(obj, pop)) <= tol(O.evaluate(obj, pop)))
+    finally:
+        a.close()
+        b.close()
