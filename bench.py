@@ -395,6 +395,9 @@ def main():
                     help="run one side workload alone (for profiling); prints its own JSON line")
     ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
     ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
+    ap.add_argument("--xo", default="nec", choices=["nec", "bin", "exp"],
+                    help="headline crossover (other values are for profiling one kernel)")
+    ap.add_argument("--obj", default="rosenbrock", choices=["rosenbrock", "ackley"], help="headline objective")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -431,7 +434,7 @@ def main():
 
     # headline: NEC on Rosenbrock, clocks sampled across the ramp and the timed region
     with ClockSampler(local) as clk:
-        opt, ms, d_acc, d_msk, shape = time_variant(DE, torch, N, D, "nec", "rosenbrock", K, W, seed,
+        opt, ms, d_acc, d_msk, shape = time_variant(DE, torch, N, D, args.xo, args.obj, K, W, seed,
                                                     ramp_s=1.0)
     ms_max = max_over_ranks(torch, ms)
     units = float(N) * D * K
@@ -440,7 +443,7 @@ def main():
     avg_launch_s = ms / 1e3 / K
     peak, peak_src = measured_hbm_peak()
     achieved = bytes_alg / K / avg_launch_s / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic() if (args.xo, args.obj, N, D) == ("nec", "rosenbrock", N_DEF, D_DEF) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
                 "kernel": shape,
@@ -452,7 +455,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         from paper_2101_06599_gb300 import workloads as Wk
-        host = torch.from_numpy(Wk.population(N, D, *BOXES["rosenbrock"], seed + 1000)).pin_memory()
+        host = torch.from_numpy(Wk.population(N, D, *BOXES[args.obj], seed + 1000)).pin_memory()
         host_np = host.numpy()
         xbest = torch.empty(D, dtype=torch.float32).pin_memory().numpy()
         torch.cuda.synchronize()
@@ -506,7 +509,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "objective": "rosenbrock", "crossover": "nec", "N": N, "D": D,
+            "config": {"workload": WORKLOAD, "objective": args.obj, "crossover": args.xo, "N": N, "D": D,
                        "F": F_DEF, "CR": CR_DEF, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (two 0.66 GB population buffers), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
