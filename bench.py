@@ -188,13 +188,16 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         raise
 
 
-def time_batched(DE, torch, steps, warmup, seed, peak):
+def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
     """The 512-instance workload (D log-uniform in [10, 2000], N = min(10 D,
     4096), sphere/Rastrigin/Ackley/Rosenbrock round-robin, NEC, F = 0.5,
-    Cr = 0.9), one generation of every instance per step."""
+    Cr = 0.9), one generation of every instance per step. n_inst keeps the
+    first n_inst instances (a smaller case of the same mix, for profiling)."""
     from paper_2101_06599_gb300 import workloads as Wk
     specs = [dict(N=s.N, D=s.D, obj=s.objective, bounds=Wk.BOXES[s.objective], xo="nec", CR=CR_DEF, F=F_DEF)
              for s in Wk.batched_specs()]
+    if n_inst:
+        specs = specs[:n_inst]
     units = float(sum(s["N"] * s["D"] for s in specs))
     rows = float(sum(s["N"] for s in specs))
     b = DE.Batch(specs, seed=seed + 4)
@@ -221,7 +224,8 @@ def time_batched(DE, torch, steps, warmup, seed, peak):
     byts = (4.0 * units * steps + 12.0 * d_msk + 4.0 * acc_genes + 64.0 * rows * steps
             + 6.0 * rows * steps + 4.0 * d_acc)
     gbs = byts / (ms / 1e3) / 1e9
-    return {"workload": "batched_512_instances", "instances": len(specs), "ind_dims_per_step": units,
+    return {"workload": "batched_512_instances" if len(specs) == 512 else "batched_first_%d_instances" % len(specs),
+            "instances": len(specs), "ind_dims_per_step": units,
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_gen": ms / steps,
             "hbm_gbs": gbs, "frac": gbs / peak, "launches_per_step": 3,
             "a_acceptance": d_acc / (rows * steps), "m_masked_fraction": d_msk / (units * steps)}
@@ -391,6 +395,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-rotated", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=0,
+                    help="batched leg: keep the first K of the 512 instances (profiling)")
     ap.add_argument("--only", choices=["rotated", "small", "batched"],
                     help="run one side workload alone (for profiling); prints its own JSON line")
     ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
@@ -425,7 +431,7 @@ def main():
         elif args.only == "small":
             res = time_small_configs(DE, torch, W)
         else:
-            res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0])
+            res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0], args.batch_instances)
         if rank == 0:
             print(json.dumps({"only": args.only, "steps": K, "warmup": W, "result": res}))
         if _dist is not None:
