@@ -96,6 +96,8 @@ struct BatchSmem {
   float first[kBatchVmax][kBatchThreads / 32];
   float red[4][kBatchThreads / 32];
   int accept[kBatchThreads / 4];
+  int masked[kBatchThreads / 4];
+  unsigned long long key[kBatchThreads / 4];
 };
 
 // The rows of one tile, specialised for one objective and crossover. Kept
@@ -114,6 +116,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   const long long gen = p.st->gen;
   const uint32_t g = (uint32_t)gen;
   const int D = p.D, D4 = p.D4;
+  const int V = (D4 + G - 1) / G;                   // slots per lane this instance uses (uniform)
   const float F = p.F, lo = p.lo, hi = p.hi;
 
   RowPlan32 pl{};
@@ -132,6 +135,12 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   unsigned mk[kBatchVmax];
 #pragma unroll
   for (int k = 0; k < kBatchVmax; ++k) {
+    x[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    mk[k] = 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kBatchVmax; ++k) {
+    if (k >= V) break;                               // uniform: unused slots cost one branch
     const int q = gl + k * G;
     const bool in = active && q < D4;
     x[k] = in ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -161,6 +170,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   int cnt = 0;
 #pragma unroll
   for (int k = 0; k < kBatchVmax; ++k) {
+    if (k >= V) break;
     if (mk[k]) {
       const int q = gl + k * G;
       const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
@@ -186,6 +196,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     const int gwn = (G + 31) >> 5;                 // warps per group
 #pragma unroll
     for (int k = 0; k < kBatchVmax; ++k) {
+      if (k >= V) break;
       float nb = __shfl_down_sync(0xFFFFFFFFu, x[k].x, 1, W);
       const float next0 = __shfl_sync(0xFFFFFFFFu, (k + 1 < kBatchVmax) ? x[k + 1].x : 0.0f, 0, W);
       if ((gl & (W - 1)) == W - 1) {
@@ -206,6 +217,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     if (active) {
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
+        if (k >= V) break;
         const int q = gl + k * G;
         if (q < D4) {
           const int j0 = 4 * q;
@@ -250,25 +262,28 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     }
   }
 
-  // decision by the group leader
+  // decision by the group leader; the tile's counters go to the state once
+  if (gl == 0) {
+    sm.accept[gi] = 0;
+    sm.masked[gi] = 0;
+    sm.key[gi] = ~0ull;
+  }
   if (active && gl == 0) {
     float f = finalize_fitness<OBJ>(s, p);
     if (f != f) f = __int_as_float(0x7F800000);
     if (eval_only) {
       p.fit[i] = f;
-      atomicMin(&p.st->best_key, best_key_of(f, i));
-      sm.accept[gi] = 0;
+      sm.key[gi] = best_key_of(f, i);
     } else {
       const int acc = (f < pl.fit_i) ? 1 : 0;
       sm.accept[gi] = acc;
       p.slots[(size_t)((gen + 1) & 1) * p.N + i] = (uint8_t)(acc ? 1 - si : si);
       const int Lrow = (XO == kBin) ? cnt : pl.L;
+      sm.masked[gi] = Lrow;
       if (acc) {
         p.fit[i] = f;
-        atomicMin(&p.st->best_key, best_key_of(f, i));
-        atomicAdd(&p.st->accepts, 1ull);
+        sm.key[gi] = best_key_of(f, i);
       }
-      atomicAdd(&p.st->masked, (unsigned long long)Lrow);
       if (p.dbg_ftrial) p.dbg_ftrial[i] = f;
       if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)acc;
       if (p.dbg_draws) {
@@ -278,11 +293,26 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    const int R = kBatchThreads / G;
+    unsigned long long k = ~0ull, masked = 0, accepts = 0;
+    for (int r = 0; r < R; ++r) {
+      k = (sm.key[r] < k) ? sm.key[r] : k;
+      masked += (unsigned long long)sm.masked[r];
+      accepts += (unsigned long long)sm.accept[r];
+    }
+    if (k != ~0ull) atomicMin(&p.st->best_key, k);
+    if (!eval_only) {
+      if (accepts) atomicAdd(&p.st->accepts, accepts);
+      atomicAdd(&p.st->masked, masked);
+    }
+  }
   if (active && !eval_only) {
     if (sm.accept[gi]) {
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
+        if (k >= V) break;
         const int q = gl + k * G;
         if (q < D4) st_stream(out + q, x[k]);
       }
@@ -291,6 +321,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
       float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch);
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
+        if (k >= V) break;
         const int q = gl + k * G;
         if (q < D4) o[q] = x[k];
       }
