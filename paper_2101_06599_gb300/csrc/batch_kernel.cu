@@ -116,7 +116,6 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   const long long gen = p.st->gen;
   const uint32_t g = (uint32_t)gen;
   const int D = p.D, D4 = p.D4;
-  const int V = (D4 + G - 1) / G;                   // slots per lane this instance uses (uniform)
   const float F = p.F, lo = p.lo, hi = p.hi;
 
   RowPlan32 pl{};
@@ -135,12 +134,6 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   unsigned mk[kBatchVmax];
 #pragma unroll
   for (int k = 0; k < kBatchVmax; ++k) {
-    x[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    mk[k] = 0u;
-  }
-#pragma unroll
-  for (int k = 0; k < kBatchVmax; ++k) {
-    if (k >= V) break;                               // uniform: unused slots cost one branch
     const int q = gl + k * G;
     const bool in = active && q < D4;
     x[k] = in ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -155,12 +148,16 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
         m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == pl.jrand) ? 8u : 0u;
       } else {
         int dd = j0 - pl.jrand;
-        if (dd < 0) dd += D;
+        if (dd < 0) dd += D;                       // (j0 - j_rand) mod D
+        if (dd >= pl.L && dd + 3 < D) {
+          m = 0u;                                  // the slot lies wholly outside the segment
+        } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int de = dd + e;
-          if (de >= D) de -= D;
-          m |= (de < pl.L) ? (1u << e) : 0u;
+          for (int e = 0; e < 4; ++e) {
+            int de = dd + e;
+            if (de >= D) de -= D;
+            m |= (de < pl.L) ? (1u << e) : 0u;
+          }
         }
       }
       m &= (1u << min(4, D - j0)) - 1u;
@@ -170,7 +167,6 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   int cnt = 0;
 #pragma unroll
   for (int k = 0; k < kBatchVmax; ++k) {
-    if (k >= V) break;
     if (mk[k]) {
       const int q = gl + k * G;
       const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
@@ -196,8 +192,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     const int gwn = (G + 31) >> 5;                 // warps per group
 #pragma unroll
     for (int k = 0; k < kBatchVmax; ++k) {
-      if (k >= V) break;
-      float nb = __shfl_down_sync(0xFFFFFFFFu, x[k].x, 1, W);
+        float nb = __shfl_down_sync(0xFFFFFFFFu, x[k].x, 1, W);
       const float next0 = __shfl_sync(0xFFFFFFFFu, (k + 1 < kBatchVmax) ? x[k + 1].x : 0.0f, 0, W);
       if ((gl & (W - 1)) == W - 1) {
         if (G <= 32) nb = next0;                   // group lane 0, next slot
@@ -217,8 +212,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
     if (active) {
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
-        if (k >= V) break;
-        const int q = gl + k * G;
+            const int q = gl + k * G;
         if (q < D4) {
           const int j0 = 4 * q;
           accum_gene<OBJ>(s, x[k].x, j0, p);
@@ -312,8 +306,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
-        if (k >= V) break;
-        const int q = gl + k * G;
+            const int q = gl + k * G;
         if (q < D4) st_stream(out + q, x[k]);
       }
     }
@@ -321,8 +314,7 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
       float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch);
 #pragma unroll
       for (int k = 0; k < kBatchVmax; ++k) {
-        if (k >= V) break;
-        const int q = gl + k * G;
+            const int q = gl + k * G;
         if (q < D4) o[q] = x[k];
       }
     }
