@@ -4,10 +4,11 @@
 // Device memory: one arena per context holding, per instance, two slot
 // buffers (N x pitch floats), fitness, slot bytes and NEC thresholds, plus
 // one DevState per instance (contiguous, so the totals are one copy).
-// Tiles: instance k is cut into ceil(N_k / R_k) tiles of R_k = 256 / G_k
-// rows; the tile list is grouped by (objective, crossover) and ordered by
-// tile cost (R_k D_k, descending) within a group, a longest-processing-time
-// schedule for the grid-stride walk. A second list
+// Tiles: instance k is cut into ceil(N_k / R_k) tiles, R_k = 32 / G_k rows
+// (warp tiles, G_k <= 32) or 256 / G_k rows (CTA tiles); each tile list is
+// grouped by (objective, crossover) and ordered by tile cost (R_k D_k,
+// descending) within a group, a longest-processing-time schedule for the
+// grid-stride walk. A second list
 // of 256-row tiles drives the plan kernel; plans (32 bytes per row of every
 // instance) live in one buffer indexed by the instance's first row.
 #include <algorithm>
@@ -61,23 +62,40 @@ static int build_tiles(de_ctx* c) {
     return (double)(kBatchThreadsHost / c->bgroup[a]) * c->bp[a].D >
            (double)(kBatchThreadsHost / c->bgroup[b]) * c->bp[b].D;
   });
-  std::vector<BatchTile> tiles;
+  // rows of G <= 32 lanes go to warp tiles of 32 / G rows, wider rows to CTA
+  // tiles of 256 / G rows
+  std::vector<BatchTile> wt, ct;
   c->bt0.assign((size_t)c->n_inst, 0);
   c->bt1.assign((size_t)c->n_inst, 0);
   for (int k : order) {
-    const int R = kBatchThreadsHost / c->bgroup[k];
+    const bool warp = c->bgroup[k] <= 32;
+    std::vector<BatchTile>& tiles = warp ? wt : ct;
+    const int R = (warp ? 32 : kBatchThreadsHost) / c->bgroup[k];
     const int nt = (c->bp[k].N + R - 1) / R;
     c->bt0[k] = (int)tiles.size();
     for (int t = 0; t < nt; ++t) tiles.push_back(BatchTile{k, t * R});
     c->bt1[k] = (int)tiles.size();
   }
   if (c->d_tiles) ctx_free(c, c->d_tiles);
-  c->d_tiles = (BatchTile*)ctx_alloc(c, tiles.size() * sizeof(BatchTile));
-  if (!c->d_tiles) return DE_ENOMEM;
-  c->ntiles = (int)tiles.size();
-  if (cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,
-                      c->stream) != cudaSuccess)
-    return DE_ECUDA;
+  if (c->d_ctiles) ctx_free(c, c->d_ctiles);
+  c->d_tiles = nullptr;
+  c->d_ctiles = nullptr;
+  c->ntiles = (int)wt.size();
+  c->nctiles = (int)ct.size();
+  if (!wt.empty()) {
+    c->d_tiles = (BatchTile*)ctx_alloc(c, wt.size() * sizeof(BatchTile));
+    if (!c->d_tiles) return DE_ENOMEM;
+    if (cudaMemcpyAsync(c->d_tiles, wt.data(), wt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return DE_ECUDA;
+  }
+  if (!ct.empty()) {
+    c->d_ctiles = (BatchTile*)ctx_alloc(c, ct.size() * sizeof(BatchTile));
+    if (!c->d_ctiles) return DE_ENOMEM;
+    if (cudaMemcpyAsync(c->d_ctiles, ct.data(), ct.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return DE_ECUDA;
+  }
   drop_graphs(c);
   return upload_insts(c);
 }
@@ -85,18 +103,24 @@ static int build_tiles(de_ctx* c) {
 // Evaluate the parents of every instance (inst < 0) or of one instance.
 static int batch_evaluate(de_ctx* c, int inst) {
   cudaError_t e;
-  if (inst < 0)
-    e = launch_batch_evaluate(c->d_insts, c->d_tiles, c->ntiles, c->d_states, 0, c->n_inst, c->batch_grid,
-                              c->stream);
-  else
-    e = launch_batch_evaluate(c->d_insts, c->d_tiles + c->bt0[inst], c->bt1[inst] - c->bt0[inst], c->d_states,
-                              inst, 1, c->batch_grid, c->stream);
+  if (inst < 0) {
+    e = launch_batch_evaluate(c->d_insts, c->d_tiles, c->ntiles, c->d_ctiles, c->nctiles, c->d_states, 0, c->n_inst,
+                              c->batch_grid, c->stream);
+  } else {
+    const int n = c->bt1[inst] - c->bt0[inst];
+    if (c->bgroup[inst] <= 32)
+      e = launch_batch_evaluate(c->d_insts, c->d_tiles + c->bt0[inst], n, nullptr, 0, c->d_states, inst, 1,
+                                c->batch_grid, c->stream);
+    else
+      e = launch_batch_evaluate(c->d_insts, nullptr, 0, c->d_ctiles + c->bt0[inst], n, c->d_states, inst, 1,
+                                c->batch_grid, c->stream);
+  }
   return cuda_status(e);
 }
 
 cudaError_t batch_launch_generation(de_ctx* c, bool, int) {
-  return launch_batch_generation(c->d_insts, c->d_tiles, c->ntiles, c->d_ptiles, c->nptiles, c->d_plans,
-                                 c->d_states, c->n_inst, c->batch_grid, c->stream);
+  return launch_batch_generation(c->d_insts, c->d_tiles, c->ntiles, c->d_ctiles, c->nctiles, c->d_ptiles,
+                                 c->nptiles, c->d_plans, c->d_states, c->n_inst, c->batch_grid, c->stream);
 }
 
 // Plan tiles: 256 consecutive rows of one instance, instances in order.

@@ -59,13 +59,14 @@ struct de_ctx {
   std::vector<float> bF;
   std::vector<de_bounds> bb;
   de::BatchInst* d_insts = nullptr;
-  de::BatchTile* d_tiles = nullptr;
+  de::BatchTile* d_tiles = nullptr;      // warp tiles (instances with G <= 32)
+  de::BatchTile* d_ctiles = nullptr;     // CTA tiles (G > 32)
   de::BatchTile* d_ptiles = nullptr;  // plan tiles: 256 rows of one instance
   de::RowPlan32* d_plans = nullptr;
   int nptiles = 0;
   std::vector<long long> brow_base;
   de::DevState* d_states = nullptr;
-  int ntiles = 0, batch_grid = 0, max_pitch = 0;
+  int ntiles = 0, nctiles = 0, batch_grid = 0, max_pitch = 0;
   // shifted-rotated objectives (sr_api.cu)
   bool rotated = false;
   de::SrParams sp{};

@@ -59,13 +59,14 @@ constexpr int kBatchThreadsHost = 256;
 constexpr int kBatchMaxGroup = 256;
 constexpr int kBatchMaxD4PerLane = 16;
 // plan kernel + row kernel + close kernel (one generation of every instance)
-cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* tiles, int ntiles,
-                                    const BatchTile* ptiles, int nptiles, RowPlan32* plans, DevState* states,
-                                    int n_inst, int grid, cudaStream_t s);
+cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
+                                    const BatchTile* ctiles, int nctiles, const BatchTile* ptiles, int nptiles,
+                                    RowPlan32* plans, DevState* states, int n_inst, int grid, cudaStream_t s);
 // reset best keys, evaluate the parents of the tiles' rows, close (instances
 // first_inst .. first_inst + n_inst - 1)
-cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* tiles, int ntiles, DevState* states,
-                                  int first_inst, int n_inst, int grid, cudaStream_t s);
+cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
+                                  const BatchTile* ctiles, int nctiles, DevState* states, int first_inst,
+                                  int n_inst, int grid, cudaStream_t s);
 
 // Shifted-rotated objectives (sr_kernels.cu, sr_tc.cu); SrParams and
 // SrBound in sr_common.cuh.
