@@ -328,8 +328,8 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
 // its own tiles at its own pace (more rows in flight per SM). Counters are
 // reduced over the warp and added once per warp tile.
 template <int OBJ, int XO>
-__device__ __noinline__ void batch_rows_warp(const BatchInst& I, const BatchTile tl, const RowPlan32 pl,
-                                             int eval_only) {
+__device__ __noinline__ void batch_rows_warp(const BatchInst& I, const BatchTile tl,
+                                             const RowPlan32* __restrict__ plans, int eval_only) {
   const GenParams& p = I.g;
   const int lane = threadIdx.x & 31;
   const int G = I.group;                          // 4 .. 32
@@ -341,6 +341,11 @@ __device__ __noinline__ void batch_rows_warp(const BatchInst& I, const BatchTile
   const int D = p.D, D4 = p.D4;
   const float F = p.F, lo = p.lo, hi = p.hi;
 
+  RowPlan32 pl{};
+  if (active) {
+    if (eval_only) pl.slots = p.slots[(size_t)(gen & 1) * p.N + i];
+    else pl = plans[I.row_base + i];
+  }
   const int si = (int)(pl.slots & 0xFFu);
   const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)(active ? i : 0) * p.pitch);
   const float4* d1 = reinterpret_cast<const float4*>(((pl.slots >> 8) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch);
@@ -501,61 +506,29 @@ __device__ __noinline__ void batch_rows_warp(const BatchInst& I, const BatchTile
 
 template <int OBJ>
 __device__ __forceinline__ void batch_rows_warp_xo(int xo, const BatchInst& I, const BatchTile tl,
-                                                   const RowPlan32 pl, int eval_only) {
-  if (xo == kBin) batch_rows_warp<OBJ, kBin>(I, tl, pl, eval_only);
-  else if (xo == kExp) batch_rows_warp<OBJ, kExp>(I, tl, pl, eval_only);
-  else batch_rows_warp<OBJ, kNec>(I, tl, pl, eval_only);
-}
-
-// The plan of this lane's row of warp tile tl (the slot byte only when
-// evaluating).
-__device__ __forceinline__ RowPlan32 batch_fetch_plan(const BatchInst* insts, const BatchTile tl,
-                                                      const RowPlan32* plans, int eval_only) {
-  const BatchInst& I = insts[tl.inst];
-  const GenParams& p = I.g;
-  const int gi = (threadIdx.x & 31) / I.group;
-  const int i = tl.row0 + gi;
-  RowPlan32 pl{};
-  if (i < p.N) {
-    if (eval_only) pl.slots = p.slots[(size_t)(p.st->gen & 1) * p.N + i];
-    else pl = plans[I.row_base + i];
-  }
-  return pl;
+                                                   const RowPlan32* plans, int eval_only) {
+  if (xo == kBin) batch_rows_warp<OBJ, kBin>(I, tl, plans, eval_only);
+  else if (xo == kExp) batch_rows_warp<OBJ, kExp>(I, tl, plans, eval_only);
+  else batch_rows_warp<OBJ, kNec>(I, tl, plans, eval_only);
 }
 
 // Warp tiles: warp w of CTA b takes tiles b * 8 + w, then every
-// gridDim.x * 8-th; no CTA barrier anywhere. The next tile's descriptor and
-// plan are fetched before the current tile is processed, so their three
-// dependent loads overlap its work.
+// gridDim.x * 8-th; no CTA barrier anywhere.
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_warp_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                   const RowPlan32* __restrict__ plans, int eval_only) {
   const int warps = kBatchThreads / 32;
-  const int stride = gridDim.x * warps;
-  int wt = blockIdx.x * warps + (threadIdx.x >> 5);
-  if (wt >= ntiles) return;
-  BatchTile tl = tiles[wt];
-  RowPlan32 pl = batch_fetch_plan(insts, tl, plans, eval_only);
-  while (wt < ntiles) {
-    const int wn = wt + stride;
-    BatchTile tn = tl;
-    RowPlan32 pn{};
-    if (wn < ntiles) {
-      tn = tiles[wn];
-      pn = batch_fetch_plan(insts, tn, plans, eval_only);
-    }
+  for (int wt = blockIdx.x * warps + (threadIdx.x >> 5); wt < ntiles; wt += gridDim.x * warps) {
+    const BatchTile tl = tiles[wt];
     const BatchInst& I = insts[tl.inst];
     switch (I.obj) {                                 // uniform over the warp
-      case kSphere: batch_rows_warp_xo<kSphere>(I.xo, I, tl, pl, eval_only); break;
-      case kRastrigin: batch_rows_warp_xo<kRastrigin>(I.xo, I, tl, pl, eval_only); break;
-      case kAckley: batch_rows_warp_xo<kAckley>(I.xo, I, tl, pl, eval_only); break;
-      case kRosenbrock: batch_rows_warp_xo<kRosenbrock>(I.xo, I, tl, pl, eval_only); break;
-      case kGriewank: batch_rows_warp_xo<kGriewank>(I.xo, I, tl, pl, eval_only); break;
-      default: batch_rows_warp_xo<kElliptic>(I.xo, I, tl, pl, eval_only); break;
+      case kSphere: batch_rows_warp_xo<kSphere>(I.xo, I, tl, plans, eval_only); break;
+      case kRastrigin: batch_rows_warp_xo<kRastrigin>(I.xo, I, tl, plans, eval_only); break;
+      case kAckley: batch_rows_warp_xo<kAckley>(I.xo, I, tl, plans, eval_only); break;
+      case kRosenbrock: batch_rows_warp_xo<kRosenbrock>(I.xo, I, tl, plans, eval_only); break;
+      case kGriewank: batch_rows_warp_xo<kGriewank>(I.xo, I, tl, plans, eval_only); break;
+      default: batch_rows_warp_xo<kElliptic>(I.xo, I, tl, plans, eval_only); break;
     }
-    wt = wn;
-    tl = tn;
-    pl = pn;
   }
 }
 
