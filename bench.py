@@ -302,6 +302,54 @@ def time_small_configs(DE, torch, warmup):
     return out
 
 
+# Table I's CUDA columns (GTX 760, CuPy, seconds for Cr = 0.2 .. 1.0 x 100 runs): context only
+PAPER_TABLE1_CUDA = {  # (D, Np): (CUDA-nec, CUDA-bin)
+    (10, 100): (1.76, 6.99), (10, 1000): (1.18, 0.64), (10, 10000): (1.34, 0.94),
+    (100, 100): (1.16, 0.66), (100, 1000): (1.23, 0.64), (100, 10000): (1.11, 1.36),
+    (1000, 100): (0.66, 0.56), (1000, 1000): (1.07, 1.00), (1000, 10000): (4.31, 4.56),
+    (10000, 100): (1.48, 0.97), (10000, 1000): (4.43, 3.91), (10000, 10000): (33.26, 39.14),
+}
+
+
+def time_crossover_grid(DE, torch, reps=100):
+    """Crossover alone over Table I's grid: U = mask ? V : X on Np x D FP32
+    matrices resident on the device (X, V seeded normal), 100 calls at each
+    Cr in {0.2, 0.4, 0.6, 0.8, 1.0} (generation = call index), per crossover;
+    the total seconds of the 500 calls (CUDA events, calls queued from
+    Python) as Table I reports them, and the bytes moved per second on the
+    device (12 bytes per gene: X and V read, U written)."""
+    crs = (0.2, 0.4, 0.6, 0.8, 1.0)
+    out = {"protocol": "de_crossover_apply, %d calls per Cr, Cr in %s" % (reps, list(crs)), "cells": []}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    for (D, Np), paper in PAPER_TABLE1_CUDA.items():
+        x = torch.randn((Np, D), generator=g, device="cuda")
+        v = torch.randn((Np, D), generator=g, device="cuda")
+        u = torch.empty_like(x)
+        cell = {"D": D, "Np": Np, "paper_gtx760_s": {"nec": paper[0], "bin": paper[1]}}
+        s = torch.cuda.current_stream()
+        for xo in ("nec", "bin", "exp"):
+            for cr in crs[:1]:                          # warm-up (first launch of each kernel)
+                DE.de_crossover_apply(u.data_ptr(), x.data_ptr(), v.data_ptr(), D, Np, D, cr, xo, SEED, 0,
+                                      stream=s.cuda_stream)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(s)
+            for cr in crs:
+                for r in range(reps):
+                    DE.de_crossover_apply(u.data_ptr(), x.data_ptr(), v.data_ptr(), D, Np, D, cr, xo, SEED, r,
+                                          stream=s.cuda_stream)
+            ev1.record(s)
+            ev1.synchronize()
+            sec = ev0.elapsed_time(ev1) / 1e3
+            calls = reps * len(crs)
+            cell[xo + "_s"] = sec
+            cell[xo + "_gbs"] = 12.0 * Np * D * calls / sec / 1e9
+        out["cells"].append(cell)
+        del x, v, u
+    return out
+
+
 _dist = None
 
 
@@ -397,7 +445,8 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=0,
                     help="batched leg: keep the first K of the 512 instances (profiling)")
-    ap.add_argument("--only", choices=["rotated", "small", "batched"],
+    ap.add_argument("--no-crossover", action="store_true")
+    ap.add_argument("--only", choices=["rotated", "small", "batched", "crossover"],
                     help="run one side workload alone (for profiling); prints its own JSON line")
     ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
     ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
@@ -430,6 +479,8 @@ def main():
             res = time_rotated(DE, torch, K, W)
         elif args.only == "small":
             res = time_small_configs(DE, torch, W)
+        elif args.only == "crossover":
+            res = time_crossover_grid(DE, torch)
         else:
             res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0], args.batch_instances)
         if rank == 0:
@@ -502,6 +553,10 @@ def main():
     if not args.no_small:
         small = time_small_configs(DE, torch, W)
 
+    xgrid = None
+    if not args.no_crossover:
+        xgrid = time_crossover_grid(DE, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, timed, secs = oracle_generation_rate(N, D, "rosenbrock", "nec", 12.0)
@@ -520,7 +575,7 @@ def main():
                        "l2": "inputs larger than L2 (two 0.66 GB population buffers), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
             "clocks": clk.summary(), "variants": variants, "batched": batched, "rotated": rotated,
-            "small_configs": small,
+            "small_configs": small, "crossover_table1": xgrid,
         }
         print(json.dumps(line))
     if _dist is not None:

@@ -324,6 +324,36 @@ int de_nec_step_noalloc(const float *pop_in, const float *fit_in, float *pop_out
                         int32_t N, int32_t D, int32_t pitch, float F, double CR, de_objective obj,
                         de_bounds b, uint64_t seed, int64_t generation, void *cuda_stream);
 
+/* ---- crossover alone (Table I) --------------------------------------------- */
+/* The crossover step by itself, as Table I times it, on caller-owned device
+ * buffers; nothing is allocated and the work is queued on `cuda_stream`.
+ * Row i (0 <= i < N) of generation `generation` gets the mask de_step uses for
+ * row i at that generation with that seed and Philox instance field:
+ *   bin: gene j crosses iff word j of the row's BIN stream < Cr 2^32, or
+ *        j = j_rand (Eq. 2, Alg. 7);
+ *   exp: the genes ((j - j_rand) mod D) < L, L from the sequential walk of
+ *        Alg. 8 over the EXP stream;
+ *   nec: the same circular segment with L from Eq. (9) (L = smallest n with
+ *        Cr^n <= U, at most D; Alg. 9);
+ * j_rand = word 3 of the row's IDX block scaled to [0, D). Each row's draws
+ * depend only on (seed, generation, instance, i), not on N.
+ * Arguments: 1 <= N, 1 <= D <= ld, 0 <= Cr <= 1, generation >= 0 (its low 32
+ * bits enter the counter, as in de_step), instance < 2^24; DE_EINVAL
+ * otherwise, DE_ECUDA if the launch fails. Errors of the queued work surface
+ * at the caller's next synchronisation of the stream.
+ *
+ * de_crossover_mask: mask (device, N rows of ld bytes) gets 1 where gene j
+ * crosses, 0 elsewhere; bytes j >= D of a row are not written.
+ * de_crossover_apply: U = mask ? V : X elementwise (the trial matrix of Alg. 9 /
+ * Alg. 10); u, x, v are device, N rows of ld floats; u must not alias x or v.
+ * Elements j >= D of a row are neither read nor written. 16-byte aligned
+ * bases with ld % 4 == 0 take 128-bit loads and stores. */
+int de_crossover_mask(uint8_t *mask, int64_t ld, int32_t N, int32_t D, double CR, de_crossover xo,
+                      uint64_t seed, int64_t generation, uint32_t instance, void *cuda_stream);
+int de_crossover_apply(float *u, const float *x, const float *v, int64_t ld, int32_t N, int32_t D,
+                       double CR, de_crossover xo, uint64_t seed, int64_t generation, uint32_t instance,
+                       void *cuda_stream);
+
 /* ---- misc ----------------------------------------------------------------- */
 const char *de_strerror(int code);
 

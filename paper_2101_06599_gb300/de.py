@@ -107,6 +107,8 @@ def load_library(build_if_missing: bool = True):
         "de_batch_size": ([vp, C.POINTER(i32)], C.c_int),
         "de_nec_step_noalloc": ([vp, vp, vp, vp, i32, i32, i32, f32, f64, C.c_int, de_bounds, C.c_uint64,
                                  i64, vp], C.c_int),
+        "de_crossover_mask": ([vp, i64, i32, i32, f64, C.c_int, C.c_uint64, i64, C.c_uint32, vp], C.c_int),
+        "de_crossover_apply": ([vp, vp, vp, i64, i32, i32, f64, C.c_int, C.c_uint64, i64, C.c_uint32, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -537,3 +539,23 @@ class Optimizer:
             self.close()
         except Exception:
             pass
+
+
+def de_crossover_mask(mask, ld, N, D, CR, xo, seed, generation, instance=0, stream=None):
+    """The N x D crossover mask of generation `generation` (1 = the gene
+    crosses) into device bytes at `mask` (rows of `ld` bytes), the draws of
+    de_step. See include/de.h."""
+    xo_i = XOVER[xo] if isinstance(xo, str) else int(xo)
+    _check(load_library().de_crossover_mask(
+        C.c_void_p(mask), int(ld), int(N), int(D), float(CR), xo_i, int(seed) & (2**64 - 1), int(generation),
+        int(instance), C.c_void_p(stream) if stream else None), "de_crossover_mask")
+
+
+def de_crossover_apply(u, x, v, ld, N, D, CR, xo, seed, generation, instance=0, stream=None):
+    """U = mask ? V : X on device matrices (rows of `ld` floats), the mask of
+    de_crossover_mask. See include/de.h."""
+    xo_i = XOVER[xo] if isinstance(xo, str) else int(xo)
+    _check(load_library().de_crossover_apply(
+        C.c_void_p(u), C.c_void_p(x), C.c_void_p(v), int(ld), int(N), int(D), float(CR), xo_i,
+        int(seed) & (2**64 - 1), int(generation), int(instance), C.c_void_p(stream) if stream else None),
+        "de_crossover_apply")

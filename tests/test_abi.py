@@ -84,6 +84,31 @@ def test_rotated_bound_parameters_are_validated(lib, extra):
         DE.BOUND.pop(7, None)
 
 
+@pytest.mark.parametrize("args", [
+    dict(ptr=0, ld=10, N=4, D=10, CR=0.5, xo=2),           # NULL output
+    dict(ptr=64, ld=9, N=4, D=10, CR=0.5, xo=2),           # ld < D
+    dict(ptr=64, ld=10, N=0, D=10, CR=0.5, xo=2),          # N < 1
+    dict(ptr=64, ld=10, N=4, D=10, CR=1.5, xo=2),          # Cr outside [0, 1]
+    dict(ptr=64, ld=10, N=4, D=10, CR=0.5, xo=7),          # no such crossover
+])
+def test_crossover_calls_validate_arguments(lib, args):
+    import ctypes as C
+    rc = lib.de_crossover_mask(C.c_void_p(args["ptr"]), args["ld"], args["N"], args["D"], args["CR"], args["xo"],
+                               1, 0, 0, None)
+    assert rc == DE.DE_EINVAL
+    rc = lib.de_crossover_apply(C.c_void_p(args["ptr"]), C.c_void_p(128), C.c_void_p(256), args["ld"], args["N"],
+                                args["D"], args["CR"], args["xo"], 1, 0, 0, None)
+    assert rc == DE.DE_EINVAL
+
+
+def test_crossover_apply_rejects_aliasing_and_bad_counters(lib):
+    import ctypes as C
+    p = C.c_void_p(64)
+    assert lib.de_crossover_apply(p, p, C.c_void_p(128), 10, 4, 10, 0.5, 2, 1, 0, 0, None) == DE.DE_EINVAL
+    assert lib.de_crossover_mask(p, 10, 4, 10, 0.5, 2, 1, -1, 0, None) == DE.DE_EINVAL       # generation < 0
+    assert lib.de_crossover_mask(p, 10, 4, 10, 0.5, 2, 1, 0, 1 << 24, None) == DE.DE_EINVAL  # instance >= 2^24
+
+
 def test_null_context_calls_are_rejected(lib):
     assert lib.de_step(None) == DE.DE_EINVAL
     assert lib.de_run(None, 3) == DE.DE_EINVAL
