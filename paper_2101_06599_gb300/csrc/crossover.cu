@@ -112,7 +112,30 @@ __global__ void __launch_bounds__(kXoWarps * 32) xo_apply_kernel(const __grid_co
   int jrand, L;
   xo_row_draws<XO>(p, cr, g, i, lane, jrand, L);
   const size_t base = (size_t)i * (size_t)ld;
-  for (int q = lane; q < p.D4; q += 32) {
+  const int full4 = VEC ? p.D / 4 : 0;              // slots whose 4 genes are all < D
+  constexpr int U = 4;                               // slots per lane in flight
+  int q0 = 0;
+  for (; q0 + 32 * U <= full4; q0 += 32 * U) {
+    float4 xv[U], vv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int j0 = 4 * (q0 + lane + 32 * k);
+      xv[k] = ld_stream(reinterpret_cast<const float4*>(x + base + j0));
+      vv[k] = ld_stream(reinterpret_cast<const float4*>(v + base + j0));
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int q = q0 + lane + 32 * k;
+      const unsigned m = xo_slot_mask<XO>(p, g, i, q, jrand, L);
+      float4 o;
+      o.x = (m & 1u) ? vv[k].x : xv[k].x;
+      o.y = (m & 2u) ? vv[k].y : xv[k].y;
+      o.z = (m & 4u) ? vv[k].z : xv[k].z;
+      o.w = (m & 8u) ? vv[k].w : xv[k].w;
+      st_stream(reinterpret_cast<float4*>(u + base + 4 * q), o);
+    }
+  }
+  for (int q = q0 + lane; q < p.D4; q += 32) {
     const unsigned m = xo_slot_mask<XO>(p, g, i, q, jrand, L);
     const int j0 = 4 * q;
     if (VEC && j0 + 4 <= p.D) {
