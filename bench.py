@@ -350,6 +350,57 @@ def time_crossover_grid(DE, torch, reps=100):
     return out
 
 
+# The paper's DE workloads (its parameter table) and its CUDA-DE rows (GTX 760):
+# (objective, D, Np, F, Cr, generations, box, Ackley constant), paper {crossover: (best value, best gen, s)}
+PAPER_TABLE2 = [
+    ("ackley", 1000, 500, 0.5, 0.2, 30000, (-30.0, 30.0), 0.02,
+     {"nec": (2.62e-05, 29991, 323.97), "bin": (2.28e-04, 29983, 321.45)}),
+    ("griewank", 500, 300, 0.25, 0.45, 20000, (-400.0, 400.0), 0.0,
+     {"nec": (1.73e-16, 19936, 149.03), "bin": (2.22e-16, 6041, 143.95)}),
+    ("rosenbrock", 50, 100, 0.65, 0.95, 10000, (-5.12, 5.12), 0.0,
+     {"nec": (1.16e-07, 9996, 58.92), "bin": (9.93e-10, 10000, 56.72)}),
+]
+
+
+def time_paper_table2(DE, torch, chunk=1000):
+    """The paper's three DE runs (Ackley 1000-D / 500 individuals / 30000
+    generations with its printed inner constant 0.02, Griewank 500-D / 300 /
+    20000 on [-400, 400], Rosenbrock 50-D / 100 / 10000) with NEC (DE/rand/1/L)
+    and binomial crossover: total device time of all generations (graphs of
+    `chunk` generations), best value and best generation. The best values are
+    not a parity claim: the random streams differ from the paper's."""
+    out = []
+    for obj, D, Np, F, CR, G, box, b, paper in PAPER_TABLE2:
+        for xo in ("nec", "bin"):
+            params = {"ackley_b": b} if b else None
+            opt = DE.Optimizer(Np, D, F=F, CR=CR, xo=xo, obj=obj, bounds=box, seed=SEED, params=params)
+            try:
+                opt.run(chunk)                            # builds the graph; counted below from a fresh start
+                opt.synchronize()
+                opt.close()
+                opt = DE.Optimizer(Np, D, F=F, CR=CR, xo=xo, obj=obj, bounds=box, seed=SEED, params=params)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(opt.stream)
+                done = 0
+                while done < G:
+                    k = min(chunk, G - done)
+                    opt.run(k)
+                    done += k
+                ev1.record(opt.stream)
+                ev1.synchronize()
+                sec = ev0.elapsed_time(ev1) / 1e3
+                st = opt.stats()
+            finally:
+                opt.close()
+            out.append({"objective": obj, "D": D, "Np": Np, "F": F, "CR": CR, "generations": G,
+                        "crossover": xo, "seconds": sec, "us_per_gen": 1e6 * sec / G,
+                        "value": Np * D * G / sec, "best_value": st["best_f"], "best_gen": st["best_gen"],
+                        "paper_cuda_gtx760": {"best_value": paper[xo][0], "best_gen": paper[xo][1],
+                                              "seconds": paper[xo][2]}})
+    return out
+
+
 _dist = None
 
 
@@ -446,7 +497,8 @@ def main():
     ap.add_argument("--batch-instances", type=int, default=0,
                     help="batched leg: keep the first K of the 512 instances (profiling)")
     ap.add_argument("--no-crossover", action="store_true")
-    ap.add_argument("--only", choices=["rotated", "small", "batched", "crossover"],
+    ap.add_argument("--no-table2", action="store_true")
+    ap.add_argument("--only", choices=["rotated", "small", "batched", "crossover", "table2"],
                     help="run one side workload alone (for profiling); prints its own JSON line")
     ap.add_argument("--N", type=int, default=N_DEF, help="rows (smaller cases for profiling)")
     ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
@@ -481,6 +533,8 @@ def main():
             res = time_small_configs(DE, torch, W)
         elif args.only == "crossover":
             res = time_crossover_grid(DE, torch)
+        elif args.only == "table2":
+            res = time_paper_table2(DE, torch)
         else:
             res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0], args.batch_instances)
         if rank == 0:
@@ -557,6 +611,10 @@ def main():
     if not args.no_crossover:
         xgrid = time_crossover_grid(DE, torch)
 
+    table2 = None
+    if not args.no_table2:
+        table2 = time_paper_table2(DE, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, timed, secs = oracle_generation_rate(N, D, "rosenbrock", "nec", 12.0)
@@ -575,7 +633,7 @@ def main():
                        "l2": "inputs larger than L2 (two 0.66 GB population buffers), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
             "clocks": clk.summary(), "variants": variants, "batched": batched, "rotated": rotated,
-            "small_configs": small, "crossover_table1": xgrid,
+            "small_configs": small, "crossover_table1": xgrid, "paper_table2": table2,
         }
         print(json.dumps(line))
     if _dist is not None:
