@@ -124,6 +124,34 @@ def test_lockstep_generations_sphere_N100_D30(xo):
         opt.close()
 
 
+@pytest.mark.parametrize("xo", ["bin", "nec"])
+@pytest.mark.parametrize("obj,D,N,F,CR,box,b,G", [
+    ("ackley", 1000, 500, 0.5, 0.2, (-30.0, 30.0), 0.02, 40),
+    ("griewank", 500, 300, 0.25, 0.45, (-400.0, 400.0), 0.2, 60),
+    ("rosenbrock", 50, 100, 0.65, 0.95, (-5.12, 5.12), 0.2, 300),
+])
+def test_lockstep_generations_paper_workloads(xo, obj, D, N, F, CR, box, b, G):
+    """The paper's three DE workloads (its parameter table): every generation
+    checked against the oracle stepping from the GPU's own population."""
+    seed = 1
+    lo, hi = box
+    opt = DE.Optimizer(N, D, F=F, CR=CR, xo=xo, obj=obj, bounds=box, seed=seed, params={"ackley_b": b})
+    try:
+        for g in range(G):
+            pop, fit32 = opt.population()
+            fit64 = O.evaluate(obj, pop, ackley_b=b)
+            check_fitness(fit32, fit64, "gen %d fitness" % g)
+            trial, ft, acc, draws = opt.debug_step()
+            s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g, ackley_b=b)
+            assert np.array_equal(draws, s.draws)
+            assert np.array_equal(trial.view(np.uint32), s.trial.view(np.uint32))
+            check_fitness(ft, s.ftrial, "gen %d trial fitness" % g)
+            amb = np.abs(s.ftrial - fit64) <= tol(s.ftrial) + tol(fit64)
+            assert np.array_equal(acc[~amb], s.accept[~amb])
+    finally:
+        opt.close()
+
+
 def test_run_graph_matches_steps_and_stats():
     N, D = 96, 200
     a, lo, hi = make(N, D, "nec", "rastrigin", seed=5)
