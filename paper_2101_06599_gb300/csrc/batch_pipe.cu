@@ -38,12 +38,9 @@ struct BpMeta {
   float fit_i;
 };
 
-// One row's copies and metadata, prepared by its producer lane.
-struct BpIssue {
-  const float* src[4];             // parent row, donors r1, r2, r3
-  int inst, i, jrand, L, si, r1, r2, r3, seg_ok, a0, len0, len1;
-  float fit_i;
-  uint32_t row_bytes;
+struct BpPlan {
+  int inst, i;
+  RowPlan32 pl;
 };
 
 struct BpLayout {
@@ -59,7 +56,7 @@ __host__ __device__ inline BpLayout bp_layout(int stage_floats) {
   L.abort = 16u * slots;
   L.meta = bp_align128(L.abort + 16u);
   L.plan = bp_align128(L.meta + (unsigned)(slots * sizeof(BpMeta)));
-  L.stage = bp_align128(L.plan + (unsigned)(32 * sizeof(BpIssue)));
+  L.stage = bp_align128(L.plan + (unsigned)(32 * sizeof(BpPlan)));
   L.total = L.stage + (unsigned)slots * (unsigned)stage_floats * 4u;
   return L;
 }
@@ -162,73 +159,57 @@ batch_pipe_kernel(const BatchInst* __restrict__ insts, const BatchRow* __restric
 
   if (warp == 0) {
     // ------------------------------ producer ------------------------------
-    // every lane prepares one of the next 32 rows (plan, instance, addresses,
-    // span pieces); lane 0 then refills each row's slot as soon as its
-    // consumer released it: copy the metadata, arm the barrier, issue the copies
-    BpIssue* prep = reinterpret_cast<BpIssue*>(smem + lay.plan);
+    // rows go out SL at a time from an SL-aligned base, so lane k < SL owns
+    // the distinct slot of row base + k: no lane ever waits on another lane
     int issued = 0;
-    for (int base = 0; base < ncta; base += 32) {
+    for (int base = 0; base < ncta; base += SL) {
       if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? *abort_flag : 0, 0)) break;
-      const int n = base + lane;
-      if (n < ncta) {
-        const BatchRow r = rows[b + n * G];
+      const int n2 = base + lane;
+      bool ok = true;
+      if (lane < SL && n2 < ncta) {
+        const int w = n2 % kBpCW, kk = n2 / kBpCW, s = kk % kBpStages, use = kk / kBpStages;
+        const int slot = w * kBpStages + s;
+        const BatchRow r = rows[b + n2 * G];
         const RowPlan32 pl = plans[insts[r.inst].row_base + r.i];
         const GenParams& p = insts[r.inst].g;
-        BpIssue e;
-        e.inst = r.inst;
-        e.i = r.i;
-        e.jrand = pl.jrand;
-        e.L = pl.L;
-        e.si = (int)(pl.slots & 0xFFu);
-        e.r1 = pl.r1; e.r2 = pl.r2; e.r3 = pl.r3;
-        e.fit_i = pl.fit_i;
-        const int e0 = min(pl.jrand + pl.L, p.D);           // piece 0 genes [jrand, e0)
-        e.a0 = pl.jrand & ~3;
-        e.len0 = ((e0 + 3) & ~3) - e.a0;
-        const int wrap = pl.jrand + pl.L - p.D;             // piece 1 genes [0, wrap)
-        e.len1 = wrap > 0 ? ((wrap + 3) & ~3) : 0;
-        e.seg_ok = (e.len0 + e.len1 <= segcap) ? 1 : 0;
-        e.src[0] = (e.si ? p.pop1 : p.pop0) + (size_t)r.i * p.pitch;
-        e.src[1] = (((pl.slots >> 8) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch;
-        e.src[2] = (((pl.slots >> 16) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r2 * p.pitch;
-        e.src[3] = (((pl.slots >> 24) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r3 * p.pitch;
-        e.row_bytes = 16u * (uint32_t)p.D4;
-        prep[lane] = e;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        const int cnt = min(32, ncta - base);
-        for (int k = 0; k < cnt; ++k) {
-          const int n2 = base + k;
-          const int w = n2 % kBpCW, kk = n2 / kBpCW, s = kk % kBpStages, use = kk / kBpStages;
-          const int slot = w * kBpStages + s;
-          if (use > 0 && !mbar_wait(smem_u32(empty + slot), (uint32_t)((use - 1) & 1))) {
-            bp_flag_error(insts, abort_flag);
-            break;
-          }
-          const BpIssue& e = prep[k];
+        if (use > 0 && !mbar_wait(smem_u32(empty + slot), (uint32_t)((use - 1) & 1))) {
+          bp_flag_error(insts, abort_flag);
+          ok = false;
+        }
+        if (ok) {
+          const int si = (int)(pl.slots & 0xFFu);
+          const int e0 = min(pl.jrand + pl.L, p.D);           // piece 0 genes [jrand, e0)
+          const int a0 = pl.jrand & ~3;
+          const int len0 = ((e0 + 3) & ~3) - a0;
+          const int wrap = pl.jrand + pl.L - p.D;             // piece 1 genes [0, wrap)
+          const int len1 = wrap > 0 ? ((wrap + 3) & ~3) : 0;
+          const int seg_ok = (len0 + len1 <= segcap) ? 1 : 0;
+          const float* src[4] = {(si ? p.pop1 : p.pop0) + (size_t)r.i * p.pitch,
+                                 (((pl.slots >> 8) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch,
+                                 (((pl.slots >> 16) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r2 * p.pitch,
+                                 (((pl.slots >> 24) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r3 * p.pitch};
           BpMeta& m = meta[slot];
-          m.dsrc[0] = e.src[1]; m.dsrc[1] = e.src[2]; m.dsrc[2] = e.src[3];
-          m.inst = e.inst; m.i = e.i; m.jrand = e.jrand; m.L = e.L; m.si = e.si;
-          m.r1 = e.r1; m.r2 = e.r2; m.r3 = e.r3; m.seg_ok = e.seg_ok;
-          m.a0 = e.a0; m.len0 = e.len0; m.fit_i = e.fit_i;
+          m.dsrc[0] = src[1]; m.dsrc[1] = src[2]; m.dsrc[2] = src[3];
+          m.inst = r.inst; m.i = r.i; m.jrand = pl.jrand; m.L = pl.L; m.si = si;
+          m.r1 = pl.r1; m.r2 = pl.r2; m.r3 = pl.r3; m.seg_ok = seg_ok;
+          m.a0 = a0; m.len0 = len0; m.fit_i = pl.fit_i;
+          const uint32_t row_bytes = 16u * (uint32_t)p.D4;
           const uint32_t fb = smem_u32(full + slot);
-          mbar_arrive_expect_tx(fb, e.row_bytes + (e.seg_ok ? 12u * (uint32_t)(e.len0 + e.len1) : 0u));
+          mbar_arrive_expect_tx(fb, row_bytes + (seg_ok ? 12u * (uint32_t)(len0 + len1) : 0u));
           float* st = stages + (size_t)slot * stage_floats;
-          bulk_g2s(smem_u32(st), e.src[0], e.row_bytes, fb);
-          if (e.seg_ok) {
+          bulk_g2s(smem_u32(st), src[0], row_bytes, fb);
+          if (seg_ok) {
 #pragma unroll
             for (int k3 = 0; k3 < 3; ++k3) {
               const uint32_t sd = smem_u32(st + seg_off + k3 * segcap);
-              bulk_g2s(sd, e.src[1 + k3] + e.a0, 4u * (uint32_t)e.len0, fb);
-              if (e.len1 > 0) bulk_g2s(sd + 4u * (uint32_t)e.len0, e.src[1 + k3], 4u * (uint32_t)e.len1, fb);
+              bulk_g2s(sd, src[1 + k3] + a0, 4u * (uint32_t)len0, fb);
+              if (len1 > 0) bulk_g2s(sd + 4u * (uint32_t)len0, src[1 + k3], 4u * (uint32_t)len1, fb);
             }
           }
-          ++issued;
         }
       }
-      issued = __shfl_sync(0xFFFFFFFFu, issued, 0);
       __syncwarp();
+      issued = min(ncta, base + SL);
     }
     // drain: the copies of the last armed stages must have landed before exit;
     // each slot is waited on for its last use only (an older phase of a slot
