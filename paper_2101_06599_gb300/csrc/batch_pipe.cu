@@ -140,6 +140,7 @@ batch_pipe_kernel(const BatchInst* __restrict__ insts, const BatchRow* __restric
   uint64_t* empty = full + SL;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + lay.abort);
   BpMeta* meta = reinterpret_cast<BpMeta*>(smem + lay.meta);
+  BpPlan* plan = reinterpret_cast<BpPlan*>(smem + lay.plan);
   float* stages = reinterpret_cast<float*>(smem + lay.stage);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -159,24 +160,32 @@ batch_pipe_kernel(const BatchInst* __restrict__ insts, const BatchRow* __restric
 
   if (warp == 0) {
     // ------------------------------ producer ------------------------------
-    // rows go out SL at a time from an SL-aligned base, so lane k < SL owns
-    // the distinct slot of row base + k: no lane ever waits on another lane
     int issued = 0;
-    for (int base = 0; base < ncta; base += SL) {
+    for (int base = 0; base < ncta; base += 32) {
       if (__shfl_sync(0xFFFFFFFFu, lane == 0 ? *abort_flag : 0, 0)) break;
-      const int n2 = base + lane;
-      bool ok = true;
-      if (lane < SL && n2 < ncta) {
-        const int w = n2 % kBpCW, kk = n2 / kBpCW, s = kk % kBpStages, use = kk / kBpStages;
-        const int slot = w * kBpStages + s;
-        const BatchRow r = rows[b + n2 * G];
-        const RowPlan32 pl = plans[insts[r.inst].row_base + r.i];
-        const GenParams& p = insts[r.inst].g;
-        if (use > 0 && !mbar_wait(smem_u32(empty + slot), (uint32_t)((use - 1) & 1))) {
-          bp_flag_error(insts, abort_flag);
-          ok = false;
-        }
-        if (ok) {
+      const int n = base + lane;
+      if (n < ncta) {
+        const BatchRow r = rows[b + n * G];
+        BpPlan e;
+        e.inst = r.inst;
+        e.i = r.i;
+        e.pl = plans[insts[r.inst].row_base + r.i];
+        plan[lane] = e;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const int cnt = min(32, ncta - base);
+        for (int k = 0; k < cnt; ++k) {
+          const int n2 = base + k;
+          const int w = n2 % kBpCW, kk = n2 / kBpCW, s = kk % kBpStages, use = kk / kBpStages;
+          const int slot = w * kBpStages + s;
+          if (use > 0 && !mbar_wait(smem_u32(empty + slot), (uint32_t)((use - 1) & 1))) {
+            bp_flag_error(insts, abort_flag);
+            break;
+          }
+          const BpPlan e = plan[k];
+          const GenParams& p = insts[e.inst].g;
+          const RowPlan32& pl = e.pl;
           const int si = (int)(pl.slots & 0xFFu);
           const int e0 = min(pl.jrand + pl.L, p.D);           // piece 0 genes [jrand, e0)
           const int a0 = pl.jrand & ~3;
@@ -184,13 +193,13 @@ batch_pipe_kernel(const BatchInst* __restrict__ insts, const BatchRow* __restric
           const int wrap = pl.jrand + pl.L - p.D;             // piece 1 genes [0, wrap)
           const int len1 = wrap > 0 ? ((wrap + 3) & ~3) : 0;
           const int seg_ok = (len0 + len1 <= segcap) ? 1 : 0;
-          const float* src[4] = {(si ? p.pop1 : p.pop0) + (size_t)r.i * p.pitch,
+          const float* src[4] = {(si ? p.pop1 : p.pop0) + (size_t)e.i * p.pitch,
                                  (((pl.slots >> 8) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch,
                                  (((pl.slots >> 16) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r2 * p.pitch,
                                  (((pl.slots >> 24) & 0xFFu) ? p.pop1 : p.pop0) + (size_t)pl.r3 * p.pitch};
           BpMeta& m = meta[slot];
           m.dsrc[0] = src[1]; m.dsrc[1] = src[2]; m.dsrc[2] = src[3];
-          m.inst = r.inst; m.i = r.i; m.jrand = pl.jrand; m.L = pl.L; m.si = si;
+          m.inst = e.inst; m.i = e.i; m.jrand = pl.jrand; m.L = pl.L; m.si = si;
           m.r1 = pl.r1; m.r2 = pl.r2; m.r3 = pl.r3; m.seg_ok = seg_ok;
           m.a0 = a0; m.len0 = len0; m.fit_i = pl.fit_i;
           const uint32_t row_bytes = 16u * (uint32_t)p.D4;
@@ -206,10 +215,10 @@ batch_pipe_kernel(const BatchInst* __restrict__ insts, const BatchRow* __restric
               if (len1 > 0) bulk_g2s(sd + 4u * (uint32_t)len0, src[1 + k3], 4u * (uint32_t)len1, fb);
             }
           }
+          ++issued;
         }
       }
       __syncwarp();
-      issued = min(ncta, base + SL);
     }
     // drain: the copies of the last armed stages must have landed before exit;
     // each slot is waited on for its last use only (an older phase of a slot
