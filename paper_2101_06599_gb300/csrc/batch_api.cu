@@ -51,33 +51,6 @@ static int upload_insts(de_ctx* c) {
   return sync_stream(c);
 }
 
-// Instances run by the pipelined kernel: segment crossovers with rows of
-// 256 .. 2048 genes. Their donor span buffer covers segments up to the
-// length exceeded with probability 1e-6 (P(L > n) = Cr^n), at most 256
-// floats; longer segments read their donor genes from global memory.
-static bool pipe_eligible(const de_ctx* c, int k) {
-  return c->bpipe_ok && c->bxo[k] != DE_XOVER_BIN && c->bp[k].D4 >= kBpMinD4 && c->bp[k].D4 <= kBpMaxD4;
-}
-
-static int span_floats(double CR, int D) {
-  int need = 16;
-  if (CR >= 1.0) need = D + 8;
-  else if (CR > 0.0) need = (int)std::min(1.0e6, std::ceil(std::log(1e-6) / std::log(CR))) + 16;
-  return std::max(16, std::min(256, (need + 3) & ~3));
-}
-
-static int upload_tiles(de_ctx* c, const std::vector<BatchTile>& t, BatchTile** dst) {
-  if (*dst) ctx_free(c, *dst);
-  *dst = nullptr;
-  if (t.empty()) return DE_OK;
-  *dst = (BatchTile*)ctx_alloc(c, t.size() * sizeof(BatchTile));
-  if (!*dst) return DE_ENOMEM;
-  if (cudaMemcpyAsync(*dst, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
-      cudaSuccess)
-    return DE_ECUDA;
-  return DE_OK;
-}
-
 static int build_tiles(de_ctx* c) {
   std::vector<int> order((size_t)c->n_inst);
   std::iota(order.begin(), order.end(), 0);
@@ -90,56 +63,38 @@ static int build_tiles(de_ctx* c) {
            (double)(kBatchThreadsHost / c->bgroup[b]) * c->bp[b].D;
   });
   // rows of G <= 32 lanes go to warp tiles of 32 / G rows, wider rows to CTA
-  // tiles of 256 / G rows (every instance: these lists also evaluate); the
-  // generation lists leave out the instances of the pipelined kernel
-  std::vector<BatchTile> wt, ct, gwt, gct;
-  std::vector<BatchRow> prow;
-  int segcap = 16, maxrow = 0;
+  // tiles of 256 / G rows
+  std::vector<BatchTile> wt, ct;
   c->bt0.assign((size_t)c->n_inst, 0);
   c->bt1.assign((size_t)c->n_inst, 0);
   for (int k : order) {
     const bool warp = c->bgroup[k] <= 32;
-    const bool piped = pipe_eligible(c, k);
     std::vector<BatchTile>& tiles = warp ? wt : ct;
     const int R = (warp ? 32 : kBatchThreadsHost) / c->bgroup[k];
     const int nt = (c->bp[k].N + R - 1) / R;
     c->bt0[k] = (int)tiles.size();
-    for (int t = 0; t < nt; ++t) {
-      tiles.push_back(BatchTile{k, t * R});
-      if (!piped) (warp ? gwt : gct).push_back(BatchTile{k, t * R});
-    }
+    for (int t = 0; t < nt; ++t) tiles.push_back(BatchTile{k, t * R});
     c->bt1[k] = (int)tiles.size();
-    if (piped) {
-      for (int i = 0; i < c->bp[k].N; ++i) prow.push_back(BatchRow{k, i});
-      segcap = std::max(segcap, span_floats(c->bcr[k], c->bp[k].D));
-      maxrow = std::max(maxrow, 4 * c->bp[k].D4);
-    }
   }
+  if (c->d_tiles) ctx_free(c, c->d_tiles);
+  if (c->d_ctiles) ctx_free(c, c->d_ctiles);
+  c->d_tiles = nullptr;
+  c->d_ctiles = nullptr;
   c->ntiles = (int)wt.size();
   c->nctiles = (int)ct.size();
-  c->ngtiles = (int)gwt.size();
-  c->ngctiles = (int)gct.size();
-  int rc = upload_tiles(c, wt, &c->d_tiles);
-  if (rc == DE_OK) rc = upload_tiles(c, ct, &c->d_ctiles);
-  if (rc == DE_OK) rc = upload_tiles(c, gwt, &c->d_gtiles);
-  if (rc == DE_OK) rc = upload_tiles(c, gct, &c->d_gctiles);
-  if (rc != DE_OK) return rc;
-  if (c->d_prows) ctx_free(c, c->d_prows);
-  c->d_prows = nullptr;
-  c->bpipe = BatchPipeLaunch{};
-  if (!prow.empty()) {
-    c->d_prows = (BatchRow*)ctx_alloc(c, prow.size() * sizeof(BatchRow));
-    if (!c->d_prows) return DE_ENOMEM;
-    if (cudaMemcpyAsync(c->d_prows, prow.data(), prow.size() * sizeof(BatchRow), cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess)
+  if (!wt.empty()) {
+    c->d_tiles = (BatchTile*)ctx_alloc(c, wt.size() * sizeof(BatchTile));
+    if (!c->d_tiles) return DE_ENOMEM;
+    if (cudaMemcpyAsync(c->d_tiles, wt.data(), wt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
       return DE_ECUDA;
-    BatchPipeLaunch& bl = c->bpipe;
-    bl.rows = c->d_prows;
-    bl.nrows = (int)prow.size();
-    bl.segcap = segcap;
-    bl.stage_floats = ((maxrow + 3 * segcap + 31) / 32) * 32;
-    bl.smem = batch_pipe_smem_bytes(bl.stage_floats);
-    bl.grid = std::max(1, c->sm_count);
+  }
+  if (!ct.empty()) {
+    c->d_ctiles = (BatchTile*)ctx_alloc(c, ct.size() * sizeof(BatchTile));
+    if (!c->d_ctiles) return DE_ENOMEM;
+    if (cudaMemcpyAsync(c->d_ctiles, ct.data(), ct.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return DE_ECUDA;
   }
   drop_graphs(c);
   return upload_insts(c);
@@ -164,9 +119,8 @@ static int batch_evaluate(de_ctx* c, int inst) {
 }
 
 cudaError_t batch_launch_generation(de_ctx* c, bool, int) {
-  return launch_batch_generation(c->d_insts, c->d_gtiles, c->ngtiles, c->d_gctiles, c->ngctiles, c->d_ptiles,
-                                 c->nptiles, c->d_plans, c->d_states, c->n_inst, c->batch_grid, c->bpipe,
-                                 c->stream);
+  return launch_batch_generation(c->d_insts, c->d_tiles, c->ntiles, c->d_ctiles, c->nctiles, c->d_ptiles,
+                                 c->nptiles, c->d_plans, c->d_states, c->n_inst, c->batch_grid, c->stream);
 }
 
 // Plan tiles: 256 consecutive rows of one instance, instances in order.
@@ -234,14 +188,6 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   c->batch_grid = std::max(1, c->sm_count) * 2;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaGetLastError();
-  {
-    // the largest stage any eligible instance can need: 2048 floats + 3 spans of 256
-    const size_t most = batch_pipe_smem_bytes(((4 * kBpMaxD4 + 3 * 256 + 31) / 32) * 32);
-    c->bpipe_ok = c->sm_count > 0 && c->smem_optin >= (int)most && prepare_batch_pipe(most) == cudaSuccess;
-    cudaGetLastError();
-  }
 
   // arena layout
   auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };

@@ -67,14 +67,6 @@ struct de_ctx {
   std::vector<long long> brow_base;
   de::DevState* d_states = nullptr;
   int ntiles = 0, nctiles = 0, batch_grid = 0, max_pitch = 0;
-  // generation lists: the tiles of instances not run by the pipelined kernel,
-  // and that kernel's rows and shape (evaluation uses d_tiles / d_ctiles)
-  de::BatchTile* d_gtiles = nullptr;
-  de::BatchTile* d_gctiles = nullptr;
-  de::BatchRow* d_prows = nullptr;
-  int ngtiles = 0, ngctiles = 0;
-  de::BatchPipeLaunch bpipe{};
-  bool bpipe_ok = false;             // the pipelined kernel's largest stage fits the SM
   // shifted-rotated objectives (sr_api.cu)
   bool rotated = false;
   de::SrParams sp{};

@@ -55,30 +55,13 @@ struct RowPlan32 {
   float fit_i;
   int pad;
 };
-// One row of a batched instance in the pipelined kernel's row list.
-struct BatchRow {
-  int inst, i;
-};
-// The pipelined kernel's part of a batched generation (batch_pipe.cu).
-struct BatchPipeLaunch {
-  const BatchRow* rows;
-  int nrows, segcap, stage_floats, grid;
-  size_t smem;
-};
-constexpr int kBpMinD4 = 64;       // rows of at least 256 genes fill a consumer warp
-constexpr int kBpMaxD4 = 512;      // and at most 2048 fit a stage
-unsigned batch_pipe_smem_bytes(int stage_floats);
-cudaError_t prepare_batch_pipe(size_t smem);
-cudaError_t launch_batch_pipe(const BatchInst* insts, const BatchRow* rows, int nrows, const RowPlan32* plans,
-                              int segcap, int stage_floats, size_t smem, int grid, cudaStream_t s);
 constexpr int kBatchThreadsHost = 256;
 constexpr int kBatchMaxGroup = 256;
 constexpr int kBatchMaxD4PerLane = 16;
 // plan kernel + row kernel + close kernel (one generation of every instance)
 cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
                                     const BatchTile* ctiles, int nctiles, const BatchTile* ptiles, int nptiles,
-                                    RowPlan32* plans, DevState* states, int n_inst, int grid,
-                                    const BatchPipeLaunch& pipe, cudaStream_t s);
+                                    RowPlan32* plans, DevState* states, int n_inst, int grid, cudaStream_t s);
 // reset best keys, evaluate the parents of the tiles' rows, close (instances
 // first_inst .. first_inst + n_inst - 1)
 cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
