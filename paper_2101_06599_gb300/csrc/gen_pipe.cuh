@@ -268,9 +268,40 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
       if (patched) fence_proxy_async_smem();      // patches precede the stage's next bulk fill
       named_bar_sync(2, NC);                      // patched genes visible to every consumer
 
-      // 2. fitness of the trial, from shared memory
-      Acc a{0.0f, 0.0f, 0.0f};
-      for (int q = ct; q < p.D4; q += NC) {
+      // 2. fitness of the trial, from shared memory: slots whose four genes
+      //    are all in the row go two at a time into two independent partial
+      //    sums (shorter dependency chains), the rest through the checked loop
+      Acc a{0.0f, 0.0f, 0.0f}, a2{0.0f, 0.0f, 0.0f};
+      const int qfull = p.D >> 2;
+      int q0 = ct;
+      for (; q0 + NC < qfull; q0 += 2 * NC) {
+        const float4 v0 = ld_shared_v4(row + 4 * q0);
+        const float4 v1 = ld_shared_v4(row + 4 * (q0 + NC));
+        const int j0 = 4 * q0, j1 = 4 * (q0 + NC);
+        if constexpr (OBJ == kRosenbrock) {
+          accum_pair(a, v0.x, v0.y);
+          accum_pair(a2, v1.x, v1.y);
+          accum_pair(a, v0.y, v0.z);
+          accum_pair(a2, v1.y, v1.z);
+          accum_pair(a, v0.z, v0.w);
+          accum_pair(a2, v1.z, v1.w);
+          if (j0 + 4 < p.D) accum_pair(a, v0.w, row[j0 + 4]);
+          if (j1 + 4 < p.D) accum_pair(a2, v1.w, row[j1 + 4]);
+        } else {
+          accum_gene<OBJ>(a, v0.x, j0, p);
+          accum_gene<OBJ>(a2, v1.x, j1, p);
+          accum_gene<OBJ>(a, v0.y, j0 + 1, p);
+          accum_gene<OBJ>(a2, v1.y, j1 + 1, p);
+          accum_gene<OBJ>(a, v0.z, j0 + 2, p);
+          accum_gene<OBJ>(a2, v1.z, j1 + 2, p);
+          accum_gene<OBJ>(a, v0.w, j0 + 3, p);
+          accum_gene<OBJ>(a2, v1.w, j1 + 3, p);
+        }
+      }
+      a.a += a2.a;
+      a.b += a2.b;
+      a.c += a2.c;
+      for (int q = q0; q < p.D4; q += NC) {
         const float4 v = ld_shared_v4(row + 4 * q);
         const int j0 = 4 * q;
         if constexpr (OBJ == kRosenbrock) {
