@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 2) gen_stream_kernel(const 
     r.d2 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd2, 0));
     r.d3 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd3, 0));
 
-    // pass 1: the trial's objective
-    Acc s{0.0f, 0.0f, 0.0f};
+    // pass 1: the trial's objective (even and odd slots of a chunk into two
+    // independent partial sums: shorter dependency chains)
+    Acc s{0.0f, 0.0f, 0.0f}, s2{0.0f, 0.0f, 0.0f};
     int cnt = 0;
     float carry = 0.0f;                              // Rosenbrock: last gene of the previous chunk
     for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
@@ -143,28 +144,32 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 2) gen_stream_kernel(const 
         if constexpr (XO == kBin) cnt += __popc(m[u]);
         const int q = q0 + lane + 32 * u;
         const int j0 = 4 * q;
+        Acc& su = (u & 1) ? s2 : s;
         if constexpr (OBJ == kRosenbrock) {
           float nb = __shfl_down_sync(0xFFFFFFFFu, v[u].x, 1);
           const float first_next = (u + 1 < kStreamU) ? __shfl_sync(0xFFFFFFFFu, v[(u + 1) % kStreamU].x, 0) : 0.0f;
           if (lane == 31) nb = first_next;
-          if (u == 0 && lane == 0 && q0 > 0) accum_pair(s, carry, v[0].x);   // the pair across chunks
+          if (u == 0 && lane == 0 && q0 > 0) accum_pair(su, carry, v[0].x);   // the pair across chunks
           if (q < p.D4) {
-            if (j0 + 1 < p.D) accum_pair(s, v[u].x, v[u].y);
-            if (j0 + 2 < p.D) accum_pair(s, v[u].y, v[u].z);
-            if (j0 + 3 < p.D) accum_pair(s, v[u].z, v[u].w);
-            if (j0 + 4 < p.D && !(lane == 31 && u + 1 == kStreamU)) accum_pair(s, v[u].w, nb);
+            if (j0 + 1 < p.D) accum_pair(su, v[u].x, v[u].y);
+            if (j0 + 2 < p.D) accum_pair(su, v[u].y, v[u].z);
+            if (j0 + 3 < p.D) accum_pair(su, v[u].z, v[u].w);
+            if (j0 + 4 < p.D && !(lane == 31 && u + 1 == kStreamU)) accum_pair(su, v[u].w, nb);
           }
         } else {
           if (q < p.D4) {
-            accum_gene<OBJ>(s, v[u].x, j0, p);
-            if (j0 + 1 < p.D) accum_gene<OBJ>(s, v[u].y, j0 + 1, p);
-            if (j0 + 2 < p.D) accum_gene<OBJ>(s, v[u].z, j0 + 2, p);
-            if (j0 + 3 < p.D) accum_gene<OBJ>(s, v[u].w, j0 + 3, p);
+            accum_gene<OBJ>(su, v[u].x, j0, p);
+            if (j0 + 1 < p.D) accum_gene<OBJ>(su, v[u].y, j0 + 1, p);
+            if (j0 + 2 < p.D) accum_gene<OBJ>(su, v[u].z, j0 + 2, p);
+            if (j0 + 3 < p.D) accum_gene<OBJ>(su, v[u].w, j0 + 3, p);
           }
         }
       }
       if constexpr (OBJ == kRosenbrock) carry = __shfl_sync(0xFFFFFFFFu, v[kStreamU - 1].w, 31);
     }
+    s.a += s2.a;
+    s.b += s2.b;
+    s.c += s2.c;
     constexpr int NS = ObjTraits<OBJ>::kSums;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
