@@ -514,28 +514,13 @@ __device__ __forceinline__ void batch_rows_warp_xo(int xo, const BatchInst& I, c
 
 // Warp tiles: warp w of CTA b takes tiles b * 8 + w, then every
 // gridDim.x * 8-th; no CTA barrier anywhere.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_warp_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
                   const RowPlan32* __restrict__ plans, int eval_only) {
   const int warps = kBatchThreads / 32;
-  const int stride = gridDim.x * warps;
-  const int lane = threadIdx.x & 31;
-  for (int wt = blockIdx.x * warps + (threadIdx.x >> 5); wt < ntiles; wt += stride) {
+  for (int wt = blockIdx.x * warps + (threadIdx.x >> 5); wt < ntiles; wt += gridDim.x * warps) {
     const BatchTile tl = tiles[wt];
     const BatchInst& I = insts[tl.inst];
-    // while this tile runs, bring the next tile's plans and the descriptor
-    // after it into L2 (the next descriptor itself is one load away)
-    if (!eval_only && wt + stride < ntiles) {
-      const BatchTile tn = tiles[wt + stride];
-      const BatchInst& In = insts[tn.inst];
-      const int rows = 32 / In.group;
-      if (lane < rows && tn.row0 + lane < In.g.N) prefetch_l2(plans + In.row_base + tn.row0 + lane);
-      if (lane == 0 && wt + 2 * stride < ntiles) prefetch_l2(tiles + wt + 2 * stride);
-    }
     switch (I.obj) {                                 // uniform over the warp
       case kSphere: batch_rows_warp_xo<kSphere>(I.xo, I, tl, plans, eval_only); break;
       case kRastrigin: batch_rows_warp_xo<kRastrigin>(I.xo, I, tl, plans, eval_only); break;
