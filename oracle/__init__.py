@@ -81,6 +81,15 @@ def lib():
         L.or_step.restype = C.c_int
         L.or_argmin.argtypes = [C.c_int32, C.c_void_p]
         L.or_argmin.restype = C.c_int32
+        L.or_step_base.argtypes = L.or_step.argtypes + [C.c_int, C.c_int32]
+        L.or_step_base.restype = C.c_int
+        L.or_donors_base.argtypes = [C.c_int32, C.c_int32, C.c_uint64, C.c_uint32, C.c_int64, C.c_int32,
+                                     C.c_int, C.c_int32, C.c_void_p, C.c_void_p]
+        L.or_donors_base.restype = None
+        L.or_base_offset.argtypes = [C.c_int32, C.c_uint64, C.c_uint32, C.c_int64]
+        L.or_base_offset.restype = C.c_int32
+        L.or_base_perm.argtypes = [C.c_int32, C.c_uint64, C.c_uint32, C.c_int64, C.c_int32]
+        L.or_base_perm.restype = C.c_int32
         _lib = L
     return _lib
 
@@ -112,6 +121,26 @@ def donors(N, D, seed, g, i, inst=0):
     j = C.c_int32()
     lib().or_donors(N, D, seed, inst, g, i, r, C.byref(j))
     return (int(r[0]), int(r[1]), int(r[2])), int(j.value)
+
+
+BASE = {"distinct": 0, "random": 1, "offset": 2, "permutation": 3, "best": 4}
+
+
+def donors_base(N, D, seed, g, i, base, best=0, inst=0):
+    """(r0, r1, r2) and j_rand of row i under a base index rule."""
+    r = (C.c_int32 * 3)()
+    j = C.c_int32()
+    lib().or_donors_base(N, D, seed, inst, g, i, BASE[base] if isinstance(base, str) else int(base), best,
+                         r, C.byref(j))
+    return (int(r[0]), int(r[1]), int(r[2])), int(j.value)
+
+
+def base_offset(N, seed, g, inst=0):
+    return int(lib().or_base_offset(N, seed, inst, g))
+
+
+def base_perm(N, seed, g, i, inst=0):
+    return int(lib().or_base_perm(N, seed, inst, g, i))
 
 
 def nec_length(w, Cr, D):
@@ -176,8 +205,10 @@ class StepResult:
 
 
 def step(pop, fit, F, Cr, xo, obj, lo, hi, seed, g, inst=0, ackley_b=0.2,
-         shift=None, rot=None, rows=None, want_trial=True, want_mask=False):
-    """One generation of Alg. 1 (rows `rows` = (i0, i1), default all)."""
+         shift=None, rot=None, rows=None, want_trial=True, want_mask=False, base="distinct", best=None):
+    """One generation of Alg. 1 (rows `rows` = (i0, i1), default all) with a
+    base index rule; `best` (the best row at the start of the generation, for
+    the "best" rule) defaults to the argmin of `fit`."""
     pop = _f32(pop)
     fit = np.ascontiguousarray(fit, dtype=np.float64)
     N, D = pop.shape
@@ -191,17 +222,20 @@ def step(pop, fit, F, Cr, xo, obj, lo, hi, seed, g, inst=0, ackley_b=0.2,
     accept = np.empty(n, dtype=np.uint8)
     msk = np.empty((n, D), dtype=np.uint8) if want_mask else None
     shift, rot = _f32(shift), _f32(rot)
-    rc = lib().or_step(N, D, float(F), float(Cr), XO[xo], OBJ[obj] if isinstance(obj, str) else int(obj),
-                       float(lo), float(hi), int(seed), int(inst), int(g), float(ackley_b),
-                       _ptr(shift), _ptr(rot), _ptr(pop), _ptr(fit), _ptr(pop_out), _ptr(fit_out),
-                       i0, i1, _ptr(draws), _ptr(trial), _ptr(ftrial), _ptr(accept), _ptr(msk))
+    if best is None:
+        best = argmin(fit)
+    rc = lib().or_step_base(N, D, float(F), float(Cr), XO[xo], OBJ[obj] if isinstance(obj, str) else int(obj),
+                            float(lo), float(hi), int(seed), int(inst), int(g), float(ackley_b),
+                            _ptr(shift), _ptr(rot), _ptr(pop), _ptr(fit), _ptr(pop_out), _ptr(fit_out),
+                            i0, i1, _ptr(draws), _ptr(trial), _ptr(ftrial), _ptr(accept), _ptr(msk),
+                            BASE[base] if isinstance(base, str) else int(base), int(best))
     if rc != 0:
         raise ValueError("oracle step rejected its arguments")
     return StepResult(pop_out, fit_out, draws, trial, ftrial, accept.astype(bool), msk)
 
 
 def run(N, D, F, Cr, xo, obj, lo, hi, seed, G, inst=0, ackley_b=0.2, shift=None, rot=None,
-        pop=None):
+        pop=None, base="distinct"):
     """Init (or take `pop`), evaluate, then G generations. Returns
     (pop, fit, best_index, best_f, best_gen, accepts, sumL)."""
     if pop is None:
@@ -213,7 +247,7 @@ def run(N, D, F, Cr, xo, obj, lo, hi, seed, G, inst=0, ackley_b=0.2, shift=None,
     sumL = 0
     for g in range(G):
         s = step(pop, fit, F, Cr, xo, obj, lo, hi, seed, g, inst, ackley_b, shift, rot,
-                 want_trial=False)
+                 want_trial=False, base=base)
         pop, fit = s.pop, s.fit
         accepts += int(s.accept.sum())
         sumL += int(s.L.astype(np.int64).sum())

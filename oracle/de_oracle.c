@@ -123,6 +123,92 @@ void or_donors(int32_t N, int32_t D, uint64_t seed, uint32_t inst, int64_t g,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Base index rules. A per-generation draw uses the row field 2^32 - 1 of   */
+/* the counter (no population row has that index).                         */
+/* ------------------------------------------------------------------------ */
+int32_t or_base_offset(int32_t N, uint64_t seed, uint32_t inst, int64_t g)
+{
+  uint32_t w = or_word(seed, inst, OR_STREAM_IDX, g, -1, 0);
+  return 1 + randint_from_word(w, N - 1);
+}
+
+/* One Feistel round function on h-bit halves. */
+static uint32_t feistel_f(uint32_t r, uint32_t k, uint32_t mask)
+{
+  uint32_t t = (r ^ k) * 0x9E3779B1u;
+  t ^= t >> 15;
+  t *= 0x2C1B3C6Du;
+  t ^= t >> 13;
+  return t & mask;
+}
+
+/* A bijection of [0, N): a 4-round Feistel network on 2h bits (the least
+ * h >= 1 with 2^(2h) >= N), keyed by the 4 words of the generation's PERM
+ * block, applied until the value falls in [0, N) (cycle walking: the orbit
+ * of i under the bijection of [0, 2^(2h)) re-enters [0, N), and the first
+ * element it meets there defines a bijection of [0, N)). */
+int32_t or_base_perm(int32_t N, uint64_t seed, uint32_t inst, int64_t g, int32_t i)
+{
+  uint32_t k[4];
+  for (uint32_t q = 0; q < 4; q++) k[q] = or_word(seed, inst, OR_STREAM_PERM, g, -1, q);
+  int h = 1;
+  while ((1ull << (2 * h)) < (uint64_t)N) h++;
+  const uint32_t mask = (1u << h) - 1u;
+  uint32_t x = (uint32_t)i;
+  do {
+    uint32_t L = x >> h, R = x & mask;
+    for (int r = 0; r < 4; r++) {
+      uint32_t nR = L ^ feistel_f(R, k[r], mask);
+      L = R;
+      R = nR;
+    }
+    x = (L << h) | R;
+  } while (x >= (uint32_t)N);
+  return (int32_t)x;
+}
+
+void or_donors_base(int32_t N, int32_t D, uint64_t seed, uint32_t inst, int64_t g,
+                    int32_t i, int base, int32_t best, int32_t r[3], int32_t *jrand)
+{
+  if (base == OR_BASE_DISTINCT) {
+    or_donors(N, D, seed, inst, g, i, r, jrand);
+    return;
+  }
+  uint32_t w[4];
+  for (uint32_t k = 0; k < 4; k++) w[k] = or_word(seed, inst, OR_STREAM_IDX, g, i, k);
+  if (base == OR_BASE_BEST) {
+    /* r1, r2: distinct, != i and != best, by the same skip rule as or_donors
+       with {i, best} excluded from the start */
+    int32_t excl[4];
+    int n_excl = 0;
+    excl[n_excl++] = i < best ? i : best;
+    if (best != i) excl[n_excl++] = i < best ? best : i;
+    r[0] = best;
+    for (int k = 0; k < 2; k++) {
+      int32_t v = randint_from_word(w[k], N - n_excl);
+      for (int e = 0; e < n_excl; e++)
+        if (v >= excl[e]) v++;
+      r[1 + k] = v;
+      int pos = n_excl;
+      while (pos > 0 && excl[pos - 1] > v) { excl[pos] = excl[pos - 1]; pos--; }
+      excl[pos] = v;
+      n_excl++;
+    }
+    *jrand = randint_from_word(w[3], D);
+    return;
+  }
+  int32_t r0;
+  if (base == OR_BASE_RANDOM) r0 = randint_from_word(w[0], N);
+  else if (base == OR_BASE_OFFSET) r0 = (int32_t)(((int64_t)i + or_base_offset(N, seed, inst, g)) % N);
+  else r0 = or_base_perm(N, seed, inst, g, i);
+  /* Alg. 6: each difference row a non-zero offset from the previous index */
+  int32_t r1 = (int32_t)(((int64_t)r0 + 1 + randint_from_word(w[1], N - 1)) % N);
+  int32_t r2 = (int32_t)(((int64_t)r1 + 1 + randint_from_word(w[2], N - 1)) % N);
+  r[0] = r0; r[1] = r1; r[2] = r2;
+  *jrand = randint_from_word(w[3], D);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Eq. (9): L = 1 if Cr = 0; D if Cr = 1; else min(ceil(ln U / ln Cr), D).   */
 /* For U in (0,1) and Cr in (0,1), ceil(ln U / ln Cr) is the smallest n >= 1 */
 /* with Cr^n <= U (multiplying n >= ln U / ln Cr by ln Cr < 0 flips it).     */
@@ -339,7 +425,21 @@ int or_step(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
             int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
             uint8_t *mask_out)
 {
+  return or_step_base(N, D, F, Cr, xo, obj, lo, hi, seed, inst, g, ackley_b, shift, rot,
+                      pop_in, fit_in, pop_out, fit_out, i0, i1, draws, trial, ftrial,
+                      accept, mask_out, OR_BASE_DISTINCT, 0);
+}
+
+int or_step_base(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
+                 float lo, float hi, uint64_t seed, uint32_t inst, int64_t g,
+                 double ackley_b, const float *shift, const float *rot,
+                 const float *pop_in, const double *fit_in,
+                 float *pop_out, double *fit_out, int32_t i0, int32_t i1,
+                 int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
+                 uint8_t *mask_out, int base, int32_t best)
+{
   if (N < 4 || D < 1 || i0 < 0 || i1 > N || i0 > i1) return -1;
+  if (base < OR_BASE_DISTINCT || base > OR_BASE_BEST || best < 0 || best >= N) return -1;
   if (!(Cr >= 0.0 && Cr <= 1.0)) return -1;
   if (xo < OR_XO_BIN || xo > OR_XO_NEC) return -1;
 
@@ -355,7 +455,7 @@ int or_step(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
   for (int32_t i = i0; i < i1; i++) {
     const float *xi = pop_in + (size_t)i * D;
     int32_t r[3], jrand;
-    or_donors(N, D, seed, inst, g, i, r, &jrand);
+    or_donors_base(N, D, seed, inst, g, i, base, best, r, &jrand);
     const float *x1 = pop_in + (size_t)r[0] * D;
     const float *x2 = pop_in + (size_t)r[1] * D;
     const float *x3 = pop_in + (size_t)r[2] * D;

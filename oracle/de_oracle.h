@@ -35,7 +35,21 @@ enum {
 
 /* Philox stream identifiers (top 8 bits of the fourth counter word). */
 enum { OR_STREAM_INIT = 0, OR_STREAM_IDX = 1, OR_STREAM_LEN = 2,
-       OR_STREAM_BIN = 3, OR_STREAM_EXP = 4 };
+       OR_STREAM_BIN = 3, OR_STREAM_EXP = 4, OR_STREAM_PERM = 5 };
+
+/* Base index rules (Section 2 lists several; DE/rand/1 and DE/best/1):
+ * DISTINCT     r1, r2, r3 distinct and != i (the default, DE/rand/1);
+ * RANDOM       Alg. 3: r0 uniform over all rows, then Alg. 6: r1 = r0 + k1,
+ *              r2 = r1 + k2 (mod N), k1, k2 uniform in [1, N-1];
+ * OFFSET       Alg. 4: r0 = i + r_g (mod N), one r_g in [1, N-1] per
+ *              generation, then Alg. 6;
+ * PERMUTATION  Alg. 5: r0 = pi_g(i), a permutation of the rows per
+ *              generation, then Alg. 6;
+ * BEST         DE/best/1: r0 = the best row at the start of the generation,
+ *              r1, r2 distinct, != i and != that row (the skip rule of the
+ *              distinct donors with both excluded). */
+enum { OR_BASE_DISTINCT = 0, OR_BASE_RANDOM = 1, OR_BASE_OFFSET = 2,
+       OR_BASE_PERMUTATION = 3, OR_BASE_BEST = 4 };
 
 /* Philox4x32-10 block function (Salmon et al., SC'11). */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -48,6 +62,18 @@ uint32_t or_word(uint64_t seed, uint32_t inst, uint32_t stream, int64_t g,
 /* Donors r[0..2] (distinct, all != i) and j_rand for row i. */
 void or_donors(int32_t N, int32_t D, uint64_t seed, uint32_t inst, int64_t g,
                int32_t i, int32_t r[3], int32_t *jrand);
+
+/* Base and difference indices of row i under a base rule (r[0] is the base
+ * vector's row, r[1] and r[2] the difference rows) and j_rand. `best` is the
+ * best row at the start of generation g (read by BEST only). */
+void or_donors_base(int32_t N, int32_t D, uint64_t seed, uint32_t inst, int64_t g,
+                    int32_t i, int base, int32_t best, int32_t r[3], int32_t *jrand);
+
+/* Alg. 4's offset of generation g, in [1, N-1]. */
+int32_t or_base_offset(int32_t N, uint64_t seed, uint32_t inst, int64_t g);
+
+/* Alg. 5's permutation of generation g at row i. */
+int32_t or_base_perm(int32_t N, uint64_t seed, uint32_t inst, int64_t g, int32_t i);
 
 /* Eq. (9) for one uniform word w (U = w / 2^32). */
 int32_t or_nec_length(uint32_t w, double Cr, int32_t D);
@@ -83,6 +109,15 @@ int or_step(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
             float *pop_out, double *fit_out, int32_t i0, int32_t i1,
             int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
             uint8_t *mask);
+
+/* or_step with a base index rule; `best` is read by OR_BASE_BEST only. */
+int or_step_base(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
+                 float lo, float hi, uint64_t seed, uint32_t inst, int64_t g,
+                 double ackley_b, const float *shift, const float *rot,
+                 const float *pop_in, const double *fit_in,
+                 float *pop_out, double *fit_out, int32_t i0, int32_t i1,
+                 int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
+                 uint8_t *mask, int base, int32_t best);
 
 /* Argmin of fit[0..N) with the lowest index winning ties; NaN counts as +inf. */
 int32_t or_argmin(int32_t N, const double *fit);
