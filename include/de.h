@@ -269,6 +269,36 @@ int de_batch_size(de_ctx *ctx, int32_t *n_inst);
 int de_set_launch(de_ctx *ctx, int32_t threads, int32_t vec4);
 int de_get_launch(de_ctx *ctx, int32_t *threads, int32_t *vec4);
 
+/* Base index rule: which rows form the mutant v = x_r0 + F (x_r1 - x_r2)
+ * (Eq. 1; Section 2 lists several base index selections):
+ *   DE_BASE_DISTINCT     r0, r1, r2 distinct and != i (DE/rand/1; default);
+ *   DE_BASE_RANDOM       Alg. 3: r0 uniform over all rows (i included), then
+ *                        Alg. 6: r1 = (r0 + k1) mod N, r2 = (r1 + k2) mod N with
+ *                        k1, k2 uniform in [1, N - 1];
+ *   DE_BASE_OFFSET       Alg. 4: r0 = (i + r_g) mod N, one r_g in [1, N - 1] per
+ *                        generation, then Alg. 6;
+ *   DE_BASE_PERMUTATION  Alg. 5: r0 = pi_g(i), a pseudorandom permutation of the
+ *                        rows per generation (a keyed Feistel network with cycle
+ *                        walking), then Alg. 6;
+ *   DE_BASE_BEST         DE/best/1: r0 = the best row when the previous
+ *                        generation closed (lowest value, lowest index), r1, r2
+ *                        distinct and != i, != r0.
+ * j_rand and the crossover draws do not depend on the rule. The debug draws
+ * report (r0, r1, r2). Every rule draws from the row's IDX block; OFFSET and
+ * PERMUTATION add a per-generation block (row field 2^32 - 1). */
+typedef enum {
+  DE_BASE_DISTINCT = 0,
+  DE_BASE_RANDOM = 1,
+  DE_BASE_OFFSET = 2,
+  DE_BASE_PERMUTATION = 3,
+  DE_BASE_BEST = 4
+} de_base;
+
+/* Set the base index rule of a context (every instance of a batch); it
+ * applies from the next generation. DE_EINVAL for an unknown rule. */
+int de_set_base(de_ctx *ctx, de_base base);
+int de_get_base(de_ctx *ctx, de_base *base);
+
 /* Generation kernel: 0 = automatic, 1 = one CTA per row (row held in
  * registers; every crossover, every D), 2 = persistent pipelined kernel (one
  * CTA per SM, a producer warp streams parent rows and the masked donor spans

@@ -633,6 +633,20 @@ int de_set_kernel(de_ctx* c, int32_t kind) {
   return DE_OK;
 }
 
+int de_set_base(de_ctx* c, de_base base) {
+  if (!c || (int)base < DE_BASE_DISTINCT || (int)base > DE_BASE_BEST) return DE_EINVAL;
+  if (c->batch) return batch_set_base(c, (int)base);
+  c->p.base = (int)base;
+  drop_graphs(c);
+  return DE_OK;
+}
+
+int de_get_base(de_ctx* c, de_base* base) {
+  if (!c || !base) return DE_EINVAL;
+  *base = (de_base)(c->batch ? (c->bp.empty() ? 0 : c->bp[0].base) : c->p.base);
+  return DE_OK;
+}
+
 int de_get_kernel(de_ctx* c, int32_t* kind) {
   if (!c || !kind) return DE_EINVAL;
   if (c->batch) return DE_ESTATE;

@@ -91,6 +91,7 @@ __global__ void best_from_fit_kernel(const __grid_constant__ GenParams p) {
 
 __global__ void close_eval_kernel(DevState* st) {
   st->best_f = from_ordered_bits((uint32_t)(st->best_key >> 32));
+  st->base_row = (int)(uint32_t)(st->best_key & 0xFFFFFFFFull);
   st->best_gen = st->gen;
   st->done = 0u;
 }

@@ -137,6 +137,12 @@ static int build_plan_tiles(de_ctx* c) {
   return sync_stream(c);
 }
 
+int batch_set_base(de_ctx* c, int base) {
+  for (int k = 0; k < c->n_inst; ++k) c->bp[k].base = base;
+  drop_graphs(c);
+  return upload_insts(c);
+}
+
 int batch_stats(de_ctx* c, de_stats_t* out) {
   std::vector<DevState> h((size_t)c->n_inst);
   if (cudaMemcpyAsync(h.data(), c->d_states, h.size() * sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=

@@ -567,6 +567,7 @@ __global__ void batch_close_kernel(DevState* states, int n, int eval_only) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     DevState& st = states[k];
     const float bf = from_ordered_bits((uint32_t)(st.best_key >> 32));
+    st.base_row = (int)(uint32_t)(st.best_key & 0xFFFFFFFFull);
     if (eval_only) {
       st.best_f = bf;
       st.best_gen = st.gen;

@@ -31,6 +31,8 @@ constexpr int kVecChoices[5] = {1, 2, 4, 8, 16};
 
 // Cr special cases of Eq. (9).
 enum CrMode : int { kCrGeneral = 0, kCrZero = 1, kCrOne = 2 };
+// Base index rules (de_base in de.h).
+enum BaseRule : int { kBaseDistinct = 0, kBaseRandom = 1, kBaseOffset = 2, kBasePermutation = 3, kBaseBest = 4 };
 
 struct DevState {
   unsigned long long best_key;   // (orderable FP32 bits << 32) | row
@@ -42,7 +44,8 @@ struct DevState {
   unsigned int done;             // CTAs finished in the running generation
   unsigned int error;            // sticky device error code (0 = none)
   float best_f;                  // best fitness at the end of the last generation
-  float pad_[3];
+  int base_row;                  // best row when the last generation closed (DE/best/1's base)
+  float pad_[2];
   double incumbent_f64;          // shifted-rotated: FP64 objective of the best row
   long long incumbent_gen;       // generation of that re-evaluation (-1 = none)
 };
@@ -58,6 +61,7 @@ struct GenParams {
   int N, D, pitch, D4;      // D4 = ceil(D / 4) float4 slots per row
   float F, lo, hi;
   int cr_mode;
+  int base;                 // base index rule (kBaseDistinct .. kBaseBest)
   unsigned long long cr_t;  // ceil(Cr * 2^32): rand < Cr  <=>  w < cr_t
   Key2 key;
   uint32_t inst;

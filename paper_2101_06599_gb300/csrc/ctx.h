@@ -89,6 +89,7 @@ int sync_stream(de_ctx* c);
 std::vector<uint32_t> nec_thresholds(double CR, int D);
 // Validation shared by de_create and de_batch_create (non-rotated objectives).
 bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de_bounds b);
+int batch_set_base(de_ctx* c, int base);
 // Batched contexts (batch_api.cu).
 cudaError_t batch_launch_generation(de_ctx* c, bool with_debug_of_inst, int inst);
 int batch_stats(de_ctx* c, de_stats_t* out);

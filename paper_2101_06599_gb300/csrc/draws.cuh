@@ -34,9 +34,92 @@ struct RowDraws {
   int r1, r2, r3, jrand, L;
 };
 
+// One Feistel round on h-bit halves (the permutation base rule).
+__device__ __forceinline__ uint32_t feistel_f(uint32_t r, uint32_t k, uint32_t mask) {
+  uint32_t t = (r ^ k) * 0x9E3779B1u;
+  t ^= t >> 15;
+  t *= 0x2C1B3C6Du;
+  t ^= t >> 13;
+  return t & mask;
+}
+
+// Alg. 5's permutation of generation g at row i: a 4-round Feistel network on
+// 2h bits (the least h >= 1 with 2^(2h) >= N) keyed by the generation's PERM
+// block, applied until the value falls in [0, N) (cycle walking; at most
+// 2^(2h) - N steps, fewer than 3N).
+__device__ __forceinline__ int base_permutation(const GenParams& p, uint32_t g, int i) {
+  const uint4 k = philox_block(p.key, kStreamPerm, p.inst, g, 0xFFFFFFFFu, 0u);
+  int h = 1;
+  while ((1ull << (2 * h)) < (unsigned long long)p.N) ++h;
+  const uint32_t mask = (1u << h) - 1u;
+  uint32_t x = (uint32_t)i;
+  do {
+    uint32_t L = x >> h, R = x & mask;
+    uint32_t nR = L ^ feistel_f(R, k.x, mask); L = R; R = nR;
+    nR = L ^ feistel_f(R, k.y, mask); L = R; R = nR;
+    nR = L ^ feistel_f(R, k.z, mask); L = R; R = nR;
+    nR = L ^ feistel_f(R, k.w, mask); L = R; R = nR;
+    x = (L << h) | R;
+  } while (x >= (uint32_t)p.N);
+  return (int)x;
+}
+
+// Rows of row i under the base rules other than the default (Section 2's
+// base index selections, Alg. 3-5, with Alg. 6's difference indices; and
+// DE/best/1): d.r1 is the base vector's row, d.r2 and d.r3 the difference
+// rows. Every rule takes j_rand from word 3 of the row's IDX block.
+static __device__ __noinline__ void draw_donors_rule(const GenParams& p, uint32_t g, int i, const uint4 b, RowDraws& d) {
+  if (p.base == kBaseBest) {
+    int best = p.st->base_row;
+    if (best < 0 || best >= p.N) best = 0;
+    // two draws by the skip rule with {i, best} excluded from the start
+    int e0 = min(i, best), e1 = max(i, best);
+    const int nex = (best != i) ? 2 : 1;
+    int v = randint_w(b.x, (uint32_t)(p.N - nex));
+    v += (v >= e0);
+    if (nex == 2) v += (v >= e1);
+    const int r2 = v;
+    int f0, f1, f2;                                // sorted {e0, (e1), r2}
+    if (nex == 2) {
+      if (r2 < e0) { f0 = r2; f1 = e0; f2 = e1; }
+      else if (r2 < e1) { f0 = e0; f1 = r2; f2 = e1; }
+      else { f0 = e0; f1 = e1; f2 = r2; }
+    } else {
+      f0 = min(e0, r2); f1 = max(e0, r2); f2 = 0x7FFFFFFF;
+    }
+    v = randint_w(b.y, (uint32_t)(p.N - nex - 1));
+    v += (v >= f0);
+    v += (v >= f1);
+    if (nex == 2) v += (v >= f2);
+    d.r1 = best;
+    d.r2 = r2;
+    d.r3 = v;
+  } else {
+    int r0;
+    if (p.base == kBaseRandom) {
+      r0 = randint_w(b.x, (uint32_t)p.N);
+    } else if (p.base == kBaseOffset) {
+      const uint32_t w = philox_block(p.key, kStreamIdx, p.inst, g, 0xFFFFFFFFu, 0u).x;
+      r0 = (int)(((long long)i + 1 + randint_w(w, (uint32_t)(p.N - 1))) % p.N);
+    } else {
+      r0 = base_permutation(p, g, i);
+    }
+    const int r1 = (int)(((long long)r0 + 1 + randint_w(b.y, (uint32_t)(p.N - 1))) % p.N);
+    const int r2 = (int)(((long long)r1 + 1 + randint_w(b.z, (uint32_t)(p.N - 1))) % p.N);
+    d.r1 = r0;
+    d.r2 = r1;
+    d.r3 = r2;
+  }
+  d.jrand = randint_w(b.w, (uint32_t)p.D);
+}
+
 // Donors and j_rand of row i in generation g.
 __device__ __forceinline__ void draw_donors(const GenParams& p, uint32_t g, int i, RowDraws& d) {
   const uint4 b = philox_block(p.key, kStreamIdx, p.inst, g, (uint32_t)i, 0u);
+  if (p.base != kBaseDistinct) {
+    draw_donors_rule(p, g, i, b, d);
+    return;
+  }
   int e0 = i;                                  // sorted excluded values e0 < e1 < e2
   int v = randint_w(b.x, (uint32_t)(p.N - 1));
   v += (v >= e0);

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
         p.st->best_gen = gen + 1;
       }
       p.st->gen = gen + 1;
+      p.st->base_row = (int)(uint32_t)(bk & 0xFFFFFFFFull);
       p.st->done = 0u;
     }
   }

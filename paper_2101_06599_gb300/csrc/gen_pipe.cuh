@@ -382,6 +382,7 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
         p.st->best_gen = gen + 1;
       }
       p.st->gen = gen + 1;
+      p.st->base_row = (int)(uint32_t)(bk & 0xFFFFFFFFull);
       p.st->done = 0u;
     }
   }

@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 2) gen_stream_kernel(const 
         p.st->best_gen = gen + 1;
       }
       p.st->gen = gen + 1;
+      p.st->base_row = (int)(uint32_t)(bk & 0xFFFFFFFFull);
       p.st->done = 0u;
     }
   }

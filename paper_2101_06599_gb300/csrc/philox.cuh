@@ -20,6 +20,7 @@ enum : uint32_t {
   kStreamLen = 2u,   // NEC segment length (word 0)
   kStreamBin = 3u,   // binomial crossover: word j for gene j
   kStreamExp = 4u,   // classic exponential crossover: word k for step k+1
+  kStreamPerm = 5u,  // permutation base rule: Feistel keys of a generation
 };
 
 struct Key2 { uint32_t k0, k1; };

@@ -719,6 +719,7 @@ __global__ void __launch_bounds__(kIncWarps * 32) sr_finish_kernel(const __grid_
         st->best_gen = gnext;
       }
       st->gen = gnext;
+      st->base_row = (int)(uint32_t)(st->best_key & 0xFFFFFFFFull);
       *sp.amb_count = 0u;
     }
     *sp.inc_count = 0u;

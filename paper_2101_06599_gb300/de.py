@@ -21,6 +21,7 @@ OBJECTIVE = {"sphere": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "griewan
              "elliptic": 5, "sr_rastrigin": 6, "sr_elliptic": 7}
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
 BOUND = {"probabilistic": 0, "worst_case": 1}
+BASE = {"distinct": 0, "random": 1, "offset": 2, "permutation": 3, "best": 4}
 
 
 class DEError(RuntimeError):
@@ -107,6 +108,8 @@ def load_library(build_if_missing: bool = True):
         "de_batch_size": ([vp, C.POINTER(i32)], C.c_int),
         "de_nec_step_noalloc": ([vp, vp, vp, vp, i32, i32, i32, f32, f64, C.c_int, de_bounds, C.c_uint64,
                                  i64, vp], C.c_int),
+        "de_set_base": ([vp, C.c_int], C.c_int),
+        "de_get_base": ([vp, C.POINTER(C.c_int)], C.c_int),
         "de_crossover_mask": ([vp, i64, i32, i32, f64, C.c_int, C.c_uint64, i64, C.c_uint32, vp], C.c_int),
         "de_crossover_apply": ([vp, vp, vp, i64, i32, i32, f64, C.c_int, C.c_uint64, i64, C.c_uint32, vp], C.c_int),
     }
@@ -281,6 +284,17 @@ def de_set_kernel(ctx, kind):
     _check(load_library().de_set_kernel(C.c_void_p(ctx), int(kind)), "de_set_kernel")
 
 
+def de_set_base(ctx, base):
+    b = BASE[base] if isinstance(base, str) else int(base)
+    _check(load_library().de_set_base(C.c_void_p(ctx), b), "de_set_base")
+
+
+def de_get_base(ctx):
+    b = C.c_int()
+    _check(load_library().de_get_base(C.c_void_p(ctx), C.byref(b)), "de_get_base")
+    return {v: k for k, v in BASE.items()}[b.value]
+
+
 def de_get_kernel(ctx):
     k = C.c_int32()
     _check(load_library().de_get_kernel(C.c_void_p(ctx), C.byref(k)), "de_get_kernel")
@@ -433,6 +447,9 @@ class Batch:
         de_batch_debug_step(self.ctx, inst, trial, ft, acc, dr)
         return trial, ft, acc.astype(bool), dr
 
+    def set_base(self, base):
+        de_set_base(self.ctx, base)
+
     def groups(self):
         return de_batch_get_groups(self.ctx)
 
@@ -516,6 +533,14 @@ class Optimizer:
 
     def launch(self):
         return de_get_launch(self.ctx)
+
+    def set_base(self, base):
+        """Base index rule: "distinct" (default), "random", "offset",
+        "permutation" or "best" (see de_set_base)."""
+        de_set_base(self.ctx, base)
+
+    def base(self):
+        return de_get_base(self.ctx)
 
     def set_kernel(self, kind):
         de_set_kernel(self.ctx, kind)
