@@ -366,19 +366,24 @@ def time_paper_table2(DE, torch, chunk=1000):
     """The paper's three DE runs (Ackley 1000-D / 500 individuals / 30000
     generations with its printed inner constant 0.02, Griewank 500-D / 300 /
     20000 on [-400, 400], Rosenbrock 50-D / 100 / 10000) with NEC (DE/rand/1/L)
-    and binomial crossover: total device time of all generations (graphs of
-    `chunk` generations), best value and best generation. The best values are
-    not a parity claim: the random streams differ from the paper's."""
+    and binomial crossover, under the distinct-donor rule and under the
+    paper's random base rule (Alg. 3 with Alg. 6): total device time of all
+    generations (graphs of `chunk` generations), best value and best
+    generation. The best values are not a parity claim: the random streams
+    differ from the paper's."""
     out = []
     for obj, D, Np, F, CR, G, box, b, paper in PAPER_TABLE2:
-        for xo in ("nec", "bin"):
+        for base in ("distinct", "random"):
+          for xo in ("nec", "bin"):
             params = {"ackley_b": b} if b else None
             opt = DE.Optimizer(Np, D, F=F, CR=CR, xo=xo, obj=obj, bounds=box, seed=SEED, params=params)
             try:
+                opt.set_base(base)
                 opt.run(chunk)                            # builds the graph; counted below from a fresh start
                 opt.synchronize()
                 opt.close()
                 opt = DE.Optimizer(Np, D, F=F, CR=CR, xo=xo, obj=obj, bounds=box, seed=SEED, params=params)
+                opt.set_base(base)
                 torch.cuda.synchronize()
                 ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 ev0.record(opt.stream)
@@ -394,7 +399,7 @@ def time_paper_table2(DE, torch, chunk=1000):
             finally:
                 opt.close()
             out.append({"objective": obj, "D": D, "Np": Np, "F": F, "CR": CR, "generations": G,
-                        "crossover": xo, "seconds": sec, "us_per_gen": 1e6 * sec / G,
+                        "crossover": xo, "base": base, "seconds": sec, "us_per_gen": 1e6 * sec / G,
                         "value": Np * D * G / sec, "best_value": st["best_f"], "best_gen": st["best_gen"],
                         "paper_cuda_gtx760": {"best_value": paper[xo][0], "best_gen": paper[xo][1],
                                               "seconds": paper[xo][2]}})
