@@ -87,7 +87,7 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
 }
 
 template <int XO, int OBJ>
-__global__ void __launch_bounds__(kStreamWarps * 32, 3) gen_stream_kernel(const __grid_constant__ GenParams p) {
+__global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const __grid_constant__ GenParams p) {
   __shared__ unsigned long long s_key[kStreamWarps];
   __shared__ int s_cnt[kStreamWarps];
   __shared__ int s_acc[kStreamWarps];
