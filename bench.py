@@ -37,7 +37,7 @@ METRIC = "individual·dims/s per DE generation (NEC vs bin vs seq-exp), % of HBM
 UNIT = "ind·dims/s"
 WORKLOAD = "rosenbrock_ackley_N16384_D10000"
 N_DEF, D_DEF, F_DEF, CR_DEF, SEED = 16384, 10000, 0.5, 0.9, 1
-BOXES = {"rosenbrock": (-5.12, 5.12), "ackley": (-30.0, 30.0)}
+BOXES = {"rosenbrock": (-5.12, 5.12), "ackley": (-30.0, 30.0), "rastrigin": (-5.12, 5.12)}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE = os.path.join(ROOT, "profiles", "gen_pipe_nec_rosenbrock_N16384_D10000.md")
 KERNEL_SOURCES = ["common.cuh", "draws.cuh", "objectives.cuh", "gen_kernel.cuh", "gen_pipe.cuh", "ptx.cuh",
@@ -509,7 +509,8 @@ def main():
     ap.add_argument("--D", type=int, default=D_DEF, help="genes per row")
     ap.add_argument("--xo", default="nec", choices=["nec", "bin", "exp"],
                     help="headline crossover (other values are for profiling one kernel)")
-    ap.add_argument("--obj", default="rosenbrock", choices=["rosenbrock", "ackley"], help="headline objective")
+    ap.add_argument("--obj", default="rosenbrock", choices=["rosenbrock", "ackley", "rastrigin"],
+                    help="headline objective")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
