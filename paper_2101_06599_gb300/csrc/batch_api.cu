@@ -51,18 +51,6 @@ static int upload_insts(de_ctx* c) {
   return sync_stream(c);
 }
 
-static int upload_tiles(de_ctx* c, const std::vector<BatchTile>& t, BatchTile** dst) {
-  if (*dst) ctx_free(c, *dst);
-  *dst = nullptr;
-  if (t.empty()) return DE_OK;
-  *dst = (BatchTile*)ctx_alloc(c, t.size() * sizeof(BatchTile));
-  if (!*dst) return DE_ENOMEM;
-  if (cudaMemcpyAsync(*dst, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
-      cudaSuccess)
-    return DE_ECUDA;
-  return DE_OK;
-}
-
 static int build_tiles(de_ctx* c) {
   std::vector<int> order((size_t)c->n_inst);
   std::iota(order.begin(), order.end(), 0);
@@ -75,71 +63,41 @@ static int build_tiles(de_ctx* c) {
            (double)(kBatchThreadsHost / c->bgroup[b]) * c->bp[b].D;
   });
   // rows of G <= 32 lanes go to warp tiles of 32 / G rows, wider rows to CTA
-  // tiles of 256 / G rows (every instance: these lists also evaluate); the
-  // generation lists leave out the instances of the streaming kernel, whose
-  // rows form their own list (instance-major)
-  std::vector<BatchTile> wt, ct, gwt, gct;
-  std::vector<BatchRow> srows;
-  std::vector<long long> work;                     // float4 slots before each streamed row
+  // tiles of 256 / G rows
+  std::vector<BatchTile> wt, ct;
   c->bt0.assign((size_t)c->n_inst, 0);
   c->bt1.assign((size_t)c->n_inst, 0);
-  long long total = 0;
   for (int k : order) {
     const bool warp = c->bgroup[k] <= 32;
-    const bool streamed = c->bp[k].D4 >= kBsMinD4 && c->sm_count > 0;
     std::vector<BatchTile>& tiles = warp ? wt : ct;
     const int R = (warp ? 32 : kBatchThreadsHost) / c->bgroup[k];
     const int nt = (c->bp[k].N + R - 1) / R;
     c->bt0[k] = (int)tiles.size();
-    for (int t = 0; t < nt; ++t) {
-      tiles.push_back(BatchTile{k, t * R});
-      if (!streamed) (warp ? gwt : gct).push_back(BatchTile{k, t * R});
-    }
+    for (int t = 0; t < nt; ++t) tiles.push_back(BatchTile{k, t * R});
     c->bt1[k] = (int)tiles.size();
-    if (streamed)
-      for (int i = 0; i < c->bp[k].N; ++i) {
-        work.push_back(total);
-        srows.push_back(BatchRow{k, i});
-        total += c->bp[k].D4;
-      }
   }
+  if (c->d_tiles) ctx_free(c, c->d_tiles);
+  if (c->d_ctiles) ctx_free(c, c->d_ctiles);
+  c->d_tiles = nullptr;
+  c->d_ctiles = nullptr;
   c->ntiles = (int)wt.size();
   c->nctiles = (int)ct.size();
-  c->ngtiles = (int)gwt.size();
-  c->ngctiles = (int)gct.size();
-  int rc = upload_tiles(c, wt, &c->d_tiles);
-  if (rc == DE_OK) rc = upload_tiles(c, ct, &c->d_ctiles);
-  if (rc == DE_OK) rc = upload_tiles(c, gwt, &c->d_gtiles);
-  if (rc == DE_OK) rc = upload_tiles(c, gct, &c->d_gctiles);
-  if (rc != DE_OK) return rc;
-  if (c->d_brows) ctx_free(c, c->d_brows);
-  if (c->d_bseg) ctx_free(c, c->d_bseg);
-  c->d_brows = nullptr;
-  c->d_bseg = nullptr;
-  c->bstream = BatchStreamLaunch{};
-  if (!srows.empty()) {
-    // warp w takes the rows whose first slot lies in [w total / W, (w + 1) total / W)
-    const int grid = 4 * c->sm_count;
-    const int W = grid * 8;
-    std::vector<int> seg((size_t)W + 1);
-    size_t k = 0;
-    for (int w = 0; w <= W; ++w) {
-      const long long target = (long long)((double)total * w / W);
-      while (k < srows.size() && work[k] < target) ++k;
-      seg[(size_t)w] = (w == W) ? (int)srows.size() : (int)k;
-    }
-    c->d_brows = (BatchRow*)ctx_alloc(c, srows.size() * sizeof(BatchRow));
-    c->d_bseg = (int*)ctx_alloc(c, seg.size() * sizeof(int));
-    if (!c->d_brows || !c->d_bseg) return DE_ENOMEM;
-    if (cudaMemcpyAsync(c->d_brows, srows.data(), srows.size() * sizeof(BatchRow), cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_bseg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream) !=
-            cudaSuccess)
+  if (!wt.empty()) {
+    c->d_tiles = (BatchTile*)ctx_alloc(c, wt.size() * sizeof(BatchTile));
+    if (!c->d_tiles) return DE_ENOMEM;
+    if (cudaMemcpyAsync(c->d_tiles, wt.data(), wt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
       return DE_ECUDA;
-    c->bstream = BatchStreamLaunch{c->d_brows, c->d_bseg, (int)srows.size(), grid};
+  }
+  if (!ct.empty()) {
+    c->d_ctiles = (BatchTile*)ctx_alloc(c, ct.size() * sizeof(BatchTile));
+    if (!c->d_ctiles) return DE_ENOMEM;
+    if (cudaMemcpyAsync(c->d_ctiles, ct.data(), ct.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return DE_ECUDA;
   }
   drop_graphs(c);
-  return upload_insts(c);                          // synchronises: the host lists above are consumed
+  return upload_insts(c);
 }
 
 // Evaluate the parents of every instance (inst < 0) or of one instance.
@@ -161,9 +119,8 @@ static int batch_evaluate(de_ctx* c, int inst) {
 }
 
 cudaError_t batch_launch_generation(de_ctx* c, bool, int) {
-  return launch_batch_generation(c->d_insts, c->d_gtiles, c->ngtiles, c->d_gctiles, c->ngctiles, c->d_ptiles,
-                                 c->nptiles, c->d_plans, c->d_states, c->n_inst, c->batch_grid, c->bstream,
-                                 c->stream);
+  return launch_batch_generation(c->d_insts, c->d_tiles, c->ntiles, c->d_ctiles, c->nctiles, c->d_ptiles,
+                                 c->nptiles, c->d_plans, c->d_states, c->n_inst, c->batch_grid, c->stream);
 }
 
 // Plan tiles: 256 consecutive rows of one instance, instances in order.

@@ -7,9 +7,7 @@
 //     memory, exp by the sequential walk), and gathers the slot bytes of the
 //     row and its donors and the parent fitness into a 32-byte plan. Rows are
 //     independent, so the serial draw work of one row never delays another.
-//  2. batch_stream_kernel (batch_stream.cu: instances with rows of at least
-//     256 genes, one warp per row, streamed in chunks), then
-//     batch_warp_kernel (the other instances with G <= 32 lanes per row: warp tiles
+//  2. batch_warp_kernel (instances with G <= 32 lanes per row: warp tiles
 //     of 32 / G rows, each warp walking its own tiles) and batch_gen_kernel
 //     (G > 32: CTA tiles of R = 256 / G rows); G is a power of two, 4..256,
 //     per instance, and the grid walks each tile list with a grid stride. The list is
@@ -591,14 +589,9 @@ __global__ void batch_reset_best_kernel(DevState* states, int n) {
 
 cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
                                     const BatchTile* ctiles, int nctiles, const BatchTile* ptiles, int nptiles,
-                                    RowPlan32* plans, DevState* states, int n_inst, int grid,
-                                    const BatchStreamLaunch& bs, cudaStream_t s) {
-  if (nwtiles + nctiles + bs.nrows <= 0) return cudaSuccess;
+                                    RowPlan32* plans, DevState* states, int n_inst, int grid, cudaStream_t s) {
+  if (nwtiles + nctiles <= 0) return cudaSuccess;
   batch_plan_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
-  if (bs.nrows > 0) {
-    const cudaError_t e = launch_batch_stream(insts, bs, plans, s);
-    if (e != cudaSuccess) return e;
-  }
   if (nwtiles > 0) batch_warp_kernel<<<grid, kBatchThreads, 0, s>>>(insts, wtiles, nwtiles, plans, 0);
   if (nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ctiles, nctiles, plans, 0);
   batch_close_kernel<<<(n_inst + 255) / 256, 256, 0, s>>>(states, n_inst, 0);

@@ -67,14 +67,6 @@ struct de_ctx {
   std::vector<long long> brow_base;
   de::DevState* d_states = nullptr;
   int ntiles = 0, nctiles = 0, batch_grid = 0, max_pitch = 0;
-  // generation lists: the tiles of the instances the streaming kernel does
-  // not run, and that kernel's rows (evaluation uses d_tiles / d_ctiles)
-  de::BatchTile* d_gtiles = nullptr;
-  de::BatchTile* d_gctiles = nullptr;
-  de::BatchRow* d_brows = nullptr;
-  int* d_bseg = nullptr;
-  int ngtiles = 0, ngctiles = 0;
-  de::BatchStreamLaunch bstream{};
   // shifted-rotated objectives (sr_api.cu)
   bool rotated = false;
   de::SrParams sp{};

@@ -55,28 +55,13 @@ struct RowPlan32 {
   float fit_i;
   int pad;
 };
-// One row of a batched instance in the streaming kernel's row list.
-struct BatchRow {
-  int inst, i;
-};
-// The streaming kernel's part of a batched generation (batch_stream.cu):
-// grid warps, warp w taking rows [seg[w], seg[w + 1]).
-struct BatchStreamLaunch {
-  const BatchRow* rows;
-  const int* seg;
-  int nrows, grid;
-};
-constexpr int kBsMinD4 = 64;       // rows of at least 256 genes go to the streaming kernel
-cudaError_t launch_batch_stream(const BatchInst* insts, const BatchStreamLaunch& b, const RowPlan32* plans,
-                                cudaStream_t s);
 constexpr int kBatchThreadsHost = 256;
 constexpr int kBatchMaxGroup = 256;
 constexpr int kBatchMaxD4PerLane = 16;
 // plan kernel + row kernel + close kernel (one generation of every instance)
 cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
                                     const BatchTile* ctiles, int nctiles, const BatchTile* ptiles, int nptiles,
-                                    RowPlan32* plans, DevState* states, int n_inst, int grid,
-                                    const BatchStreamLaunch& bs, cudaStream_t s);
+                                    RowPlan32* plans, DevState* states, int n_inst, int grid, cudaStream_t s);
 // reset best keys, evaluate the parents of the tiles' rows, close (instances
 // first_inst .. first_inst + n_inst - 1)
 cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
