@@ -86,6 +86,86 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
   }
 }
 
+// Pass 1 of one row: the trial chunk by chunk, its objective (even and odd
+// slots of a chunk into two independent partial sums: shorter dependency
+// chains) reduced over the warp; every lane returns the value (NaN as +inf).
+// cnt gets the binomial mask's popcount. Writes the trial to p.dbg_trial when set.
+template <int XO, int OBJ>
+__device__ __forceinline__ float stream_row_value(const GenParams& p, const StreamRow& r, int lane, int& cnt) {
+  Acc s{0.0f, 0.0f, 0.0f}, s2{0.0f, 0.0f, 0.0f};
+  cnt = 0;
+  float carry = 0.0f;                              // Rosenbrock: last gene of the previous chunk
+  for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
+    float4 v[kStreamU];
+    unsigned m[kStreamU];
+    stream_trial_chunk<XO>(p, r, q0, lane, v, m);
+    if (p.dbg_trial) {
+      float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)r.i * p.pitch);
+#pragma unroll
+      for (int u = 0; u < kStreamU; ++u) {
+        const int q = q0 + lane + 32 * u;
+        if (q < p.D4) o[q] = v[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamU; ++u) {
+      if constexpr (XO == kBin) cnt += __popc(m[u]);
+      const int q = q0 + lane + 32 * u;
+      const int j0 = 4 * q;
+      Acc& su = (u & 1) ? s2 : s;
+      if constexpr (OBJ == kRosenbrock) {
+        float nb = __shfl_down_sync(0xFFFFFFFFu, v[u].x, 1);
+        const float first_next = (u + 1 < kStreamU) ? __shfl_sync(0xFFFFFFFFu, v[(u + 1) % kStreamU].x, 0) : 0.0f;
+        if (lane == 31) nb = first_next;
+        if (u == 0 && lane == 0 && q0 > 0) accum_pair(su, carry, v[0].x);   // the pair across chunks
+        if (q < p.D4) {
+          if (j0 + 1 < p.D) accum_pair(su, v[u].x, v[u].y);
+          if (j0 + 2 < p.D) accum_pair(su, v[u].y, v[u].z);
+          if (j0 + 3 < p.D) accum_pair(su, v[u].z, v[u].w);
+          if (j0 + 4 < p.D && !(lane == 31 && u + 1 == kStreamU)) accum_pair(su, v[u].w, nb);
+        }
+      } else {
+        if (q < p.D4) {
+          accum_gene<OBJ>(su, v[u].x, j0, p);
+          if (j0 + 1 < p.D) accum_gene<OBJ>(su, v[u].y, j0 + 1, p);
+          if (j0 + 2 < p.D) accum_gene<OBJ>(su, v[u].z, j0 + 2, p);
+          if (j0 + 3 < p.D) accum_gene<OBJ>(su, v[u].w, j0 + 3, p);
+        }
+      }
+    }
+    if constexpr (OBJ == kRosenbrock) carry = __shfl_sync(0xFFFFFFFFu, v[kStreamU - 1].w, 31);
+  }
+  s.a += s2.a;
+  s.b += s2.b;
+  s.c += s2.c;
+  constexpr int NS = ObjTraits<OBJ>::kSums;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.a += __shfl_xor_sync(0xFFFFFFFFu, s.a, o);
+    if (NS > 1) s.b += __shfl_xor_sync(0xFFFFFFFFu, s.b, o);
+    if (NS > 2) s.c += __shfl_xor_sync(0xFFFFFFFFu, s.c, o);
+    if (XO == kBin) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+  }
+  float f = finalize_fitness<OBJ>(s, p);
+  if (f != f) f = __int_as_float(0x7F800000);     // NaN counts as +inf
+  return f;
+}
+
+// Pass 2 of a winning row: its trial again, chunk by chunk, stored to `out`.
+template <int XO>
+__device__ __forceinline__ void stream_row_store(const GenParams& p, const StreamRow& r, int lane, float4* out) {
+  for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
+    float4 v[kStreamU];
+    unsigned m[kStreamU];
+    stream_trial_chunk<XO>(p, r, q0, lane, v, m);
+#pragma unroll
+    for (int u = 0; u < kStreamU; ++u) {
+      const int q = q0 + lane + 32 * u;
+      if (q < p.D4) st_stream(out + q, v[u]);
+    }
+  }
+}
+
 template <int XO, int OBJ>
 __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const __grid_constant__ GenParams p) {
   __shared__ unsigned long long s_key[kStreamWarps];
@@ -122,64 +202,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
     r.d2 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd2, 0));
     r.d3 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd3, 0));
 
-    // pass 1: the trial's objective (even and odd slots of a chunk into two
-    // independent partial sums: shorter dependency chains)
-    Acc s{0.0f, 0.0f, 0.0f}, s2{0.0f, 0.0f, 0.0f};
     int cnt = 0;
-    float carry = 0.0f;                              // Rosenbrock: last gene of the previous chunk
-    for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
-      float4 v[kStreamU];
-      unsigned m[kStreamU];
-      stream_trial_chunk<XO>(p, r, q0, lane, v, m);
-      if (p.dbg_trial) {
-        float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch);
-#pragma unroll
-        for (int u = 0; u < kStreamU; ++u) {
-          const int q = q0 + lane + 32 * u;
-          if (q < p.D4) o[q] = v[u];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kStreamU; ++u) {
-        if constexpr (XO == kBin) cnt += __popc(m[u]);
-        const int q = q0 + lane + 32 * u;
-        const int j0 = 4 * q;
-        Acc& su = (u & 1) ? s2 : s;
-        if constexpr (OBJ == kRosenbrock) {
-          float nb = __shfl_down_sync(0xFFFFFFFFu, v[u].x, 1);
-          const float first_next = (u + 1 < kStreamU) ? __shfl_sync(0xFFFFFFFFu, v[(u + 1) % kStreamU].x, 0) : 0.0f;
-          if (lane == 31) nb = first_next;
-          if (u == 0 && lane == 0 && q0 > 0) accum_pair(su, carry, v[0].x);   // the pair across chunks
-          if (q < p.D4) {
-            if (j0 + 1 < p.D) accum_pair(su, v[u].x, v[u].y);
-            if (j0 + 2 < p.D) accum_pair(su, v[u].y, v[u].z);
-            if (j0 + 3 < p.D) accum_pair(su, v[u].z, v[u].w);
-            if (j0 + 4 < p.D && !(lane == 31 && u + 1 == kStreamU)) accum_pair(su, v[u].w, nb);
-          }
-        } else {
-          if (q < p.D4) {
-            accum_gene<OBJ>(su, v[u].x, j0, p);
-            if (j0 + 1 < p.D) accum_gene<OBJ>(su, v[u].y, j0 + 1, p);
-            if (j0 + 2 < p.D) accum_gene<OBJ>(su, v[u].z, j0 + 2, p);
-            if (j0 + 3 < p.D) accum_gene<OBJ>(su, v[u].w, j0 + 3, p);
-          }
-        }
-      }
-      if constexpr (OBJ == kRosenbrock) carry = __shfl_sync(0xFFFFFFFFu, v[kStreamU - 1].w, 31);
-    }
-    s.a += s2.a;
-    s.b += s2.b;
-    s.c += s2.c;
-    constexpr int NS = ObjTraits<OBJ>::kSums;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s.a += __shfl_xor_sync(0xFFFFFFFFu, s.a, o);
-      if (NS > 1) s.b += __shfl_xor_sync(0xFFFFFFFFu, s.b, o);
-      if (NS > 2) s.c += __shfl_xor_sync(0xFFFFFFFFu, s.c, o);
-      if (XO == kBin) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-    }
-    float f = finalize_fitness<OBJ>(s, p);
-    if (f != f) f = __int_as_float(0x7F800000);     // NaN counts as +inf
+    const float f = stream_row_value<XO, OBJ>(p, r, lane, cnt);
     acc = (f < p.fit[i]) ? 1 : 0;
     __syncwarp();                                    // every lane has read fit[i] before lane 0 writes it
     Lrow = (XO == kBin) ? cnt : r.L;
@@ -197,16 +221,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
       key = best_key_of(f, i);
       // pass 2: the winning trial again, into the other slot buffer
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
-      for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
-        float4 v[kStreamU];
-        unsigned m[kStreamU];
-        stream_trial_chunk<XO>(p, r, q0, lane, v, m);
-#pragma unroll
-        for (int u = 0; u < kStreamU; ++u) {
-          const int q = q0 + lane + 32 * u;
-          if (q < p.D4) st_stream(out + q, v[u]);
-        }
-      }
+      stream_row_store<XO>(p, r, lane, out);
     }
   }
   if (lane == 0) {
