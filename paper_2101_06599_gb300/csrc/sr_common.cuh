@@ -11,8 +11,7 @@
 
 namespace de {
 
-constexpr int kSrTile = 64;          // FP32 GEMM: 64 x 64 output tile
-constexpr int kSrKStep = 32;         // FP32 GEMM: K per shared-memory stage
+constexpr int kSrTile = 64;          // columns per partial sum of g (both FP32 products)
 
 struct SrParams {
   GenParams g;
