@@ -414,20 +414,26 @@ def barrier():
         _dist.barrier()
 
 
-def max_over_ranks(torch, v):
+def _reduce(torch, v, op):
     if _dist is None:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    _dist.all_reduce(t, op=_dist.ReduceOp.MAX)
+    dev = "cuda" if _dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    _dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(torch, v):
+    return _reduce(torch, v, _dist.ReduceOp.MAX) if _dist is not None else v
 
 
 def sum_over_ranks(torch, v):
-    if _dist is None:
-        return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    _dist.all_reduce(t, op=_dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(torch, v, _dist.ReduceOp.SUM) if _dist is not None else v
+
+
+def replica_seed(rank):
+    """Rank r runs an independent replica from seed SEED + r."""
+    return SEED + rank
 
 
 def oracle_generation_rate(N, D, obj, xo, budget_s, rows_per_step=None, steps=None, warmup=0):
@@ -530,7 +536,7 @@ def main():
         _dist = dist
     DE.load_library()
     N, D, K, W = args.N, args.D, args.steps, args.warmup
-    seed = SEED + rank
+    seed = replica_seed(rank)
 
     if args.only:
         if args.only == "rotated":
