@@ -202,6 +202,10 @@ def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
     rows = float(sum(s["N"] for s in specs))
     b = DE.Batch(specs, seed=seed + 4)
     try:
+        t_tune = time.time()
+        groups = b.autotune(reps=3)
+        t_tune = time.time() - t_tune
+        kinds = sorted({"staged" if g < 0 else ("register" if g <= 32 else "cta") for g in groups})
         b.run(warmup)
         b.synchronize()
         st0 = b.stats()
@@ -227,7 +231,10 @@ def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
     return {"workload": "batched_512_instances" if len(specs) == 512 else "batched_first_%d_instances" % len(specs),
             "instances": len(specs), "ind_dims_per_step": units,
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_gen": ms / steps,
-            "hbm_gbs": gbs, "frac": gbs / peak, "launches_per_step": 3,
+            "hbm_gbs": gbs, "frac": gbs / peak, "launches_per_step": 2 + len(kinds),
+            "row_kernels": {kd: sum(1 for g in groups if ("staged" if g < 0 else ("register" if g <= 32 else "cta")) == kd)
+                            for kd in kinds},
+            "autotune_s": round(t_tune, 3),
             "a_acceptance": d_acc / (rows * steps), "m_masked_fraction": d_msk / (units * steps)}
 
 

@@ -219,10 +219,11 @@ typedef struct {
  * 2^24); instance k draws from Philox instance field k, so instance k of a
  * batch reproduces a single population whose draws use instance field k.
  * Each instance keeps its own population, fitness, counters and best. One
- * de_step / de_run step advances every instance by one generation in one
- * kernel launch: the instances are cut into tiles of 256 / G rows with G
- * threads per row (G set per instance, see de_batch_set_groups) and the
- * tiles are walked in longest-first order. Per-instance limits as de_create
+ * de_step / de_run step advances every instance by one generation in a few
+ * launches over all instances (draws, rows, close): the rows of each
+ * instance are cut into spans of up to 32 rows (taken by warps from a queue)
+ * or, for D > 2048, into tiles of 256 / G rows; the row kernel of each
+ * instance is set by de_batch_set_groups. Per-instance limits as de_create
  * with D <= 16384 and non-rotated objectives (Ackley constant 0.2). The
  * initial populations are drawn and evaluated before the call returns.
  * Single-population calls (de_best, de_get_population, de_set_population,
@@ -252,11 +253,39 @@ int de_batch_set_population(de_ctx *ctx, int32_t inst, const float *pop, const f
 int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftrial_out,
                         uint8_t *accept_out, int32_t *draws_out);
 
-/* Tile shape per instance: threads per row G (a power of two, 4..256, with
- * ceil(ceil(D/4) / G) <= 16; 0 = the default, the smallest such G). Tuning
- * only: draws are unchanged, FP32 fitness rounding may change. */
+/* Row kernel per instance (one value per instance):
+ *   -G         the staged warp pipeline (exp and NEC only, D <= 2048) with G
+ *              lanes per row (G = 4, 8, 16 or 32): each warp loads the next
+ *              pass of up to 32 rows / 8 KB into registers while it
+ *              processes the previous one from shared memory;
+ *   1          the staged pipeline with its default G (a lane per float4
+ *              slot, at most 32);
+ *   G = 4..256 (a power of two with ceil(ceil(D/4) / G) <= 16) register
+ *              tiles of G threads per row (one warp of 32 / G rows for
+ *              G <= 32, a CTA of 256 / G rows above);
+ *   0          the default: 1 where allowed, else the smallest such G.
+ * de_batch_get_groups reports staged instances as -G. Draws are unchanged by
+ * the choice, and so are fitness values, selections and trajectories for
+ * every choice with at most 32 threads per row (staged, and G = 4..32):
+ * those kernels sum the FP32 fitness in one fixed order. G > 32 (needed only
+ * for D > 2048) sums in another order. Returns DE_EINVAL for an invalid
+ * value; the context is unchanged then. */
 int de_batch_set_groups(de_ctx *ctx, const int32_t *groups);
 int de_batch_get_groups(de_ctx *ctx, int32_t *groups);
+
+/* Autotuner: pick each instance's row kernel (the values above) by timing.
+ * Instances are grouped by objective, crossover and the octave of ceil(D/4)
+ * (rows of D <= 2048; wider rows keep their tiles). For each group in turn
+ * every candidate (register tiles of 4..32 lanes per row; for exp and NEC
+ * the staged pipeline with 4..32 lanes) runs the row kernels of one
+ * generation `reps` times (1..1000) on the current populations, the other
+ * groups as they stand, and the fastest is kept. The trials reuse the draws
+ * of the current generation and leave populations, fitness, counters and the
+ * generation as they were, and the choice changes no result (every
+ * candidate sums the fitness in one order). Synchronises; drops captured
+ * graphs. groups_out (n_inst values, may be NULL) receives the choice as
+ * de_batch_get_groups reports it. DE_ESTATE on a single population. */
+int de_batch_autotune(de_ctx *ctx, int32_t reps, int32_t *groups_out);
 /* Number of instances (0 for a single-population context). */
 int de_batch_size(de_ctx *ctx, int32_t *n_inst);
 

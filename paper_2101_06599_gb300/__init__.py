@@ -7,7 +7,7 @@ package holds the build step, the ctypes binding (de.py) and the seeded
 synthetic workloads (workloads.py).
 """
 from .de import (Batch, DEError, Optimizer, de_batch_best, de_batch_create, de_batch_debug_step,
-                 de_batch_get_groups, de_batch_get_population, de_batch_set_groups,
+                 de_batch_autotune, de_batch_get_groups, de_batch_get_population, de_batch_set_groups,
                  de_batch_set_population, de_batch_size, de_batch_stats, de_best, de_create,
                  de_debug_step, de_destroy, de_get_kernel, de_get_pipeline, de_get_launch, de_get_population, de_load,
                  de_run, de_save, de_set_kernel, de_set_launch, de_set_pipeline, de_set_population,
@@ -15,7 +15,7 @@ from .de import (Batch, DEError, Optimizer, de_batch_best, de_batch_create, de_b
                  de_nec_step_noalloc, use_torch_allocator)
 
 __all__ = ["Batch", "DEError", "Optimizer", "de_batch_best", "de_batch_create", "de_batch_debug_step",
-           "de_batch_get_groups", "de_batch_get_population", "de_batch_set_groups",
+           "de_batch_autotune", "de_batch_get_groups", "de_batch_get_population", "de_batch_set_groups",
            "de_batch_set_population", "de_batch_size", "de_batch_stats", "de_best", "de_create",
            "de_debug_step", "de_destroy", "de_get_kernel", "de_get_pipeline", "de_get_launch", "de_get_population",
            "de_load", "de_run", "de_save", "de_set_kernel", "de_set_launch", "de_set_pipeline",

@@ -4,16 +4,17 @@
 // Device memory: one arena per context holding, per instance, two slot
 // buffers (N x pitch floats), fitness, slot bytes and NEC thresholds, plus
 // one DevState per instance (contiguous, so the totals are one copy).
-// Tiles: instance k is cut into ceil(N_k / R_k) tiles, R_k = 32 / G_k rows
-// (warp tiles, G_k <= 32) or 256 / G_k rows (CTA tiles); each tile list is
-// grouped by (objective, crossover) and ordered by tile cost (R_k D_k,
-// descending) within a group, a longest-processing-time schedule for the
-// grid-stride walk. A second list
+// Row work: instance k with G_k <= 32 lanes per row is cut into spans of up
+// to 32 rows (one list per crossover, taken by warps from a queue); wider
+// rows are cut into CTA tiles of 256 / G_k rows. Lists are grouped by the
+// row code's specialisation and ordered longest first within a group. A
+// second list
 // of 256-row tiles drives the plan kernel; plans (32 bytes per row of every
 // instance) live in one buffer indexed by the instance's first row.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -23,9 +24,31 @@ using namespace de_host;
 
 namespace de_host {
 
-static int default_group(int D4) {
+// Lanes per row of the register kernels: the fewest that hold the row in at
+// most kBatchMaxD4PerLane float4 slots per lane.
+static int min_group(int D4) {
   int G = 4;
   while (G < kBatchMaxGroup && (D4 + G - 1) / G > kBatchMaxD4PerLane) G *= 2;
+  return G;
+}
+
+// Default row kernel: the staged kernel for the segment crossovers (exp, NEC)
+// up to D = 2048, the register kernels otherwise.
+static int default_group(int D4, int xo) {
+  if (xo != kBin && D4 <= kStageMaxD4) return kBatchStaged;
+  return min_group(D4);
+}
+
+static bool valid_group(int G, int D4, int xo) {
+  if (G == kBatchStaged) return xo != kBin && D4 <= kStageMaxD4;
+  if (G < 4 || G > kBatchMaxGroup || (G & (G - 1)) != 0) return false;
+  return (D4 + G - 1) / G <= kBatchMaxD4PerLane;
+}
+
+// Lanes per row in the staged kernel: enough for one slot per lane, at most 32.
+static int default_lanes(int D4) {
+  int G = 4;
+  while (G < 32 && G < D4) G *= 2;
   return G;
 }
 
@@ -37,7 +60,7 @@ static BatchInst make_inst(const de_ctx* c, int k) {
   bi.obj = c->bobj[k];
   bi.xo = c->bxo[k];
   bi.group = c->bgroup[k];
-  bi.tiles = c->bt1[k] - c->bt0[k];
+  bi.lanes = c->blanes[k];
   bi.row_base = c->brow_base[k];
   return bi;
 }
@@ -51,76 +74,105 @@ static int upload_insts(de_ctx* c) {
   return sync_stream(c);
 }
 
+static size_t span_cost(const de_ctx* c, int k) {
+  return (size_t)std::min(c->bp[k].N, kSpanRows) * (size_t)c->bp[k].D4;
+}
+
+static int upload(de_ctx* c, void** dst, const void* src, size_t bytes) {
+  if (*dst) ctx_free(c, *dst);
+  *dst = nullptr;
+  if (bytes == 0) return DE_OK;
+  *dst = ctx_alloc(c, bytes);
+  if (!*dst) return DE_ENOMEM;
+  return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, c->stream) == cudaSuccess ? DE_OK : DE_ECUDA;
+}
+
 static int build_tiles(de_ctx* c) {
   std::vector<int> order((size_t)c->n_inst);
   std::iota(order.begin(), order.end(), 0);
-  // grouped by (objective, crossover) so that one specialisation of the row
-  // code runs at a time; longest tiles first within a group
+  // instances whose rows take at most a warp go to span lists (one per
+  // crossover), grouped by (objective, G) so that one specialisation of the
+  // row code runs at a time, longest spans first within a group; wider rows
+  // go to CTA tiles of 256 / G rows, grouped by (objective, crossover)
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    const int ca = c->bobj[a] * 3 + c->bxo[a], cb = c->bobj[b] * 3 + c->bxo[b];
+    const int ca = (c->bobj[a] * 3 + c->bxo[a]) * 512 + c->bgroup[a];
+    const int cb = (c->bobj[b] * 3 + c->bxo[b]) * 512 + c->bgroup[b];
     if (ca != cb) return ca < cb;
-    return (double)(kBatchThreadsHost / c->bgroup[a]) * c->bp[a].D >
-           (double)(kBatchThreadsHost / c->bgroup[b]) * c->bp[b].D;
+    return span_cost(c, a) > span_cost(c, b);
   });
-  // rows of G <= 32 lanes go to warp tiles of 32 / G rows, wider rows to CTA
-  // tiles of 256 / G rows
-  std::vector<BatchTile> wt, ct;
+  std::vector<BatchSpan> sp[4];
+  std::vector<BatchTile> ct;
   c->bt0.assign((size_t)c->n_inst, 0);
   c->bt1.assign((size_t)c->n_inst, 0);
   for (int k : order) {
-    const bool warp = c->bgroup[k] <= 32;
-    std::vector<BatchTile>& tiles = warp ? wt : ct;
-    const int R = (warp ? 32 : kBatchThreadsHost) / c->bgroup[k];
-    const int nt = (c->bp[k].N + R - 1) / R;
-    c->bt0[k] = (int)tiles.size();
-    for (int t = 0; t < nt; ++t) tiles.push_back(BatchTile{k, t * R});
-    c->bt1[k] = (int)tiles.size();
+    const int N = c->bp[k].N;
+    if (c->bgroup[k] <= 32) {
+      std::vector<BatchSpan>& v = sp[c->bgroup[k] == kBatchStaged ? 3 : c->bxo[k]];
+      c->bt0[k] = (int)v.size();
+      for (int r = 0; r < N; r += kSpanRows) {
+        BatchSpan s;
+        std::memset(&s, 0, sizeof(s));
+        s.plan0 = c->brow_base[k] + r;
+        s.inst = k;
+        s.row0 = r;
+        s.rows = std::min(kSpanRows, N - r);
+        v.push_back(s);
+      }
+      c->bt1[k] = (int)v.size();
+    } else {
+      const int R = kBatchThreadsHost / c->bgroup[k];
+      c->bt0[k] = (int)ct.size();
+      for (int r = 0; r < N; r += R) ct.push_back(BatchTile{k, r});
+      c->bt1[k] = (int)ct.size();
+    }
   }
-  if (c->d_tiles) ctx_free(c, c->d_tiles);
-  if (c->d_ctiles) ctx_free(c, c->d_ctiles);
-  c->d_tiles = nullptr;
-  c->d_ctiles = nullptr;
-  c->ntiles = (int)wt.size();
+  int rc = DE_OK;
+  for (int x = 0; x < 4 && rc == DE_OK; ++x) {
+    rc = upload(c, (void**)&c->d_spans[x], sp[x].data(), sp[x].size() * sizeof(BatchSpan));
+    c->nspans[x] = (int)sp[x].size();
+  }
+  if (rc == DE_OK) rc = upload(c, (void**)&c->d_ctiles, ct.data(), ct.size() * sizeof(BatchTile));
   c->nctiles = (int)ct.size();
-  if (!wt.empty()) {
-    c->d_tiles = (BatchTile*)ctx_alloc(c, wt.size() * sizeof(BatchTile));
-    if (!c->d_tiles) return DE_ENOMEM;
-    if (cudaMemcpyAsync(c->d_tiles, wt.data(), wt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
-        cudaSuccess)
-      return DE_ECUDA;
-  }
-  if (!ct.empty()) {
-    c->d_ctiles = (BatchTile*)ctx_alloc(c, ct.size() * sizeof(BatchTile));
-    if (!c->d_ctiles) return DE_ENOMEM;
-    if (cudaMemcpyAsync(c->d_ctiles, ct.data(), ct.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, c->stream) !=
-        cudaSuccess)
-      return DE_ECUDA;
-  }
+  if (rc != DE_OK) return rc;
   drop_graphs(c);
   return upload_insts(c);
 }
 
+// The row work of every instance (inst < 0) or of one instance.
+static BatchWork batch_work(const de_ctx* c, int inst) {
+  BatchWork w;
+  std::memset(&w, 0, sizeof(w));
+  w.ctr = c->d_span_ctr;
+  if (inst < 0) {
+    for (int x = 0; x < 4; ++x) {
+      w.spans[x] = c->d_spans[x];
+      w.nspans[x] = c->nspans[x];
+    }
+    w.ctiles = c->d_ctiles;
+    w.nctiles = c->nctiles;
+  } else if (c->bgroup[inst] <= 32) {
+    const int x = c->bgroup[inst] == kBatchStaged ? 3 : c->bxo[inst];
+    w.spans[x] = c->d_spans[x] + c->bt0[inst];
+    w.nspans[x] = c->bt1[inst] - c->bt0[inst];
+  } else {
+    w.ctiles = c->d_ctiles + c->bt0[inst];
+    w.nctiles = c->bt1[inst] - c->bt0[inst];
+  }
+  return w;
+}
+
 // Evaluate the parents of every instance (inst < 0) or of one instance.
 static int batch_evaluate(de_ctx* c, int inst) {
-  cudaError_t e;
-  if (inst < 0) {
-    e = launch_batch_evaluate(c->d_insts, c->d_tiles, c->ntiles, c->d_ctiles, c->nctiles, c->d_states, 0, c->n_inst,
-                              c->batch_grid, c->stream);
-  } else {
-    const int n = c->bt1[inst] - c->bt0[inst];
-    if (c->bgroup[inst] <= 32)
-      e = launch_batch_evaluate(c->d_insts, c->d_tiles + c->bt0[inst], n, nullptr, 0, c->d_states, inst, 1,
-                                c->batch_grid, c->stream);
-    else
-      e = launch_batch_evaluate(c->d_insts, nullptr, 0, c->d_ctiles + c->bt0[inst], n, c->d_states, inst, 1,
-                                c->batch_grid, c->stream);
-  }
+  const BatchWork w = batch_work(c, inst);
+  const cudaError_t e = launch_batch_evaluate(c->d_insts, w, c->d_states, inst < 0 ? 0 : inst,
+                                              inst < 0 ? c->n_inst : 1, c->batch_grid, c->stream);
   return cuda_status(e);
 }
 
 cudaError_t batch_launch_generation(de_ctx* c, bool, int) {
-  return launch_batch_generation(c->d_insts, c->d_tiles, c->ntiles, c->d_ctiles, c->nctiles, c->d_ptiles,
-                                 c->nptiles, c->d_plans, c->d_states, c->n_inst, c->batch_grid, c->stream);
+  const BatchWork w = batch_work(c, -1);
+  return launch_batch_generation(c->d_insts, w, c->d_ptiles, c->nptiles, c->d_plans, c->d_states, c->n_inst,
+                                 c->batch_grid, c->stream);
 }
 
 // Plan tiles: 256 consecutive rows of one instance, instances in order.
@@ -194,6 +246,11 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   c->batch_grid = std::max(1, c->sm_count) * 2;
+  if (prepare_batch_stage() != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return DE_ECUDA;
+  }
 
   // arena layout
   auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -227,6 +284,7 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   c->bobj.resize((size_t)n_inst);
   c->bxo.resize((size_t)n_inst);
   c->bgroup.resize((size_t)n_inst);
+  c->blanes.resize((size_t)n_inst);
   c->bcr.resize((size_t)n_inst);
   c->bF.resize((size_t)n_inst);
   c->bb.resize((size_t)n_inst);
@@ -239,7 +297,8 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
     rows += specs[k].N;
   }
   c->d_plans = (RowPlan32*)ctx_alloc(c, (size_t)rows * sizeof(RowPlan32));
-  if (!c->d_plans) {
+  c->d_span_ctr = (unsigned*)ctx_alloc(c, 8 * sizeof(unsigned));
+  if (!c->d_plans || !c->d_span_ctr || cudaMemsetAsync(c->d_span_ctr, 0, 8 * sizeof(unsigned), c->stream) != cudaSuccess) {
     de_destroy(c);
     return DE_ENOMEM;
   }
@@ -269,7 +328,8 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
     p.ell_k = (s.D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(s.D - 1)) : 0.0f;
     c->bobj[k] = (int)s.obj;
     c->bxo[k] = (int)s.xo;
-    c->bgroup[k] = default_group(p.D4);
+    c->bgroup[k] = default_group(p.D4, (int)s.xo);
+    c->blanes[k] = default_lanes(p.D4);
     c->bcr[k] = s.CR;
     c->bF[k] = s.F;
     c->bb[k] = s.b;
@@ -430,24 +490,159 @@ int de_batch_debug_step(de_ctx* c, int32_t inst, float* trial_out, float* ftrial
 int de_batch_set_groups(de_ctx* c, const int32_t* groups) {
   if (!c || !groups) return DE_EINVAL;
   if (!c->batch) return DE_ESTATE;
-  std::vector<int> g((size_t)c->n_inst);
+  std::vector<int> g((size_t)c->n_inst), l = c->blanes;
   for (int k = 0; k < c->n_inst; ++k) {
     int G = groups[k];
-    if (G == 0) G = default_group(c->bp[k].D4);
-    if (G < 4 || G > kBatchMaxGroup || (G & (G - 1)) != 0) return DE_EINVAL;
-    if ((c->bp[k].D4 + G - 1) / G > kBatchMaxD4PerLane) return DE_EINVAL;
+    const int D4 = c->bp[k].D4;
+    if (G == 0) G = default_group(D4, c->bxo[k]);
+    if (G == kBatchStaged) {
+      l[k] = default_lanes(D4);
+    } else if (G < 0) {                              // staged, -G lanes per row
+      const int lanes = -G;
+      if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) return DE_EINVAL;
+      G = kBatchStaged;
+      l[k] = lanes;
+    }
+    if (!valid_group(G, D4, c->bxo[k])) return DE_EINVAL;
     g[k] = G;
   }
   if (sync_stream(c) != DE_OK) return DE_ECUDA;
   c->bgroup = g;
+  c->blanes = l;
   return build_tiles(c);
 }
 
 int de_batch_get_groups(de_ctx* c, int32_t* groups) {
   if (!c || !groups) return DE_EINVAL;
   if (!c->batch) return DE_ESTATE;
-  for (int k = 0; k < c->n_inst; ++k) groups[k] = c->bgroup[k];
+  for (int k = 0; k < c->n_inst; ++k) groups[k] = c->bgroup[k] == kBatchStaged ? -c->blanes[k] : c->bgroup[k];
   return DE_OK;
+}
+
+int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
+  if (!c) return DE_EINVAL;
+  if (!c->batch) return DE_ESTATE;
+  if (reps < 1 || reps > 1000) return DE_EINVAL;
+  int rc = sync_stream(c);
+  if (rc != DE_OK) return rc;
+  // classes: same objective, crossover and D4 octave, rows of at most 512 slots
+  std::map<long long, std::vector<int>> classes;
+  for (int k = 0; k < c->n_inst; ++k) {
+    const int D4 = c->bp[k].D4;
+    if (D4 > kStageMaxD4) continue;
+    int oct = 0;
+    while ((2 << oct) <= D4) ++oct;
+    classes[((long long)c->bobj[k] * 3 + c->bxo[k]) * 64 + oct].push_back(k);
+  }
+  // snapshot of what the trial generations change: fitness and instance states
+  size_t fit_floats = 0;
+  for (int k = 0; k < c->n_inst; ++k) fit_floats += (size_t)c->bp[k].N;
+  unsigned char* snap = (unsigned char*)ctx_alloc(c, (size_t)c->n_inst * sizeof(DevState) + fit_floats * 4);
+  BatchSpan* dsp = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!snap) return DE_ENOMEM;
+  cudaError_t e = cudaMemcpyAsync(snap, c->d_states, (size_t)c->n_inst * sizeof(DevState), cudaMemcpyDeviceToDevice,
+                                  c->stream);
+  {
+    size_t off = (size_t)c->n_inst * sizeof(DevState);
+    for (int k = 0; k < c->n_inst && e == cudaSuccess; ++k) {
+      e = cudaMemcpyAsync(snap + off, c->bp[k].fit, (size_t)c->bp[k].N * 4, cudaMemcpyDeviceToDevice, c->stream);
+      off += (size_t)c->bp[k].N * 4;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess)                               // plans of the current generation, reused by every trial
+    e = launch_batch_plans(c->d_insts, c->d_ptiles, c->nptiles, c->d_plans, c->batch_grid, c->stream);
+  rc = cuda_status(e);
+  size_t max_spans = 0;
+  for (int k = 0; k < c->n_inst; ++k) max_spans += (size_t)(c->bp[k].N + kSpanRows - 1) / kSpanRows;
+  if (rc == DE_OK) {
+    dsp = (BatchSpan*)ctx_alloc(c, std::max<size_t>(1, max_spans) * sizeof(BatchSpan));
+    if (!dsp) rc = DE_ENOMEM;
+  }
+  // one class at a time, the others as they are; the row kernels only are
+  // timed (their results do not depend on the choice, so every trial writes
+  // the same values)
+  for (auto it = classes.begin(); it != classes.end() && rc == DE_OK; ++it) {
+    const std::vector<int>& ks = it->second;
+    const int xo = c->bxo[ks[0]];
+    int d4max = 0;
+    for (int k : ks) d4max = std::max(d4max, c->bp[k].D4);
+    std::vector<std::pair<int, int>> cand;       // (group, staged lanes)
+    for (int G = 4; G <= 32; G *= 2)
+      if (valid_group(G, d4max, xo)) cand.push_back({G, c->blanes[ks[0]]});
+    if (valid_group(kBatchStaged, d4max, xo))
+      for (int l = 4; l <= 32; l *= 2) cand.push_back({kBatchStaged, l});
+    if (cand.size() < 2) continue;
+    double best_t = 1e30;
+    std::pair<int, int> best = {c->bgroup[ks[0]], c->blanes[ks[0]]};
+    for (const auto& cd : cand) {
+      for (int k : ks) {
+        c->bgroup[k] = cd.first;
+        c->blanes[k] = cd.second;
+      }
+      std::vector<BatchSpan> v;
+      for (int k : ks)
+        for (int r = 0; r < c->bp[k].N; r += kSpanRows) {
+          BatchSpan sp;
+          std::memset(&sp, 0, sizeof(sp));
+          sp.plan0 = c->brow_base[k] + r;
+          sp.inst = k;
+          sp.row0 = r;
+          sp.rows = std::min(kSpanRows, c->bp[k].N - r);
+          v.push_back(sp);
+        }
+      BatchWork w;
+      std::memset(&w, 0, sizeof(w));
+      const int kind = cd.first == kBatchStaged ? 3 : xo;
+      w.spans[kind] = dsp;
+      w.nspans[kind] = (int)v.size();
+      w.ctr = c->d_span_ctr;
+      rc = upload_insts(c);
+      if (rc != DE_OK) break;
+      e = cudaMemcpyAsync(dsp, v.data(), v.size() * sizeof(BatchSpan), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = launch_batch_rows(c->d_insts, w, c->d_plans, c->batch_grid, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = launch_batch_rows(c->d_insts, w, c->d_plans, c->batch_grid, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      rc = cuda_status(e);
+      if (rc != DE_OK) break;
+      if (ms < best_t) {
+        best_t = ms;
+        best = cd;
+      }
+    }
+    for (int k : ks) {
+      c->bgroup[k] = best.first;
+      c->blanes[k] = best.second;
+    }
+  }
+  // restore the snapshot, then the lists for the chosen kernels
+  if (snap) {
+    cudaError_t r2 = cudaMemcpyAsync(c->d_states, snap, (size_t)c->n_inst * sizeof(DevState),
+                                     cudaMemcpyDeviceToDevice, c->stream);
+    size_t off = (size_t)c->n_inst * sizeof(DevState);
+    for (int k = 0; k < c->n_inst && r2 == cudaSuccess; ++k) {
+      r2 = cudaMemcpyAsync(c->bp[k].fit, snap + off, (size_t)c->bp[k].N * 4, cudaMemcpyDeviceToDevice, c->stream);
+      off += (size_t)c->bp[k].N * 4;
+    }
+    if (rc == DE_OK) rc = cuda_status(r2);
+  }
+  const int rs = sync_stream(c);
+  if (rc == DE_OK) rc = rs;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (dsp) ctx_free(c, dsp);
+  ctx_free(c, snap);
+  const int rb = build_tiles(c);
+  if (rc == DE_OK) rc = rb;
+  if (rc == DE_OK && groups_out) rc = de_batch_get_groups(c, groups_out);
+  return rc;
 }
 
 int de_batch_size(de_ctx* c, int32_t* n_inst) {

@@ -1,25 +1,27 @@
 // batch_kernel.cu — one generation of many independent DE instances (each
 // with its own N, D, objective, crossover, Cr, F, box and Philox instance
-// field), in three launches over all instances:
+// field), in a few launches over all instances:
 //
 //  1. batch_plan_kernel: one thread per row of every instance draws r1, r2,
 //     r3, j_rand and L (NEC through the threshold table staged in shared
 //     memory, exp by the sequential walk), and gathers the slot bytes of the
 //     row and its donors and the parent fitness into a 32-byte plan. Rows are
 //     independent, so the serial draw work of one row never delays another.
-//  2. batch_warp_kernel (instances with G <= 32 lanes per row: warp tiles
-//     of 32 / G rows, each warp walking its own tiles) and batch_gen_kernel
-//     (G > 32: CTA tiles of R = 256 / G rows); G is a power of two, 4..256,
-//     per instance, and the grid walks each tile list with a grid stride. The list is
-//     grouped by (objective, crossover), longest tiles first within a group,
-//     and each tile calls the row code specialised for its group. A row's group reads its plan, then issues the parent loads and
-//     the donor loads of the masked genes together (one memory round trip),
-//     applies Eq. (1) with clipping, reduces the FP32 fitness over the group,
-//     selects (strict '<') and stores accepted rows to the other slot buffer.
+//  2. the row kernels: batch_stage_kernel (batch_stage.cu) for exp / NEC
+//     rows of D <= 2048 staged through shared memory, batch_span_kernel
+//     (batch_span.cuh; one launch per crossover present) for the instances
+//     with G <= 32 lanes per row kept in registers, and
+//     batch_gen_kernel here for wider rows (CTA tiles of R = 256 / G rows,
+//     G = 64, 128 or 256, grid-stride over a tile list grouped by
+//     (objective, crossover), longest tiles first). A row's group reads its
+//     plan, then issues the parent loads and the donor loads of the masked
+//     genes together (one memory round trip), applies Eq. (1) with clipping,
+//     reduces the FP32 fitness over the group, selects (strict '<') and
+//     stores accepted rows to the other slot buffer.
 //  3. batch_close_kernel: one thread per instance folds the generation into
 //     its best value / best generation and advances its generation counter.
 //
-// With eval_only, batch_gen_kernel evaluates the parents instead (initial
+// With eval_only, the row kernels evaluate the parents instead (initial
 // evaluation), so stored and trial fitness share one reduction order.
 #include "draws.cuh"
 #include "gen_kernel.cuh"
@@ -85,7 +87,7 @@ batch_plan_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restri
     pl.slots = (uint32_t)slot_in[i] | ((uint32_t)slot_in[d.r1] << 8) | ((uint32_t)slot_in[d.r2] << 16) |
                ((uint32_t)slot_in[d.r3] << 24);
     pl.fit_i = p.fit[i];
-    pl.pad = 0;
+    pl.gpar = (int)(gen & 1);
     plans[insts[tl.inst].row_base + i] = pl;
   }
 }
@@ -322,216 +324,6 @@ __device__ __noinline__ void batch_rows(const BatchInst& I, const BatchTile tl, 
   }
 }
 
-// The rows of one warp tile (32 / G rows, G <= 32 lanes each), for
-// instances whose rows fit in one warp: the same loads, crossover, mutation
-// and reduction order as batch_rows, with no CTA barrier, so every warp walks
-// its own tiles at its own pace (more rows in flight per SM). Counters are
-// reduced over the warp and added once per warp tile.
-template <int OBJ, int XO>
-__device__ __noinline__ void batch_rows_warp(const BatchInst& I, const BatchTile tl,
-                                             const RowPlan32* __restrict__ plans, int eval_only) {
-  const GenParams& p = I.g;
-  const int lane = threadIdx.x & 31;
-  const int G = I.group;                          // 4 .. 32
-  const int gi = lane / G, gl = lane - gi * G;
-  const int i = tl.row0 + gi;
-  const bool active = i < p.N;
-  const long long gen = p.st->gen;
-  const uint32_t g = (uint32_t)gen;
-  const int D = p.D, D4 = p.D4;
-  const float F = p.F, lo = p.lo, hi = p.hi;
-
-  RowPlan32 pl{};
-  if (active) {
-    if (eval_only) pl.slots = p.slots[(size_t)(gen & 1) * p.N + i];
-    else pl = plans[I.row_base + i];
-  }
-  const int si = (int)(pl.slots & 0xFFu);
-  const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)(active ? i : 0) * p.pitch);
-  const float4* d1 = reinterpret_cast<const float4*>(((pl.slots >> 8) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r1 * p.pitch);
-  const float4* d2 = reinterpret_cast<const float4*>(((pl.slots >> 16) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r2 * p.pitch);
-  const float4* d3 = reinterpret_cast<const float4*>(((pl.slots >> 24) & 0xFFu ? p.pop1 : p.pop0) + (size_t)pl.r3 * p.pitch);
-
-  float4 x[kBatchVmax];
-  unsigned mk[kBatchVmax];
-#pragma unroll
-  for (int k = 0; k < kBatchVmax; ++k) {
-    const int q = gl + k * G;
-    const bool in = active && q < D4;
-    x[k] = in ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    unsigned m = 0u;
-    if (in && !eval_only) {
-      const int j0 = 4 * q;
-      if constexpr (XO == kBin) {
-        const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
-        m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == pl.jrand) ? 1u : 0u;
-        m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == pl.jrand) ? 2u : 0u;
-        m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == pl.jrand) ? 4u : 0u;
-        m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == pl.jrand) ? 8u : 0u;
-      } else {
-        int dd = j0 - pl.jrand;
-        if (dd < 0) dd += D;                       // (j0 - j_rand) mod D
-        if (dd >= pl.L && dd + 3 < D) {
-          m = 0u;                                  // the slot lies wholly outside the segment
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            int de = dd + e;
-            if (de >= D) de -= D;
-            m |= (de < pl.L) ? (1u << e) : 0u;
-          }
-        }
-      }
-      m &= (1u << min(4, D - j0)) - 1u;
-    }
-    mk[k] = m;
-  }
-  int cnt = 0;
-#pragma unroll
-  for (int k = 0; k < kBatchVmax; ++k) {
-    if (mk[k]) {
-      const int q = gl + k * G;
-      const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
-      const unsigned m = mk[k];
-      if (m & 1u) x[k].x = clip_box(mutate(a1.x, a2.x, a3.x, F), lo, hi);
-      if (m & 2u) x[k].y = clip_box(mutate(a1.y, a2.y, a3.y, F), lo, hi);
-      if (m & 4u) x[k].z = clip_box(mutate(a1.z, a2.z, a3.z, F), lo, hi);
-      if (m & 8u) x[k].w = clip_box(mutate(a1.w, a2.w, a3.w, F), lo, hi);
-      cnt += __popc(m);
-    }
-  }
-
-  Acc s{0.0f, 0.0f, 0.0f};
-  if constexpr (OBJ == kRosenbrock) {
-#pragma unroll
-    for (int k = 0; k < kBatchVmax; ++k) {
-      float nb = __shfl_down_sync(0xFFFFFFFFu, x[k].x, 1, G);
-      const float next0 = __shfl_sync(0xFFFFFFFFu, (k + 1 < kBatchVmax) ? x[k + 1].x : 0.0f, 0, G);
-      if (gl == G - 1) nb = next0;                 // group lane 0, next slot
-      const int q = gl + k * G;
-      if (active && q < D4) {
-        const int j0 = 4 * q;
-        if (j0 + 1 < D) accum_pair(s, x[k].x, x[k].y);
-        if (j0 + 2 < D) accum_pair(s, x[k].y, x[k].z);
-        if (j0 + 3 < D) accum_pair(s, x[k].z, x[k].w);
-        if (j0 + 4 < D) accum_pair(s, x[k].w, nb);
-      }
-    }
-  } else {
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < kBatchVmax; ++k) {
-        const int q = gl + k * G;
-        if (q < D4) {
-          const int j0 = 4 * q;
-          accum_gene<OBJ>(s, x[k].x, j0, p);
-          if (j0 + 1 < D) accum_gene<OBJ>(s, x[k].y, j0 + 1, p);
-          if (j0 + 2 < D) accum_gene<OBJ>(s, x[k].z, j0 + 2, p);
-          if (j0 + 3 < D) accum_gene<OBJ>(s, x[k].w, j0 + 3, p);
-        }
-      }
-    }
-  }
-  constexpr int NS = ObjTraits<OBJ>::kSums;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    if (o < G) {
-      s.a += __shfl_xor_sync(0xFFFFFFFFu, s.a, o, G);
-      if (NS > 1) s.b += __shfl_xor_sync(0xFFFFFFFFu, s.b, o, G);
-      if (NS > 2) s.c += __shfl_xor_sync(0xFFFFFFFFu, s.c, o, G);
-      if (XO == kBin) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o, G);
-    }
-  }
-
-  int acc = 0, Lrow = 0;
-  unsigned long long key = ~0ull;
-  if (active && gl == 0) {
-    float f = finalize_fitness<OBJ>(s, p);
-    if (f != f) f = __int_as_float(0x7F800000);
-    if (eval_only) {
-      p.fit[i] = f;
-      key = best_key_of(f, i);
-    } else {
-      acc = (f < pl.fit_i) ? 1 : 0;
-      p.slots[(size_t)((gen + 1) & 1) * p.N + i] = (uint8_t)(acc ? 1 - si : si);
-      Lrow = (XO == kBin) ? cnt : pl.L;
-      if (acc) {
-        p.fit[i] = f;
-        key = best_key_of(f, i);
-      }
-      if (p.dbg_ftrial) p.dbg_ftrial[i] = f;
-      if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)acc;
-      if (p.dbg_draws) {
-        int* o = p.dbg_draws + 5 * (size_t)i;
-        o[0] = pl.r1; o[1] = pl.r2; o[2] = pl.r3; o[3] = pl.jrand; o[4] = Lrow;
-      }
-    }
-  }
-  // warp totals (leaders hold their row's values, other lanes zero)
-  unsigned long long kmin = key, masked = (unsigned long long)Lrow, accepts = (unsigned long long)acc;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long ko = __shfl_xor_sync(0xFFFFFFFFu, kmin, o);
-    kmin = ko < kmin ? ko : kmin;
-    masked += __shfl_xor_sync(0xFFFFFFFFu, masked, o);
-    accepts += __shfl_xor_sync(0xFFFFFFFFu, accepts, o);
-  }
-  if (lane == 0) {
-    if (kmin != ~0ull) atomicMin(&p.st->best_key, kmin);
-    if (!eval_only) {
-      if (accepts) atomicAdd(&p.st->accepts, accepts);
-      atomicAdd(&p.st->masked, masked);
-    }
-  }
-  acc = __shfl_sync(0xFFFFFFFFu, acc, gi * G);     // the group leader's decision
-  if (active && !eval_only) {
-    if (acc) {
-      float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
-#pragma unroll
-      for (int k = 0; k < kBatchVmax; ++k) {
-        const int q = gl + k * G;
-        if (q < D4) st_stream(out + q, x[k]);
-      }
-    }
-    if (p.dbg_trial) {
-      float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch);
-#pragma unroll
-      for (int k = 0; k < kBatchVmax; ++k) {
-        const int q = gl + k * G;
-        if (q < D4) o[q] = x[k];
-      }
-    }
-  }
-}
-
-template <int OBJ>
-__device__ __forceinline__ void batch_rows_warp_xo(int xo, const BatchInst& I, const BatchTile tl,
-                                                   const RowPlan32* plans, int eval_only) {
-  if (xo == kBin) batch_rows_warp<OBJ, kBin>(I, tl, plans, eval_only);
-  else if (xo == kExp) batch_rows_warp<OBJ, kExp>(I, tl, plans, eval_only);
-  else batch_rows_warp<OBJ, kNec>(I, tl, plans, eval_only);
-}
-
-// Warp tiles: warp w of CTA b takes tiles b * 8 + w, then every
-// gridDim.x * 8-th; no CTA barrier anywhere.
-__global__ void __launch_bounds__(kBatchThreads, 2)
-batch_warp_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
-                  const RowPlan32* __restrict__ plans, int eval_only) {
-  const int warps = kBatchThreads / 32;
-  for (int wt = blockIdx.x * warps + (threadIdx.x >> 5); wt < ntiles; wt += gridDim.x * warps) {
-    const BatchTile tl = tiles[wt];
-    const BatchInst& I = insts[tl.inst];
-    switch (I.obj) {                                 // uniform over the warp
-      case kSphere: batch_rows_warp_xo<kSphere>(I.xo, I, tl, plans, eval_only); break;
-      case kRastrigin: batch_rows_warp_xo<kRastrigin>(I.xo, I, tl, plans, eval_only); break;
-      case kAckley: batch_rows_warp_xo<kAckley>(I.xo, I, tl, plans, eval_only); break;
-      case kRosenbrock: batch_rows_warp_xo<kRosenbrock>(I.xo, I, tl, plans, eval_only); break;
-      case kGriewank: batch_rows_warp_xo<kGriewank>(I.xo, I, tl, plans, eval_only); break;
-      default: batch_rows_warp_xo<kElliptic>(I.xo, I, tl, plans, eval_only); break;
-    }
-  }
-}
-
 template <int OBJ>
 __device__ __forceinline__ void batch_rows_xo(int xo, const BatchInst& I, const BatchTile tl,
                                               const RowPlan32* plans, int eval_only, BatchSmem& sm) {
@@ -587,23 +379,52 @@ __global__ void batch_reset_best_kernel(DevState* states, int n) {
     states[k].best_key = ~0ULL;
 }
 
-cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
-                                    const BatchTile* ctiles, int nctiles, const BatchTile* ptiles, int nptiles,
-                                    RowPlan32* plans, DevState* states, int n_inst, int grid, cudaStream_t s) {
-  if (nwtiles + nctiles <= 0) return cudaSuccess;
+cudaError_t launch_batch_plans(const BatchInst* insts, const BatchTile* ptiles, int nptiles, RowPlan32* plans,
+                               int grid, cudaStream_t s) {
   batch_plan_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
-  if (nwtiles > 0) batch_warp_kernel<<<grid, kBatchThreads, 0, s>>>(insts, wtiles, nwtiles, plans, 0);
-  if (nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ctiles, nctiles, plans, 0);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_spans(const BatchInst* insts, const BatchWork& w, const RowPlan32* plans, int eval_only,
+                                int grid, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (w.nspans[kBin] > 0 && e == cudaSuccess)
+    e = launch_batch_span_bin(insts, w.spans[kBin], w.nspans[kBin], plans, w.ctr + 0, eval_only, grid, s);
+  if (w.nspans[kExp] > 0 && e == cudaSuccess)
+    e = launch_batch_span_exp(insts, w.spans[kExp], w.nspans[kExp], plans, w.ctr + 2, eval_only, grid, s);
+  if (w.nspans[kNec] > 0 && e == cudaSuccess)
+    e = launch_batch_span_nec(insts, w.spans[kNec], w.nspans[kNec], plans, w.ctr + 4, eval_only, grid, s);
+  if (w.nspans[3] > 0 && e == cudaSuccess)
+    e = launch_batch_stage(insts, w.spans[3], w.nspans[3], plans, w.ctr + 6, eval_only, grid, s);
+  return e;
+}
+
+cudaError_t launch_batch_rows(const BatchInst* insts, const BatchWork& w, const RowPlan32* plans, int grid,
+                              cudaStream_t s) {
+  cudaError_t e = launch_spans(insts, w, plans, 0, grid, s);
+  if (e != cudaSuccess) return e;
+  if (w.nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, w.ctiles, w.nctiles, plans, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_generation(const BatchInst* insts, const BatchWork& w, const BatchTile* ptiles,
+                                    int nptiles, RowPlan32* plans, DevState* states, int n_inst, int grid,
+                                    cudaStream_t s) {
+  if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nspans[3] + w.nctiles <= 0) return cudaSuccess;
+  batch_plan_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
+  cudaError_t e = launch_spans(insts, w, plans, 0, grid, s);
+  if (e != cudaSuccess) return e;
+  if (w.nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, w.ctiles, w.nctiles, plans, 0);
   batch_close_kernel<<<(n_inst + 255) / 256, 256, 0, s>>>(states, n_inst, 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
-                                  const BatchTile* ctiles, int nctiles, DevState* states, int first_inst,
+cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchWork& w, DevState* states, int first_inst,
                                   int n_inst, int grid, cudaStream_t s) {
   batch_reset_best_kernel<<<(n_inst + 255) / 256, 256, 0, s>>>(states + first_inst, n_inst);
-  if (nwtiles > 0) batch_warp_kernel<<<grid, kBatchThreads, 0, s>>>(insts, wtiles, nwtiles, nullptr, 1);
-  if (nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ctiles, nctiles, nullptr, 1);
+  cudaError_t e = launch_spans(insts, w, nullptr, 1, grid, s);
+  if (e != cudaSuccess) return e;
+  if (w.nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, w.ctiles, w.nctiles, nullptr, 1);
   batch_close_kernel<<<(n_inst + 255) / 256, 256, 0, s>>>(states + first_inst, n_inst, 1);
   return cudaGetLastError();
 }

@@ -54,19 +54,22 @@ struct de_ctx {
   bool batch = false;
   int n_inst = 0;
   std::vector<GenParams> bp;          // per instance, device pointers into the arena
-  std::vector<int> bobj, bxo, bgroup, bt0, bt1;   // objective, crossover, group, tile range
+  std::vector<int> bobj, bxo, bgroup, bt0, bt1;   // objective, crossover, group, span / tile range
+  std::vector<int> blanes;                         // lanes per row in the staged kernel
   std::vector<double> bcr;
   std::vector<float> bF;
   std::vector<de_bounds> bb;
   de::BatchInst* d_insts = nullptr;
-  de::BatchTile* d_tiles = nullptr;      // warp tiles (instances with G <= 32)
+  de::BatchSpan* d_spans[4] = {nullptr, nullptr, nullptr, nullptr};   // register kernel per crossover, staged
+  int nspans[4] = {0, 0, 0, 0};
+  unsigned* d_span_ctr = nullptr;        // 2 queue counters per span list
   de::BatchTile* d_ctiles = nullptr;     // CTA tiles (G > 32)
   de::BatchTile* d_ptiles = nullptr;  // plan tiles: 256 rows of one instance
   de::RowPlan32* d_plans = nullptr;
   int nptiles = 0;
   std::vector<long long> brow_base;
   de::DevState* d_states = nullptr;
-  int ntiles = 0, nctiles = 0, batch_grid = 0, max_pitch = 0;
+  int nctiles = 0, batch_grid = 0, max_pitch = 0;
   // shifted-rotated objectives (sr_api.cu)
   bool rotated = false;
   de::SrParams sp{};

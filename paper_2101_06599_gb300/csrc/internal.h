@@ -40,33 +40,69 @@ cudaError_t launch_gen_pipe(int xo, int obj, const PipeParams& pp, int grid, int
 // tile list; a tile is 256 / group rows of one instance.
 struct BatchInst {
   GenParams g;
-  int obj, xo, group, tiles;
+  int obj, xo;
+  int group;                 // lanes per row of the register kernels, or kBatchStaged
+  int lanes;                 // lanes per row in the staged kernel (4, 8, 16 or 32)
   long long row_base;        // first plan index of this instance
 };
 struct BatchTile {
   int inst, row0;
 };
 // Draws of one row, written by the plan kernel: donors, j_rand, L, the slot
-// bytes of the row and its donors (bits 0-7, 8-15, 16-23, 24-31) and the
-// parent fitness.
+// bytes of the row and its donors (bits 0-7, 8-15, 16-23, 24-31), the
+// parent fitness and the parity of the generation being made.
 struct RowPlan32 {
   int r1, r2, r3, jrand, L;
   uint32_t slots;
   float fit_i;
-  int pad;
+  int gpar;
 };
+// Up to kSpanRows consecutive rows of one instance whose rows take at most
+// one warp (G <= 32, or the staged kernel); plan0 = the plan index of row0.
+struct alignas(16) BatchSpan {
+  long long plan0;
+  int inst, row0, rows, pad_[3];
+};
+constexpr int kSpanRows = 32;
 constexpr int kBatchThreadsHost = 256;
 constexpr int kBatchMaxGroup = 256;
 constexpr int kBatchMaxD4PerLane = 16;
-// plan kernel + row kernel + close kernel (one generation of every instance)
-cudaError_t launch_batch_generation(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
-                                    const BatchTile* ctiles, int nctiles, const BatchTile* ptiles, int nptiles,
-                                    RowPlan32* plans, DevState* states, int n_inst, int grid, cudaStream_t s);
-// reset best keys, evaluate the parents of the tiles' rows, close (instances
+// The row work of one launch: span lists per crossover (bin, exp, NEC) with
+// their queue counters (2 per list, zero between launches) and the CTA tiles
+// of the instances with G > 32.
+struct BatchWork {
+  const BatchSpan* spans[4];   // register kernel for bin, exp, NEC; staged kernel (exp and NEC)
+  int nspans[4];
+  unsigned* ctr;               // 8 counters
+  const BatchTile* ctiles;
+  int nctiles;
+};
+// plan kernel + row kernels + close kernel (one generation of every instance)
+cudaError_t launch_batch_generation(const BatchInst* insts, const BatchWork& w, const BatchTile* ptiles,
+                                    int nptiles, RowPlan32* plans, DevState* states, int n_inst, int grid,
+                                    cudaStream_t s);
+// the plan kernel alone, and the row kernels alone (plans already made)
+cudaError_t launch_batch_plans(const BatchInst* insts, const BatchTile* ptiles, int nptiles, RowPlan32* plans,
+                               int grid, cudaStream_t s);
+cudaError_t launch_batch_rows(const BatchInst* insts, const BatchWork& w, const RowPlan32* plans, int grid,
+                              cudaStream_t s);
+// reset best keys, evaluate the parents of the listed rows, close (instances
 // first_inst .. first_inst + n_inst - 1)
-cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchTile* wtiles, int nwtiles,
-                                  const BatchTile* ctiles, int nctiles, DevState* states, int first_inst,
+cudaError_t launch_batch_evaluate(const BatchInst* insts, const BatchWork& w, DevState* states, int first_inst,
                                   int n_inst, int grid, cudaStream_t s);
+// the staged row kernel for exp / NEC rows of D <= 2048 (batch_stage.cu)
+constexpr int kBatchStaged = 1;          // group value that selects it
+constexpr int kStageMaxD4 = 512;
+cudaError_t prepare_batch_stage();
+cudaError_t launch_batch_stage(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
+                               cudaStream_t);
+// the span row kernel alone, one per crossover (batch_span_*.cu)
+cudaError_t launch_batch_span_bin(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
+                                  cudaStream_t);
+cudaError_t launch_batch_span_exp(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
+                                  cudaStream_t);
+cudaError_t launch_batch_span_nec(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
+                                  cudaStream_t);
 
 // Shifted-rotated objectives (sr_kernels.cu, sr_tc.cu); SrParams and
 // SrBound in sr_common.cuh.

@@ -104,6 +104,7 @@ def load_library(build_if_missing: bool = True):
         "de_batch_set_population": ([vp, i32, vp, vp], C.c_int),
         "de_batch_debug_step": ([vp, i32, vp, vp, vp, vp], C.c_int),
         "de_batch_set_groups": ([vp, C.POINTER(i32)], C.c_int),
+        "de_batch_autotune": ([vp, i32, C.POINTER(i32)], C.c_int),
         "de_batch_get_groups": ([vp, C.POINTER(i32)], C.c_int),
         "de_batch_size": ([vp, C.POINTER(i32)], C.c_int),
         "de_nec_step_noalloc": ([vp, vp, vp, vp, i32, i32, i32, f32, f64, C.c_int, de_bounds, C.c_uint64,
@@ -366,6 +367,12 @@ def de_batch_size(ctx):
     return n.value
 
 
+def de_batch_autotune(ctx, reps, n_inst):
+    out = (C.c_int32 * n_inst)()
+    _check(load_library().de_batch_autotune(C.c_void_p(ctx), int(reps), out), "de_batch_autotune")
+    return [int(v) for v in out]
+
+
 def de_batch_set_groups(ctx, groups):
     arr = (C.c_int32 * len(groups))(*[int(g) for g in groups])
     _check(load_library().de_batch_set_groups(C.c_void_p(ctx), arr), "de_batch_set_groups")
@@ -455,6 +462,11 @@ class Batch:
 
     def set_groups(self, groups):
         de_batch_set_groups(self.ctx, groups)
+
+    def autotune(self, reps=5):
+        """Time the candidate row kernels per group of instances and keep the
+        fastest (results do not depend on the choice); returns the groups."""
+        return de_batch_autotune(self.ctx, reps, len(self.specs))
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -33,7 +33,7 @@ def test_header_declares_the_calls():
     names = declared_functions()
     for required in ("de_create", "de_step", "de_run", "de_best", "de_stats", "de_destroy",
                      "de_get_population", "de_set_population", "de_save", "de_load", "de_debug_step",
-                     "de_batch_create", "de_strerror"):
+                     "de_batch_create", "de_batch_autotune", "de_strerror"):
         assert required in names
 
 
@@ -114,6 +114,8 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.de_run(None, 3) == DE.DE_EINVAL
     assert lib.de_synchronize(None) == DE.DE_EINVAL
     assert lib.de_best(None, None, None, None, None) == DE.DE_EINVAL
+    assert lib.de_batch_autotune(None, 3, None) == DE.DE_EINVAL
+    assert lib.de_batch_set_groups(None, None) == DE.DE_EINVAL
     lib.de_destroy(None)
 
 

@@ -90,14 +90,22 @@ def test_batch_one_generation_parity_every_instance():
         b.close()
 
 
+def min_group(D):
+    """Fewest lanes per row of the register kernels: ceil(ceil(D/4) / G) <= 16."""
+    G = 4
+    while G < 256 and -(-(-(-D // 4)) // G) > 16:
+        G *= 2
+    return G
+
+
 def test_batch_tile_shapes_keep_draws_and_trials():
     specs = [dict(N=40, D=D, obj="rastrigin", bounds=W.BOXES["rastrigin"], xo=xo, CR=0.9, F=0.5)
-             for D in (7, 100, 600) for xo in ("nec", "bin")]
+             for D in (7, 100, 600, 3000) for xo in ("nec", "bin")]
     ref = None
     for mult in (1, 2, 4):
         b = DE.Batch(specs, seed=3)
         try:
-            b.set_groups([min(256, g * mult) for g in b.groups()])
+            b.set_groups([min(256, min_group(sp["D"]) * mult) for sp in specs])
             out = []
             for k, sp in enumerate(specs):
                 # a fresh population right before its step: the trial depends only on it and the generation
@@ -175,4 +183,92 @@ def test_batched_512_instance_workload_sampled():
             check_instance_step(b, k, specs[k], 4)
         assert b.stats()["generation"] == 3 + len(picks)
     finally:
+        b.close()
+
+
+def test_batch_group_choice_is_bit_invariant():
+    """For rows of at most one warp (register tiles of G = 4 .. 32 lanes, or
+    the staged kernel) the fitness is summed in one order whatever the
+    kernel, so every valid choice gives the same fitness bits, selections and
+    trajectories."""
+    specs = []
+    k = 0
+    for D in (1, 3, 10, 64, 130, 257, 600, 1000, 2000):
+        for xo in ("nec", "bin", "exp"):
+            obj = OBJS[k % len(OBJS)]
+            specs.append(dict(N=37 + 3 * k, D=D, obj=obj, bounds=W.BOXES[obj], xo=xo, CR=0.9, F=0.5))
+            k += 1
+    ref = None
+    for G in (0, -4, -8, -16, -32, 4, 8, 16, 32):
+        b = DE.Batch(specs, seed=11)
+        try:
+            if G <= 0:          # the staged kernel with -G lanes per row for exp / NEC
+                b.set_groups([G if sp["xo"] != "bin" else 0 for sp in specs])
+            else:
+                b.set_groups([max(min_group(sp["D"]), G) for sp in specs])
+            for k in range(len(specs)):
+                b.set_population(k, W.population(specs[k]["N"], specs[k]["D"], *specs[k]["bounds"], 70 + k))
+            b.run(5)
+            out = [b.population(k) for k in range(len(specs))]
+            if ref is None:
+                ref = out
+            for k, ((p, f), (p0, f0)) in enumerate(zip(out, ref)):
+                assert np.array_equal(f.view(np.uint32), f0.view(np.uint32)), (G, k)
+                assert np.array_equal(p.view(np.uint32), p0.view(np.uint32)), (G, k)
+        finally:
+            b.close()
+
+
+def test_batch_groups_validation_and_defaults():
+    specs = [dict(N=20, D=D, obj="sphere", bounds=W.BOXES["sphere"], xo=xo, CR=0.9, F=0.5)
+             for (D, xo) in [(10, "nec"), (2000, "exp"), (2049, "nec"), (300, "bin"), (5000, "bin")]]
+    b = DE.Batch(specs, seed=1)
+    default = [-4, -32, min_group(2049), min_group(300), min_group(5000)]
+    try:
+        assert b.groups() == default
+        for bad in ([1, 1, 1, 0, 0], [0, 0, 0, 1, 0], [0, 2, 0, 0, 0], [0, 0, 0, 12, 0], [0, 4, 0, 0, 0],
+                    [-2, 0, 0, 0, 0], [-64, 0, 0, 0, 0], [0, 0, -32, 0, 0], [0, 0, 0, -8, 0]):
+            with pytest.raises(DE.DEError):
+                b.set_groups(bad)
+            assert b.groups() == default
+        b.set_groups([4, 32, 0, 32, 0])
+        assert b.groups() == [4, 32, min_group(2049), 32, min_group(5000)]
+        b.set_groups([-8, -16, 0, 0, 0])
+        assert b.groups() == [-8, -16, min_group(2049), min_group(300), min_group(5000)]
+        b.set_groups([1, 1, 0, 0, 0])
+        assert b.groups() == default
+    finally:
+        b.close()
+
+
+def test_batch_autotune_keeps_state_and_results():
+    """The autotuner's trial generations leave populations, fitness, counters
+    and the generation as they were, and the tuned batch follows the same
+    trajectory as an untuned one."""
+    specs = mixed_specs()
+    n = len(specs)
+    a = DE.Batch(specs, seed=21)
+    b = DE.Batch(specs, seed=21)
+    try:
+        a.run(3)
+        b.run(3)
+        before = [a.population(k) for k in range(n)]
+        st = [a.stats(k) for k in range(n)]
+        groups = a.autotune(reps=2)
+        assert groups == a.groups()
+        for k in range(n):
+            p, f = a.population(k)
+            assert np.array_equal(p.view(np.uint32), before[k][0].view(np.uint32)), k
+            assert np.array_equal(f.view(np.uint32), before[k][1].view(np.uint32)), k
+            assert a.stats(k) == st[k], k
+        a.run(4)
+        b.run(4)
+        for k in range(n):
+            pa, fa = a.population(k)
+            pb, fb = b.population(k)
+            assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32)), k
+            assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32)), k
+        assert a.stats() == b.stats()
+    finally:
+        a.close()
         b.close()
