@@ -263,7 +263,7 @@ int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftri
  *   G = 4..256 (a power of two with ceil(ceil(D/4) / G) <= 16) register
  *              tiles of G threads per row (one warp of 32 / G rows for
  *              G <= 32, a CTA of 256 / G rows above);
- *   0          the default: 1 where allowed, else the smallest such G.
+ *   0          the default: the smallest such G.
  * de_batch_get_groups reports staged instances as -G. Draws are unchanged by
  * the choice, and so are fitness values, selections and trajectories for
  * every choice with at most 32 threads per row (staged, and G = 4..32):
@@ -274,12 +274,14 @@ int de_batch_set_groups(de_ctx *ctx, const int32_t *groups);
 int de_batch_get_groups(de_ctx *ctx, int32_t *groups);
 
 /* Autotuner: pick each instance's row kernel (the values above) by timing.
- * Instances are grouped by objective, crossover and the octave of ceil(D/4)
- * (rows of D <= 2048; wider rows keep their tiles). For each group in turn
- * every candidate (register tiles of 4..32 lanes per row; for exp and NEC
- * the staged pipeline with 4..32 lanes) runs the row kernels of one
- * generation `reps` times (1..1000) on the current populations, the other
- * groups as they stand, and the fastest is kept. The trials reuse the draws
+ * Instances are grouped by crossover and the octave of ceil(D/4) (rows of
+ * D <= 2048; wider rows keep their tiles). For each group in turn, every
+ * candidate (register tiles of 4..32 lanes per row; for exp and NEC the
+ * staged pipeline with 4..32 lanes) is timed over `reps` (1..1000) runs of
+ * the row kernels of one generation of every instance, the other groups as
+ * they stand, so that kernels which slow each other down when they run
+ * together (instruction cache, occupancy) are judged together; the fastest
+ * is kept. The trials reuse the draws
  * of the current generation and leave populations, fitness, counters and the
  * generation as they were, and the choice changes no result (every
  * candidate sums the fitness in one order). Synchronises; drops captured

@@ -32,12 +32,9 @@ static int min_group(int D4) {
   return G;
 }
 
-// Default row kernel: the staged kernel for the segment crossovers (exp, NEC)
-// up to D = 2048, the register kernels otherwise.
-static int default_group(int D4, int xo) {
-  if (xo != kBin && D4 <= kStageMaxD4) return kBatchStaged;
-  return min_group(D4);
-}
+// Default row kernel: register tiles with the fewest lanes (on the
+// 512-instance NEC mix the fastest single choice; de_batch_autotune refines).
+static int default_group(int D4, int) { return min_group(D4); }
 
 static bool valid_group(int G, int D4, int xo) {
   if (G == kBatchStaged) return xo != kBin && D4 <= kStageMaxD4;
@@ -525,22 +522,21 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
   if (reps < 1 || reps > 1000) return DE_EINVAL;
   int rc = sync_stream(c);
   if (rc != DE_OK) return rc;
-  // classes: same objective, crossover and D4 octave, rows of at most 512 slots
-  std::map<long long, std::vector<int>> classes;
+  // classes: same crossover and D4 octave, rows of at most 512 slots
+  std::map<int, std::vector<int>> classes;
   for (int k = 0; k < c->n_inst; ++k) {
     const int D4 = c->bp[k].D4;
     if (D4 > kStageMaxD4) continue;
     int oct = 0;
     while ((2 << oct) <= D4) ++oct;
-    classes[((long long)c->bobj[k] * 3 + c->bxo[k]) * 64 + oct].push_back(k);
+    classes[c->bxo[k] * 64 + oct].push_back(k);
   }
   // snapshot of what the trial generations change: fitness and instance states
   size_t fit_floats = 0;
   for (int k = 0; k < c->n_inst; ++k) fit_floats += (size_t)c->bp[k].N;
   unsigned char* snap = (unsigned char*)ctx_alloc(c, (size_t)c->n_inst * sizeof(DevState) + fit_floats * 4);
-  BatchSpan* dsp = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!snap) return DE_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaMemcpyAsync(snap, c->d_states, (size_t)c->n_inst * sizeof(DevState), cudaMemcpyDeviceToDevice,
                                   c->stream);
   {
@@ -555,15 +551,56 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
   if (e == cudaSuccess)                               // plans of the current generation, reused by every trial
     e = launch_batch_plans(c->d_insts, c->d_ptiles, c->nptiles, c->d_plans, c->batch_grid, c->stream);
   rc = cuda_status(e);
-  size_t max_spans = 0;
-  for (int k = 0; k < c->n_inst; ++k) max_spans += (size_t)(c->bp[k].N + kSpanRows - 1) / kSpanRows;
+  // time of the row kernels of one generation of every instance under the
+  // current choice (their results do not depend on it: every trial writes
+  // the same values, which the snapshot undoes)
+  auto trial = [&](float& ms) -> int {
+    int r = build_tiles(c);
+    if (r != DE_OK) return r;
+    const BatchWork w = batch_work(c, -1);
+    cudaError_t t = launch_batch_rows(c->d_insts, w, c->d_plans, c->batch_grid, c->stream);
+    if (t == cudaSuccess) t = cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < reps && t == cudaSuccess; ++i)
+      t = launch_batch_rows(c->d_insts, w, c->d_plans, c->batch_grid, c->stream);
+    if (t == cudaSuccess) t = cudaEventRecord(e1, c->stream);
+    if (t == cudaSuccess) t = cudaEventSynchronize(e1);
+    if (t == cudaSuccess) t = cudaEventElapsedTime(&ms, e0, e1);
+    return cuda_status(t);
+  };
+  // start from the fastest of a few whole-batch choices: as they stand, the
+  // fewest register lanes, 32 register lanes, the staged kernel with its
+  // default lanes where allowed
   if (rc == DE_OK) {
-    dsp = (BatchSpan*)ctx_alloc(c, std::max<size_t>(1, max_spans) * sizeof(BatchSpan));
-    if (!dsp) rc = DE_ENOMEM;
+    std::vector<int> bg = c->bgroup, bl = c->blanes;
+    float best_t = 0.0f;
+    rc = trial(best_t);
+    for (int rule = 0; rule < 3 && rc == DE_OK; ++rule) {
+      std::vector<int> g0 = c->bgroup, l0 = c->blanes;
+      for (const auto& cl : classes)
+        for (int k : cl.second) {
+          const int D4 = c->bp[k].D4, xo = c->bxo[k];
+          if (rule == 0) c->bgroup[k] = min_group(D4);
+          if (rule == 1) c->bgroup[k] = std::max(min_group(D4), 32);
+          if (rule == 2 && valid_group(kBatchStaged, D4, xo)) {
+            c->bgroup[k] = kBatchStaged;
+            c->blanes[k] = default_lanes(D4);
+          }
+          if (!valid_group(c->bgroup[k], D4, xo)) c->bgroup[k] = g0[k];
+        }
+      float ms = 0.0f;
+      rc = trial(ms);
+      if (rc == DE_OK && ms < best_t) {
+        best_t = ms;
+        bg = c->bgroup;
+        bl = c->blanes;
+      }
+      c->bgroup = g0;
+      c->blanes = l0;
+    }
+    c->bgroup = bg;
+    c->blanes = bl;
   }
-  // one class at a time, the others as they are; the row kernels only are
-  // timed (their results do not depend on the choice, so every trial writes
-  // the same values)
+  // coordinate descent: one class at a time, the others as they stand
   for (auto it = classes.begin(); it != classes.end() && rc == DE_OK; ++it) {
     const std::vector<int>& ks = it->second;
     const int xo = c->bxo[ks[0]];
@@ -571,59 +608,42 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
     for (int k : ks) d4max = std::max(d4max, c->bp[k].D4);
     std::vector<std::pair<int, int>> cand;       // (group, staged lanes)
     for (int G = 4; G <= 32; G *= 2)
-      if (valid_group(G, d4max, xo)) cand.push_back({G, c->blanes[ks[0]]});
+      if (valid_group(G, d4max, xo)) cand.push_back({G, 0});
     if (valid_group(kBatchStaged, d4max, xo))
       for (int l = 4; l <= 32; l *= 2) cand.push_back({kBatchStaged, l});
     if (cand.size() < 2) continue;
-    double best_t = 1e30;
-    std::pair<int, int> best = {c->bgroup[ks[0]], c->blanes[ks[0]]};
-    for (const auto& cd : cand) {
+    std::vector<int> g0(ks.size()), l0(ks.size());
+    for (size_t u = 0; u < ks.size(); ++u) {
+      g0[u] = c->bgroup[ks[u]];
+      l0[u] = c->blanes[ks[u]];
+    }
+    float best_t = 0.0f;
+    rc = trial(best_t);                              // the class as it stands
+    int best = -1;
+    for (size_t ci = 0; ci < cand.size() && rc == DE_OK; ++ci) {
       for (int k : ks) {
-        c->bgroup[k] = cd.first;
-        c->blanes[k] = cd.second;
+        c->bgroup[k] = cand[ci].first;
+        if (cand[ci].second) c->blanes[k] = cand[ci].second;
       }
-      std::vector<BatchSpan> v;
-      for (int k : ks)
-        for (int r = 0; r < c->bp[k].N; r += kSpanRows) {
-          BatchSpan sp;
-          std::memset(&sp, 0, sizeof(sp));
-          sp.plan0 = c->brow_base[k] + r;
-          sp.inst = k;
-          sp.row0 = r;
-          sp.rows = std::min(kSpanRows, c->bp[k].N - r);
-          v.push_back(sp);
-        }
-      BatchWork w;
-      std::memset(&w, 0, sizeof(w));
-      const int kind = cd.first == kBatchStaged ? 3 : xo;
-      w.spans[kind] = dsp;
-      w.nspans[kind] = (int)v.size();
-      w.ctr = c->d_span_ctr;
-      rc = upload_insts(c);
-      if (rc != DE_OK) break;
-      e = cudaMemcpyAsync(dsp, v.data(), v.size() * sizeof(BatchSpan), cudaMemcpyHostToDevice, c->stream);
-      if (e == cudaSuccess) e = launch_batch_rows(c->d_insts, w, c->d_plans, c->batch_grid, c->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-      for (int r = 0; r < reps && e == cudaSuccess; ++r)
-        e = launch_batch_rows(c->d_insts, w, c->d_plans, c->batch_grid, c->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      rc = cuda_status(e);
-      if (rc != DE_OK) break;
-      if (ms < best_t) {
+      rc = trial(ms);
+      if (rc == DE_OK && ms < best_t) {
         best_t = ms;
-        best = cd;
+        best = (int)ci;
+      }
+      for (size_t u = 0; u < ks.size(); ++u) {
+        c->bgroup[ks[u]] = g0[u];
+        c->blanes[ks[u]] = l0[u];
       }
     }
-    for (int k : ks) {
-      c->bgroup[k] = best.first;
-      c->blanes[k] = best.second;
-    }
+    if (best >= 0)
+      for (int k : ks) {
+        c->bgroup[k] = cand[best].first;
+        if (cand[best].second) c->blanes[k] = cand[best].second;
+      }
   }
   // restore the snapshot, then the lists for the chosen kernels
-  if (snap) {
+  {
     cudaError_t r2 = cudaMemcpyAsync(c->d_states, snap, (size_t)c->n_inst * sizeof(DevState),
                                      cudaMemcpyDeviceToDevice, c->stream);
     size_t off = (size_t)c->n_inst * sizeof(DevState);
@@ -637,7 +657,6 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
   if (rc == DE_OK) rc = rs;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  if (dsp) ctx_free(c, dsp);
   ctx_free(c, snap);
   const int rb = build_tiles(c);
   if (rc == DE_OK) rc = rb;
