@@ -4,13 +4,14 @@
 // Device memory: one arena per context holding, per instance, two slot
 // buffers (N x pitch floats), fitness, slot bytes and NEC thresholds, plus
 // one DevState per instance (contiguous, so the totals are one copy).
-// Row work: instance k with G_k <= 32 lanes per row is cut into spans of up
-// to 32 rows (one list per crossover, taken by warps from a queue); wider
-// rows are cut into CTA tiles of 256 / G_k rows. Lists are grouped by the
-// row code's specialisation and ordered longest first within a group. A
-// second list
-// of 256-row tiles drives the plan kernel; plans (32 bytes per row of every
-// instance) live in one buffer indexed by the instance's first row.
+// Row work: instance k with G_k <= 32 lanes per row (or the staged kernel)
+// is cut into spans of up to 32 rows (one list per row kernel, taken by
+// warps from a queue); wider rows are cut into CTA tiles of 256 / G_k rows.
+// Lists are grouped by the row code's specialisation, the groups ordered by
+// total work (largest first) and the instances longest first within a group.
+// A second list of 256-row tiles drives the plan kernel; plans (32 bytes per
+// row of every instance) live in one buffer indexed by the instance's first
+// row.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -88,13 +89,19 @@ static int build_tiles(de_ctx* c) {
   std::vector<int> order((size_t)c->n_inst);
   std::iota(order.begin(), order.end(), 0);
   // instances whose rows take at most a warp go to span lists (one per
-  // crossover), grouped by (objective, G) so that one specialisation of the
-  // row code runs at a time, longest spans first within a group; wider rows
-  // go to CTA tiles of 256 / G rows, grouped by (objective, crossover)
+  // row kernel), wider rows to CTA tiles of 256 / G rows
+  // classes (one specialisation of the row code each) by total work, largest
+  // first, so that the warps at the head of the queue share one
+  // specialisation as long as possible
+  auto cls = [&](int k) {
+    const int kind = c->bgroup[k] == kBatchStaged ? 1024 + c->blanes[k] : c->bgroup[k];
+    return (c->bobj[k] * 3 + c->bxo[k]) * 2048 + kind;
+  };
+  std::map<int, double> work;
+  for (int k = 0; k < c->n_inst; ++k) work[cls(k)] += (double)c->bp[k].N * c->bp[k].D4;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    const int ca = (c->bobj[a] * 3 + c->bxo[a]) * 512 + c->bgroup[a];
-    const int cb = (c->bobj[b] * 3 + c->bxo[b]) * 512 + c->bgroup[b];
-    if (ca != cb) return ca < cb;
+    const int ca = cls(a), cb = cls(b);
+    if (ca != cb) return work[ca] != work[cb] ? work[ca] > work[cb] : ca < cb;
     return span_cost(c, a) > span_cost(c, b);
   });
   std::vector<BatchSpan> sp[4];
