@@ -170,6 +170,18 @@ int de_synchronize(de_ctx *ctx);
 int de_best(de_ctx *ctx, float *x_out, double *f_out, int32_t *idx_out,
             int64_t *best_gen_out);
 
+/* Best individual so far, without waiting: queues on the context's stream
+ * the gather of the best row and its copy into `record_out`, a host buffer
+ * of DE_BEST_RECORD_BYTES(D) bytes that the caller owns (page-locked, or the
+ * copy is staged and the call may block); the record is complete once the
+ * stream has reached this point (de_synchronize). Layout: double best_f at
+ * byte 0, int64 best_gen at 8, int32 best row at 16, int32 device error at
+ * 20 (0 = none; else the code de_best would return), then the D floats of
+ * the row at byte 32. Successive calls may target different records (a ring
+ * of per-step results). DE_ESTATE on a batch. */
+#define DE_BEST_RECORD_BYTES(D) (32 + 4 * (size_t)(D))
+int de_best_async(de_ctx *ctx, void *record_out);
+
 /* Device counters (synchronises). */
 int de_stats(de_ctx *ctx, de_stats_t *out);
 

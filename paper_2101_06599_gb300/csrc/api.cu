@@ -437,6 +437,25 @@ int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* b
   return DE_OK;
 }
 
+int de_best_async(de_ctx* c, void* record_out) {
+  if (!c || !record_out) return DE_EINVAL;
+  if (c->batch) return DE_ESTATE;
+  // a page-locked record the device can address is written by the gather
+  // itself; anything else goes through the staging buffer and a copy
+  cudaPointerAttributes a;
+  void* dev = nullptr;
+  if (((uintptr_t)record_out & 15u) == 0 && cudaPointerGetAttributes(&a, record_out) == cudaSuccess &&
+      a.type == cudaMemoryTypeHost && a.devicePointer != nullptr)
+    dev = a.devicePointer;
+  cudaGetLastError();
+  if (dev) return cuda_status(launch_best_gather(c->p, dev, c->stream));
+  cudaError_t e = launch_best_gather(c->p, c->staging, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(record_out, c->staging, kStagingHeader + (size_t)c->D * sizeof(float), cudaMemcpyDeviceToHost,
+                        c->stream);
+  return e == cudaSuccess ? DE_OK : DE_ECUDA;
+}
+
 int de_stats(de_ctx* c, de_stats_t* out) {
   if (!c || !out) return DE_EINVAL;
   if (c->batch) return batch_stats(c, out);
@@ -465,7 +484,7 @@ int de_get_population(de_ctx* c, float* pop_out, float* fit_out) {
   if (c->batch) return DE_ESTATE;
   cudaError_t e = launch_normalize(c->p, c->stream);
   if (e == cudaSuccess && pop_out)
-    e = cudaMemcpy2DAsync(pop_out, (size_t)c->D * sizeof(float), c->p.pop0, (size_t)c->pitch * sizeof(float),
+    e = copy_rows(pop_out, (size_t)c->D * sizeof(float), c->p.pop0, (size_t)c->pitch * sizeof(float),
                           (size_t)c->D * sizeof(float), (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && fit_out)
     e = cudaMemcpyAsync(fit_out, c->p.fit, (size_t)c->N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
@@ -479,7 +498,7 @@ int de_set_population(de_ctx* c, const float* pop, const float* fit) {
   // the current generation's slot half is cleared: buffer 0 holds every row
   cudaError_t e = cudaMemsetAsync(c->p.slots + (size_t)(c->host_gen & 1) * c->N, 0, (size_t)c->N, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(c->p.pop0, (size_t)c->pitch * sizeof(float), pop, (size_t)c->D * sizeof(float),
+    e = copy_rows(c->p.pop0, (size_t)c->pitch * sizeof(float), pop, (size_t)c->D * sizeof(float),
                           (size_t)c->D * sizeof(float), (size_t)c->N, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return DE_ECUDA;
   int rc;
@@ -558,7 +577,7 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->p.slots + (size_t)(s.gen & 1) * c->N, 0, (size_t)c->N, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(c->p.pop0, (size_t)c->pitch * sizeof(float), in + sizeof(SaveHeader),
+    e = copy_rows(c->p.pop0, (size_t)c->pitch * sizeof(float), in + sizeof(SaveHeader),
                           (size_t)c->D * sizeof(float), (size_t)c->D * sizeof(float), (size_t)c->N,
                           cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
@@ -592,7 +611,7 @@ int de_debug_step(de_ctx* c, float* trial_out, float* ftrial_out, uint8_t* accep
   }
   cudaError_t e = cudaSuccess;
   if (rc == DE_OK && trial_out)
-    e = cudaMemcpy2DAsync(trial_out, (size_t)c->D * sizeof(float), dtrial, (size_t)c->pitch * sizeof(float),
+    e = copy_rows(trial_out, (size_t)c->D * sizeof(float), dtrial, (size_t)c->pitch * sizeof(float),
                           (size_t)c->D * sizeof(float), (size_t)c->N, cudaMemcpyDeviceToHost, c->stream);
   if (rc == DE_OK && e == cudaSuccess && ftrial_out)
     e = cudaMemcpyAsync(ftrial_out, dft, (size_t)c->N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);

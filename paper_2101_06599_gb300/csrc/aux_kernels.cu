@@ -96,20 +96,34 @@ __global__ void close_eval_kernel(DevState* st) {
   st->done = 0u;
 }
 
-__global__ void best_gather_kernel(const __grid_constant__ GenParams p, unsigned char* staging) {
+// One float4 of the best row per thread (the row is read in one round trip);
+// block 0 also writes the header. `out` may be device memory or a mapped,
+// page-locked host record.
+__global__ void best_gather_kernel(const __grid_constant__ GenParams p, unsigned char* out) {
   const unsigned long long bk = p.st->best_key;
   int idx = (int)(uint32_t)(bk & 0xFFFFFFFFull);
   if (idx < 0 || idx >= p.N) idx = 0;   // only before any evaluation
   const long long gen = p.st->gen;
   const int si = p.slots[(size_t)(gen & 1) * p.N + idx];
   const float* row = (si ? p.pop1 : p.pop0) + (size_t)idx * p.pitch;
-  float* out = reinterpret_cast<float*>(staging + kStagingHeader);
-  for (int j = threadIdx.x; j < p.D; j += blockDim.x) out[j] = row[j];
-  if (threadIdx.x == 0) {
-    *reinterpret_cast<double*>(staging) = (double)from_ordered_bits((uint32_t)(bk >> 32));
-    *reinterpret_cast<long long*>(staging + 8) = p.st->best_gen;
-    *reinterpret_cast<int*>(staging + 16) = idx;
-    *reinterpret_cast<int*>(staging + 20) = (int)p.st->error;
+  float* dst = reinterpret_cast<float*>(out + kStagingHeader);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < p.D4) {
+    const float4 v = reinterpret_cast<const float4*>(row)[q];
+    const int j = 4 * q;
+    if (j + 4 <= p.D) {
+      reinterpret_cast<float4*>(dst)[q] = v;
+    } else {
+      dst[j] = v.x;
+      if (j + 1 < p.D) dst[j + 1] = v.y;
+      if (j + 2 < p.D) dst[j + 2] = v.z;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *reinterpret_cast<double*>(out) = (double)from_ordered_bits((uint32_t)(bk >> 32));
+    *reinterpret_cast<long long*>(out + 8) = p.st->best_gen;
+    *reinterpret_cast<int*>(out + 16) = idx;
+    *reinterpret_cast<int*>(out + 20) = (int)p.st->error;
   }
 }
 
@@ -147,7 +161,7 @@ cudaError_t launch_close_eval(const GenParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s) {
-  best_gather_kernel<<<1, 256, 0, s>>>(p, static_cast<unsigned char*>(staging));
+  best_gather_kernel<<<(unsigned)((p.D4 + 127) / 128), 128, 0, s>>>(p, static_cast<unsigned char*>(staging));
   return cudaGetLastError();
 }
 cudaError_t launch_normalize(const GenParams& p, cudaStream_t s) {

@@ -416,7 +416,7 @@ int de_batch_get_population(de_ctx* c, int32_t inst, float* pop_out, float* fit_
   const GenParams& p = c->bp[inst];
   cudaError_t e = launch_normalize(p, c->stream);
   if (e == cudaSuccess && pop_out)
-    e = cudaMemcpy2DAsync(pop_out, (size_t)p.D * sizeof(float), p.pop0, (size_t)p.pitch * sizeof(float),
+    e = copy_rows(pop_out, (size_t)p.D * sizeof(float), p.pop0, (size_t)p.pitch * sizeof(float),
                           (size_t)p.D * sizeof(float), (size_t)p.N, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && fit_out)
     e = cudaMemcpyAsync(fit_out, p.fit, (size_t)p.N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
@@ -431,7 +431,7 @@ int de_batch_set_population(de_ctx* c, int32_t inst, const float* pop, const flo
   const GenParams& p = c->bp[inst];
   cudaError_t e = cudaMemsetAsync(p.slots + (size_t)(c->host_gen & 1) * p.N, 0, (size_t)p.N, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(p.pop0, (size_t)p.pitch * sizeof(float), pop, (size_t)p.D * sizeof(float),
+    e = copy_rows(p.pop0, (size_t)p.pitch * sizeof(float), pop, (size_t)p.D * sizeof(float),
                           (size_t)p.D * sizeof(float), (size_t)p.N, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return DE_ECUDA;
   int rc;
@@ -473,7 +473,7 @@ int de_batch_debug_step(de_ctx* c, int32_t inst, float* trial_out, float* ftrial
     bi.g = p0;   // restore the descriptor without test outputs
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_insts + inst, &bi, sizeof(bi), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && trial_out)
-      e = cudaMemcpy2DAsync(trial_out, (size_t)p0.D * sizeof(float), dtrial, (size_t)p0.pitch * sizeof(float),
+      e = copy_rows(trial_out, (size_t)p0.D * sizeof(float), dtrial, (size_t)p0.pitch * sizeof(float),
                             (size_t)p0.D * sizeof(float), (size_t)p0.N, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && ftrial_out)
       e = cudaMemcpyAsync(ftrial_out, dft, (size_t)p0.N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);

@@ -81,6 +81,13 @@ struct de_ctx {
 
 
 namespace de_host {
+// Rows of `width` bytes between pitched buffers: one linear copy when both
+// sides are contiguous, a 2D copy otherwise.
+inline cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows,
+                             cudaMemcpyKind kind, cudaStream_t s) {
+  if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * rows, kind, s);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, kind, s);
+}
 int cuda_status(cudaError_t e);
 void* ctx_alloc(de_ctx* c, size_t bytes);
 void ctx_free(de_ctx* c, void* p);

@@ -85,6 +85,7 @@ def load_library(build_if_missing: bool = True):
         "de_run": ([vp, i32], C.c_int),
         "de_synchronize": ([vp], C.c_int),
         "de_best": ([vp, vp, C.POINTER(f64), C.POINTER(i32), C.POINTER(i64)], C.c_int),
+        "de_best_async": ([vp, vp], C.c_int),
         "de_stats": ([vp, C.POINTER(de_stats_t)], C.c_int),
         "de_get_population": ([vp, vp, vp], C.c_int),
         "de_set_population": ([vp, vp, vp], C.c_int),
@@ -233,6 +234,34 @@ def de_best(ctx, x_out=None):
     xp = None if x_out is None else _host_ptr(x_out, np.float32, 1, True)
     _check(load_library().de_best(C.c_void_p(ctx), xp, C.byref(f), C.byref(idx), C.byref(bg)), "de_best")
     return f.value, idx.value, bg.value
+
+
+def best_record_bytes(D):
+    """Bytes of one de_best_async record for rows of D genes."""
+    return 32 + 4 * int(D)
+
+
+def de_best_async(ctx, record, D):
+    """Queue the best row and value into `record` (a page-locked uint8 host
+    buffer of best_record_bytes(D) bytes); read it with parse_best_record
+    after de_synchronize."""
+    _check(load_library().de_best_async(C.c_void_p(ctx), _host_ptr(record, np.uint8, best_record_bytes(D), True)),
+           "de_best_async")
+
+
+def parse_best_record(record, D):
+    """(f, idx, best_gen, x) of a completed de_best_async record; raises the
+    device error the record carries."""
+    b = record.numpy() if hasattr(record, "numpy") else np.asarray(record)
+    b = b.view(np.uint8)
+    err = int(b[20:24].view(np.int32)[0])
+    if err:
+        raise DEError(err, "de_best_async")
+    f = float(b[0:8].view(np.float64)[0])
+    gen = int(b[8:16].view(np.int64)[0])
+    idx = int(b[16:20].view(np.int32)[0])
+    x = b[32:32 + 4 * D].view(np.float32).copy()
+    return f, idx, gen, x
 
 
 def de_stats(ctx):

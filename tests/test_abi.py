@@ -115,6 +115,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.de_synchronize(None) == DE.DE_EINVAL
     assert lib.de_best(None, None, None, None, None) == DE.DE_EINVAL
     assert lib.de_batch_autotune(None, 3, None) == DE.DE_EINVAL
+    assert lib.de_best_async(None, None) == DE.DE_EINVAL
     assert lib.de_batch_set_groups(None, None) == DE.DE_EINVAL
     lib.de_destroy(None)
 

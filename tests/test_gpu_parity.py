@@ -422,3 +422,26 @@ def test_stream_matches_row_kernel_over_generations():
     finally:
         a.close()
         b.close()
+
+
+def test_best_async_record_matches_best():
+    """de_best_async queues the same best row and value that de_best returns."""
+    N, D = 64, 37
+    opt = DE.Optimizer(N, D, F=0.5, CR=0.9, xo="nec", obj="rastrigin", bounds=W.BOXES["rastrigin"], seed=3)
+    try:
+        import torch
+        rec = DE.best_record_bytes(D)
+        ring = torch.empty(3 * rec, dtype=torch.uint8).pin_memory().numpy()
+        for k in range(3):
+            opt.step()
+            DE.de_best_async(opt.ctx, ring[k * rec:(k + 1) * rec], D)
+        DE.de_synchronize(opt.ctx)
+        f, idx, gen, x = DE.parse_best_record(ring[2 * rec:], D)
+        x2 = np.empty(D, dtype=np.float32)
+        f2, idx2, gen2 = DE.de_best(opt.ctx, x2)
+        assert (f, idx, gen) == (f2, idx2, gen2)
+        assert np.array_equal(x.view(np.uint32), x2.view(np.uint32))
+        fs = [DE.parse_best_record(ring[k * rec:(k + 1) * rec], D)[0] for k in range(3)]
+        assert fs[0] >= fs[1] >= fs[2]
+    finally:
+        opt.close()
