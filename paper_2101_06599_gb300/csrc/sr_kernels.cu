@@ -324,30 +324,34 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 // transposed copy (contiguous 64-column rows of R^T); each stage's a = x - o
 // is formed in shared memory in K-major order before use. A fixed grid walks
 // the entry tiles, so a short list still spreads over the SMs.
-constexpr int kLsM = 16, kLsN = 64, kLsK = 32, kLsStages = 4, kLsThreads = 128;
-constexpr int kLsLdA = kLsK + 4, kLsLdB = kLsN + 4, kLsLdT = kLsM + 4;
+constexpr int kLsN = 64, kLsK = 32, kLsStages = 4, kLsThreads = 128;
+constexpr int kSrListRows = 16;                  // entries per tile of the list product (8 measured slower)
+constexpr int kLsLdA = kLsK + 4, kLsLdB = kLsN + 4;
 
-template <bool VEC>
+// kLsM entries per tile (8 or 16): RPT = kLsM / 8 entries per thread.
+template <bool VEC, int kLsM>
 __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
+  constexpr int RPT = kLsM / 8;
+  constexpr int kLsLdT = kLsM + 4;
   const GenParams& p = sp.g;
   __shared__ __align__(16) float Araw[kLsStages][kLsM][kLsLdA];
   __shared__ __align__(16) float Osh[kLsStages][kLsK];
   __shared__ __align__(16) float Bsh[kLsStages][kLsK][kLsLdB];
   __shared__ __align__(16) float At[kLsK][kLsLdT];
   __shared__ const float* rowp[kLsM];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows 2 ty, 2 ty + 1
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows RPT ty .. RPT ty + RPT - 1
   const int n0 = blockIdx.x * kLsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
   const int KS = (p.D + kLsK - 1) / kLsK;
 
-  // one stage: A 16 rows x 8 chunks (row t >> 3, chunk t & 7), o 8 chunks
+  // one stage: A kLsM rows x 8 chunks (row t >> 3, chunk t & 7), o 8 chunks
   // (threads 0..7), B 32 rows of R^T x 16 chunks (q = t + 128 i: row q >> 4,
   // chunk q & 15); out-of-range pieces are zero-filled
   auto issue = [&](int step) {
     const int st = step % kLsStages, k0 = step * kLsK;
-    {
+    if (t < 8 * kLsM) {
       const int m = t >> 3, c = (t & 7) * 4, j = k0 + c;
       const float* xa = rowp[m];
       if constexpr (VEC) {
@@ -401,9 +405,9 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
       if (s0 < KS) issue(s0);
       cp_async_commit();
     }
-    float acc[2][4];
+    float acc[RPT][4];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < RPT; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
     for (int step = 0; step < KS; ++step) {
@@ -414,26 +418,32 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
       const int st = step % kLsStages;
 #pragma unroll
       for (int i = 0; i < kLsM * kLsK / kLsThreads; ++i) {   // a = x - o, K-major
-        const int e = t + kLsThreads * i, m = e & 15, k = e >> 4;
+        const int e = t + kLsThreads * i, m = e % kLsM, k = e / kLsM;
         At[k][m] = __fsub_rn(Araw[st][m][k], Osh[st][k]);
       }
       __syncthreads();
 #pragma unroll 8
       for (int kk = 0; kk < kLsK; ++kk) {
-        const float2 av = *reinterpret_cast<const float2*>(&At[kk][ty * 2]);
+        float ar[RPT];
+        if constexpr (RPT == 2) {
+          const float2 av = *reinterpret_cast<const float2*>(&At[kk][ty * 2]);
+          ar[0] = av.x;
+          ar[RPT - 1] = av.y;
+        } else {
+          ar[0] = At[kk][ty];
+        }
         const float4 bv = *reinterpret_cast<const float4*>(&Bsh[st][kk][tx * 4]);
-        const float ar[2] = {av.x, av.y};
         const float br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < RPT; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
       }
     }
     cp_async_wait<0>();
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int e = r0 + ty * 2 + a;
+    for (int a = 0; a < RPT; ++a) {
+      const int e = r0 + ty * RPT + a;
       float sg, sw;
       sr_tile_reduce(sp, acc[a], n0 + tx * 4, sg, sw);
       if (tx == 0 && e < nrows) {
@@ -601,10 +611,11 @@ cudaError_t launch_sr_trial(int xo, int /*vidx*/, const SrParams& sp, int /*bloc
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
   const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
   if (mode == 2) {
-    const int tiles = (max_rows + kLsM - 1) / kLsM;
+    constexpr int M = kSrListRows;
+    const int tiles = (max_rows + M - 1) / M;
     const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 128)));
-    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true><<<grid, kLsThreads, 0, s>>>(sp);
-    else sr_gemm_fp32_list_kernel<false><<<grid, kLsThreads, 0, s>>>(sp);
+    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true, M><<<grid, kLsThreads, 0, s>>>(sp);
+    else sr_gemm_fp32_list_kernel<false, M><<<grid, kLsThreads, 0, s>>>(sp);
     return cudaGetLastError();
   }
   const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
