@@ -23,6 +23,8 @@
 //
 // With eval_only, the row kernels evaluate the parents instead (initial
 // evaluation), so stored and trial fitness share one reduction order.
+#include <algorithm>
+
 #include "draws.cuh"
 #include "gen_kernel.cuh"
 #include "internal.h"
@@ -379,9 +381,13 @@ __global__ void batch_reset_best_kernel(DevState* states, int n) {
     states[k].best_key = ~0ULL;
 }
 
+// The plan kernel is latency-bound (table, then slot bytes and fitness, per
+// tile): four times the row kernels' grid keeps more tiles in flight.
+static int plan_grid(int nptiles, int grid) { return std::max(1, std::min(nptiles, 4 * grid)); }
+
 cudaError_t launch_batch_plans(const BatchInst* insts, const BatchTile* ptiles, int nptiles, RowPlan32* plans,
                                int grid, cudaStream_t s) {
-  batch_plan_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
+  batch_plan_kernel<<<plan_grid(nptiles, grid), kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
   return cudaGetLastError();
 }
 
@@ -411,7 +417,7 @@ cudaError_t launch_batch_generation(const BatchInst* insts, const BatchWork& w, 
                                     int nptiles, RowPlan32* plans, DevState* states, int n_inst, int grid,
                                     cudaStream_t s) {
   if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nspans[3] + w.nctiles <= 0) return cudaSuccess;
-  batch_plan_kernel<<<grid, kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
+  batch_plan_kernel<<<plan_grid(nptiles, grid), kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
   cudaError_t e = launch_spans(insts, w, plans, 0, grid, s);
   if (e != cudaSuccess) return e;
   if (w.nctiles > 0) batch_gen_kernel<<<grid, kBatchThreads, 0, s>>>(insts, w.ctiles, w.nctiles, plans, 0);
