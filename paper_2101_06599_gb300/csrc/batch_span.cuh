@@ -29,17 +29,6 @@ namespace de {
 constexpr int kSpanThreads = 256;
 constexpr int kSpanVmax = 16;
 
-struct SpanAcc {
-  float a, b, c;
-};
-
-template <int NS>
-__device__ __forceinline__ void span_acc_add(SpanAcc& d, const SpanAcc& s) {
-  d.a += s.a;
-  if (NS > 1) d.b += s.b;
-  if (NS > 2) d.c += s.c;
-}
-
 // The rows [row0, row0 + rows) of one instance, R = 32 / G rows at a time.
 // spl: the span's plans in shared memory (unused when eval_only).
 template <int OBJ, int XO, int G>
