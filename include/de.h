@@ -270,12 +270,12 @@ int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftri
  *              lanes per row (G = 4, 8, 16 or 32): each warp loads the next
  *              pass of up to 32 rows / 8 KB into registers while it
  *              processes the previous one from shared memory;
- *   1          the staged pipeline with its default G (a lane per float4
- *              slot, at most 32);
+ *   1          the staged pipeline with its default G (32);
  *   G = 4..256 (a power of two with ceil(ceil(D/4) / G) <= 16) register
  *              tiles of G threads per row (one warp of 32 / G rows for
  *              G <= 32, a CTA of 256 / G rows above);
- *   0          the default: the smallest such G.
+ *   0          the default: 1 for exp and NEC rows of D <= 2048, else the
+ *              smallest such G.
  * de_batch_get_groups reports staged instances as -G. Draws are unchanged by
  * the choice, and so are fitness values, selections and trajectories for
  * every choice with at most 32 threads per row (staged, and G = 4..32):

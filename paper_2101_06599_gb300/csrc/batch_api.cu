@@ -33,9 +33,14 @@ static int min_group(int D4) {
   return G;
 }
 
-// Default row kernel: register tiles with the fewest lanes (on the
-// 512-instance NEC mix the fastest single choice; de_batch_autotune refines).
-static int default_group(int D4, int) { return min_group(D4); }
+// Default row kernel: the staged kernel for the segment crossovers (exp, NEC)
+// on rows of D <= 2048 (on the 512-instance NEC mix the fastest single
+// choice), register tiles with the fewest lanes otherwise; de_batch_autotune
+// refines.
+static int default_group(int D4, int xo) {
+  if (xo != kBin && D4 <= kStageMaxD4) return kBatchStaged;
+  return min_group(D4);
+}
 
 static bool valid_group(int G, int D4, int xo) {
   if (G == kBatchStaged) return xo != kBin && D4 <= kStageMaxD4;
@@ -43,12 +48,9 @@ static bool valid_group(int G, int D4, int xo) {
   return (D4 + G - 1) / G <= kBatchMaxD4PerLane;
 }
 
-// Lanes per row in the staged kernel: enough for one slot per lane, at most 32.
-static int default_lanes(int D4) {
-  int G = 4;
-  while (G < 32 && G < D4) G *= 2;
-  return G;
-}
+// Lanes per row in the staged kernel by default: the whole warp (fastest on
+// the 512-instance mix for every row length).
+static int default_lanes(int) { return 32; }
 
 // The device descriptor of instance k (every field set here, nowhere else).
 static BatchInst make_inst(const de_ctx* c, int k) {

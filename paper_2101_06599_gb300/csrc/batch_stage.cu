@@ -27,6 +27,8 @@
 // copied into one of three rotating shared buffers one span ahead, so no
 // global read sits between two passes; the generation parity comes with the
 // row plans.
+#include <algorithm>
+
 #include "draws.cuh"
 #include "internal.h"
 #include "objectives.cuh"
@@ -455,14 +457,24 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
 
 size_t batch_stage_smem() { return (size_t)kPwWarps * sizeof(PassSmem); }
 
+int g_stage_ctas_per_sm = 2;                         // resident CTAs per SM (set once by prepare)
+
 cudaError_t prepare_batch_stage() {
-  return cudaFuncSetAttribute(batch_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)batch_stage_smem());
+  cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_stage_smem());
+  int n = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel, kPwThreads, batch_stage_smem());
+  if (e == cudaSuccess && n > 0) g_stage_ctas_per_sm = n;
+  return e;
 }
 
+// grid: the row kernels' grid of two CTAs per SM; this kernel fills every SM
+// with as many CTAs as fit.
 cudaError_t launch_batch_stage(const BatchInst* insts, const BatchSpan* spans, int nspans, const RowPlan32* plans,
                                unsigned* ctr, int eval_only, int grid, cudaStream_t s) {
-  batch_stage_kernel<<<grid, kPwThreads, batch_stage_smem(), s>>>(insts, spans, nspans, plans, ctr, eval_only);
+  const int g = std::max(1, grid / 2) * g_stage_ctas_per_sm;
+  batch_stage_kernel<<<g, kPwThreads, batch_stage_smem(), s>>>(insts, spans, nspans, plans, ctr, eval_only);
   return cudaGetLastError();
 }
 

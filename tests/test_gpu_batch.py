@@ -223,7 +223,7 @@ def test_batch_groups_validation_and_defaults():
     specs = [dict(N=20, D=D, obj="sphere", bounds=W.BOXES["sphere"], xo=xo, CR=0.9, F=0.5)
              for (D, xo) in [(10, "nec"), (2000, "exp"), (2049, "nec"), (300, "bin"), (5000, "bin")]]
     b = DE.Batch(specs, seed=1)
-    default = [min_group(10), min_group(2000), min_group(2049), min_group(300), min_group(5000)]
+    default = [-32, -32, min_group(2049), min_group(300), min_group(5000)]
     try:
         assert b.groups() == default
         for bad in ([1, 1, 1, 0, 0], [0, 0, 0, 1, 0], [0, 2, 0, 0, 0], [0, 0, 0, 12, 0], [0, 4, 0, 0, 0],
@@ -236,7 +236,7 @@ def test_batch_groups_validation_and_defaults():
         b.set_groups([-8, -16, 0, 0, 0])
         assert b.groups() == [-8, -16, min_group(2049), min_group(300), min_group(5000)]
         b.set_groups([1, 1, 0, 0, 0])           # the staged kernel with its default lanes
-        assert b.groups() == [-4, -32] + default[2:]
+        assert b.groups() == default
         b.set_groups([0, 0, 0, 0, 0])
         assert b.groups() == default
     finally:
