@@ -303,8 +303,8 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
     rows += specs[k].N;
   }
   c->d_plans = (RowPlan32*)ctx_alloc(c, (size_t)rows * sizeof(RowPlan32));
-  c->d_span_ctr = (unsigned*)ctx_alloc(c, 8 * sizeof(unsigned));
-  if (!c->d_plans || !c->d_span_ctr || cudaMemsetAsync(c->d_span_ctr, 0, 8 * sizeof(unsigned), c->stream) != cudaSuccess) {
+  c->d_span_ctr = (unsigned*)ctx_alloc(c, 12 * sizeof(unsigned));
+  if (!c->d_plans || !c->d_span_ctr || cudaMemsetAsync(c->d_span_ctr, 0, 12 * sizeof(unsigned), c->stream) != cudaSuccess) {
     de_destroy(c);
     return DE_ENOMEM;
   }

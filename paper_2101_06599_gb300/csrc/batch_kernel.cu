@@ -25,6 +25,7 @@
 // evaluation), so stored and trial fitness share one reduction order.
 #include <algorithm>
 
+#include "batch_plan.cuh"
 #include "draws.cuh"
 #include "gen_kernel.cuh"
 #include "internal.h"
@@ -34,7 +35,6 @@ namespace de {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchVmax = 16;
-constexpr int kBatchTableCap = 4096;
 
 // ---------------------------------------------------------------------------
 // 1. plans
@@ -46,9 +46,9 @@ batch_plan_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restri
   int cached = -1;
   for (int tile = blockIdx.x; tile < nptiles; tile += gridDim.x) {
     const BatchTile tl = ptiles[tile];
-    const GenParams& p = insts[tl.inst].g;
-    const int xo = insts[tl.inst].xo;
-    const bool tab_smem = (xo == kNec) && p.nT <= kBatchTableCap;
+    const BatchInst& I = insts[tl.inst];
+    const GenParams& p = I.g;
+    const bool tab_smem = (I.xo == kNec) && p.nT <= kBatchTableCap;
     if (tl.inst != cached) {                   // uniform: every thread sees the same tile
       __syncthreads();                         // previous table no longer read
       if (tab_smem)
@@ -58,39 +58,7 @@ batch_plan_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restri
     }
     const int i = tl.row0 + threadIdx.x;
     if (i >= p.N) continue;
-    const long long gen = p.st->gen;
-    const uint32_t g = (uint32_t)gen;
-    const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
-    RowDraws d;
-    draw_donors(p, g, i, d);
-    int L = 0;
-    if (xo == kNec) {
-      if (p.cr_mode == kCrZero) L = 1;
-      else if (p.cr_mode == kCrOne) L = p.D;
-      else {
-        const uint32_t w = philox_block(p.key, kStreamLen, p.inst, g, (uint32_t)i, 0u).x;
-        if (w == 0u) {
-          L = p.D;
-        } else {
-          int lo = 0, hi = min(p.D - 1, p.nT);
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            const uint32_t tv = tab_smem ? s_tab[mid - 1] : __ldg(p.nec_tm1 + (mid - 1));
-            if (w <= tv) lo = mid; else hi = mid - 1;
-          }
-          L = 1 + lo;
-        }
-      }
-    } else if (xo == kExp) {
-      L = exp_walk_length(p, g, i);
-    }
-    RowPlan32 pl;
-    pl.r1 = d.r1; pl.r2 = d.r2; pl.r3 = d.r3; pl.jrand = d.jrand; pl.L = L;
-    pl.slots = (uint32_t)slot_in[i] | ((uint32_t)slot_in[d.r1] << 8) | ((uint32_t)slot_in[d.r2] << 16) |
-               ((uint32_t)slot_in[d.r3] << 24);
-    pl.fit_i = p.fit[i];
-    pl.gpar = (int)(gen & 1);
-    plans[insts[tl.inst].row_base + i] = pl;
+    plans[I.row_base + i] = make_row_plan(I, i, tab_smem ? s_tab : nullptr);
   }
 }
 
@@ -358,22 +326,8 @@ batch_gen_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restric
 // 3. close
 // ---------------------------------------------------------------------------
 __global__ void batch_close_kernel(DevState* states, int n, int eval_only) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    DevState& st = states[k];
-    const float bf = from_ordered_bits((uint32_t)(st.best_key >> 32));
-    st.base_row = (int)(uint32_t)(st.best_key & 0xFFFFFFFFull);
-    if (eval_only) {
-      st.best_f = bf;
-      st.best_gen = st.gen;
-    } else {
-      if (bf < st.best_f) {
-        st.best_f = bf;
-        st.best_gen = st.gen + 1;
-      }
-      st.gen = st.gen + 1;
-    }
-    st.done = 0u;
-  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    close_instance(states[k], eval_only);
 }
 
 __global__ void batch_reset_best_kernel(DevState* states, int n) {
@@ -417,6 +371,9 @@ cudaError_t launch_batch_generation(const BatchInst* insts, const BatchWork& w, 
                                     int nptiles, RowPlan32* plans, DevState* states, int n_inst, int grid,
                                     cudaStream_t s) {
   if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nspans[3] + w.nctiles <= 0) return cudaSuccess;
+  if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nctiles == 0 && batch_fused_supported())
+    return launch_batch_fused(insts, w.spans[3], w.nspans[3], ptiles, nptiles, plans, states, n_inst, w.ctr + 6,
+                              grid, s);
   batch_plan_kernel<<<plan_grid(nptiles, grid), kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
   cudaError_t e = launch_spans(insts, w, plans, 0, grid, s);
   if (e != cudaSuccess) return e;

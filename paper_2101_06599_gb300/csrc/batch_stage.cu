@@ -28,7 +28,9 @@
 // global read sits between two passes; the generation parity comes with the
 // row plans.
 #include <algorithm>
+#include <cstring>
 
+#include "batch_plan.cuh"
 #include "draws.cuh"
 #include "internal.h"
 #include "objectives.cuh"
@@ -357,22 +359,99 @@ __device__ __forceinline__ void flush(const GenParams& p, Cnt& c, int eval_only)
   c.accepts = 0u;
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): an arrival
+// counter and a sense word that flips once all CTAs have arrived. The wait is
+// bounded; false if it gave up.
+__device__ bool grid_barrier(unsigned* count, unsigned* sense, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned s0 = atomicAdd(sense, 0u);
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1u) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicExch(sense, s0 ^ 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (atomicAdd(sense, 0u) == s0) {
+        if (global_ns() - t0 > kWaitLimitNs) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // ctr[0]: next span to take; ctr[1]: warps finished (the last one resets both).
+// FUSED (a whole generation in one cooperative launch, every instance on this
+// kernel): the plans of every row first (plan tiles of 256 rows, the NEC
+// table staged in the CTA's shared memory), a grid barrier (ctr[2], ctr[3]),
+// the rows, and the last warp to finish closes every instance.
+template <bool FUSED>
 __global__ void __launch_bounds__(kPwThreads, 3)
 batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restrict__ spans, int nspans,
-                   const RowPlan32* __restrict__ plans, unsigned* ctr, int eval_only) {
+                   RowPlan32* __restrict__ plans, unsigned* ctr, int eval_only, const BatchTile* __restrict__ ptiles,
+                   int nptiles, DevState* states, int n_inst) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PassSmem& w = reinterpret_cast<PassSmem*>(smem_raw)[warp];
   Cnt c{~0ull, 0ull, 0u};
   float4 nx[kPassVec];
+  bool go = true;
+  if constexpr (FUSED) {
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem_raw);   // the pass buffers are free until the rows
+    int cached = -1;
+    // a contiguous run of plan tiles per CTA (tiles are in instance order), so
+    // the instance's table is staged once or twice, not per tile
+    const int per = (nptiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t_end = min(nptiles, ((int)blockIdx.x + 1) * per);
+    for (int tile = (int)blockIdx.x * per; tile < t_end; ++tile) {
+      const BatchTile tl = ptiles[tile];
+      const BatchInst& I = insts[tl.inst];
+      const bool tab_smem = (I.xo == kNec) && I.g.nT <= kBatchTableCap;
+      if (tl.inst != cached) {                       // uniform over the CTA
+        __syncthreads();
+        if (tab_smem)
+          for (int k = threadIdx.x; k < I.g.nT; k += kPwThreads) tab[k] = I.g.nec_tm1[k];
+        __syncthreads();
+        cached = tl.inst;
+      }
+      // two rows per thread: both rows' draws, then both rows' gathers, so the
+      // loads of the two are in flight together
+      static_assert(kBatchThreadsHost == 2 * kPwThreads, "two plan rows per thread");
+      const long long gen = I.g.st->gen;
+      const int i0 = tl.row0 + threadIdx.x, i1 = i0 + kPwThreads;
+      RowDraws d0, d1;
+      int L0 = 0, L1 = 0;
+      if (i0 < I.g.N) row_draws(I, gen, i0, tab_smem ? tab : nullptr, d0, L0);
+      if (i1 < I.g.N) row_draws(I, gen, i1, tab_smem ? tab : nullptr, d1, L1);
+      if (i0 < I.g.N) {
+        const RowPlan32 a = row_plan(I.g, gen, i0, d0, L0);
+        if (i1 < I.g.N) {
+          const RowPlan32 b2 = row_plan(I.g, gen, i1, d1, L1);
+          plans[I.row_base + i1] = b2;
+        }
+        plans[I.row_base + i0] = a;
+      }
+    }
+    go = grid_barrier(&ctr[2], &ctr[3], gridDim.x);
+    if (!go && threadIdx.x == 0) atomicExch(&states[0].error, 4u);   // DE_ETIMEOUT
+  }
 
   // span s lives in span buffer s % 3: the current one, the next one (its
   // copies in flight, desc ns) and, being located, the one after (desc nd)
   unsigned q = 0u;
-  if (lane == 0) q = atomicAdd(&ctr[0], 1u);
+  if (lane == 0 && go) q = atomicAdd(&ctr[0], 1u);
   q = __shfl_sync(0xFFFFFFFFu, q, 0);
-  if (q < (unsigned)nspans) {
+  if (go && q < (unsigned)nspans) {
     const BatchSpan cs = spans[q];
     prefetch_span(w, 0, cs, insts, plans, eval_only, lane);
     unsigned q1 = 0u;
@@ -442,10 +521,18 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
     }
   }
   ca_wait_all();
+  unsigned done = 0u;
   if (lane == 0) {
     __threadfence();
-    const unsigned done = atomicAdd(&ctr[1], 1u);
-    if (done == gridDim.x * kPwWarps - 1u) {
+    done = atomicAdd(&ctr[1], 1u);
+  }
+  done = __shfl_sync(0xFFFFFFFFu, done, 0);
+  if (done == gridDim.x * kPwWarps - 1u) {           // the last warp of the launch
+    __threadfence();
+    if (FUSED && go)
+      for (int k = lane; k < n_inst; k += 32) close_instance(states[k], 0);
+    __syncwarp();
+    if (lane == 0) {
       ctr[0] = 0u;
       ctr[1] = 0u;
       __threadfence();
@@ -456,16 +543,24 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
 }  // namespace
 
 size_t batch_stage_smem() { return (size_t)kPwWarps * sizeof(PassSmem); }
+static_assert(kBatchTableCap * 4 <= kPwWarps * (int)sizeof(PassSmem), "NEC table fits the CTA's shared memory");
 
 int g_stage_ctas_per_sm = 2;                         // resident CTAs per SM (set once by prepare)
+int g_fused_ctas_per_sm = 0;
 
 cudaError_t prepare_batch_stage() {
-  cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)batch_stage_smem());
-  int n = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel, kPwThreads, batch_stage_smem());
+    e = cudaFuncSetAttribute(batch_stage_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_stage_smem());
+  int n = 0, m = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<false>, kPwThreads, batch_stage_smem());
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, batch_stage_kernel<true>, kPwThreads, batch_stage_smem());
   if (e == cudaSuccess && n > 0) g_stage_ctas_per_sm = n;
+  if (e == cudaSuccess) g_fused_ctas_per_sm = m;
   return e;
 }
 
@@ -474,8 +569,33 @@ cudaError_t prepare_batch_stage() {
 cudaError_t launch_batch_stage(const BatchInst* insts, const BatchSpan* spans, int nspans, const RowPlan32* plans,
                                unsigned* ctr, int eval_only, int grid, cudaStream_t s) {
   const int g = std::max(1, grid / 2) * g_stage_ctas_per_sm;
-  batch_stage_kernel<<<g, kPwThreads, batch_stage_smem(), s>>>(insts, spans, nspans, plans, ctr, eval_only);
+  batch_stage_kernel<false><<<g, kPwThreads, batch_stage_smem(), s>>>(
+      insts, spans, nspans, const_cast<RowPlan32*>(plans), ctr, eval_only, nullptr, 0, nullptr, 0);
   return cudaGetLastError();
+}
+
+bool batch_fused_supported() { return g_fused_ctas_per_sm > 0; }
+
+// One generation of every instance in one cooperative launch (all instances
+// on the staged kernel): plans, rows, close. ctr: 4 counters (queue, done,
+// barrier arrivals, barrier sense).
+cudaError_t launch_batch_fused(const BatchInst* insts, const BatchSpan* spans, int nspans, const BatchTile* ptiles,
+                               int nptiles, RowPlan32* plans, DevState* states, int n_inst, unsigned* ctr, int grid,
+                               cudaStream_t s) {
+  if (g_fused_ctas_per_sm <= 0) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(std::max(1, grid / 2) * g_fused_ctas_per_sm));
+  cfg.blockDim = dim3(kPwThreads);
+  cfg.dynamicSmemBytes = batch_stage_smem();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_stage_kernel<true>, insts, spans, nspans, plans, ctr, 0, ptiles, nptiles,
+                            states, n_inst);
 }
 
 }  // namespace de

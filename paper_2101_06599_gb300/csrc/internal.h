@@ -73,7 +73,7 @@ constexpr int kBatchMaxD4PerLane = 16;
 struct BatchWork {
   const BatchSpan* spans[4];   // register kernel for bin, exp, NEC; staged kernel (exp and NEC)
   int nspans[4];
-  unsigned* ctr;               // 8 counters
+  unsigned* ctr;               // 12 counters (2 per register list; 4 for the staged list)
   const BatchTile* ctiles;
   int nctiles;
 };
@@ -96,6 +96,12 @@ constexpr int kStageMaxD4 = 512;
 cudaError_t prepare_batch_stage();
 cudaError_t launch_batch_stage(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
                                cudaStream_t);
+// one generation of every instance in one cooperative launch when every
+// instance is on the staged kernel (plans, rows, close); ctr: 4 counters
+bool batch_fused_supported();
+cudaError_t launch_batch_fused(const BatchInst* insts, const BatchSpan* spans, int nspans, const BatchTile* ptiles,
+                               int nptiles, RowPlan32* plans, DevState* states, int n_inst, unsigned* ctr, int grid,
+                               cudaStream_t s);
 // the span row kernel alone, one per crossover (batch_span_*.cu)
 cudaError_t launch_batch_span_bin(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
                                   cudaStream_t);
