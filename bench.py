@@ -233,7 +233,9 @@ def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
     return {"workload": "batched_512_instances" if len(specs) == 512 else "batched_first_%d_instances" % len(specs),
             "instances": len(specs), "ind_dims_per_step": units,
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_gen": ms / steps,
-            "hbm_gbs": gbs, "frac": gbs / peak, "launches_per_step": 2 + len(kinds),
+            "hbm_gbs": gbs, "frac": gbs / peak,
+            # every instance on the staged kernel: one cooperative launch per generation
+            "launches_per_step": 1 if kinds == ["staged"] else 2 + len(kinds),
             "row_kernels": {kd: sum(1 for g in groups if ("staged" if g < 0 else ("register" if g <= 32 else "cta")) == kd)
                             for kd in kinds},
             "autotune_s": round(t_tune, 3),
