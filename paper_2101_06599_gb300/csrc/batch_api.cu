@@ -1,5 +1,6 @@
 // batch_api.cu — the batched part of the C ABI: many independent DE
-// instances advanced by one kernel launch per generation (batch_kernel.cu).
+// instances advanced together, one generation of all of them per step
+// (batch_kernel.cu, batch_stage.cu), and the autotuner of their row kernels.
 //
 // Device memory: one arena per context holding, per instance, two slot
 // buffers (N x pitch floats), fitness, slot bytes and NEC thresholds, plus

@@ -21,8 +21,10 @@
 //  3. batch_close_kernel: one thread per instance folds the generation into
 //     its best value / best generation and advances its generation counter.
 //
-// With eval_only, the row kernels evaluate the parents instead (initial
-// evaluation), so stored and trial fitness share one reduction order.
+// When every instance is on the staged kernel, the three steps run as one
+// cooperative launch instead (batch_stage.cu). With eval_only, the row
+// kernels evaluate the parents instead (initial evaluation), so stored and
+// trial fitness share one reduction order.
 #include <algorithm>
 
 #include "batch_plan.cuh"

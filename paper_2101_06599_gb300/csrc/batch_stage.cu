@@ -26,7 +26,11 @@
 // taken from a global queue). A span's plans and instance descriptor are
 // copied into one of three rotating shared buffers one span ahead, so no
 // global read sits between two passes; the generation parity comes with the
-// row plans.
+// row plans. The grid fills every SM with as many CTAs as fit (3 x 4 warps).
+//
+// The FUSED instantiation is a whole generation of every instance in one
+// cooperative launch: the row plans (as batch_plan_kernel), a bounded grid
+// barrier, the rows, and the close of every instance by the last warp.
 #include <algorithm>
 #include <cstring>
 
