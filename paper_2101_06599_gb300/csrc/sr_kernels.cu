@@ -324,14 +324,17 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 // transposed copy (contiguous 64-column rows of R^T); each stage's a = x - o
 // is formed in shared memory in K-major order before use. A fixed grid walks
 // the entry tiles, so a short list still spreads over the SMs.
-constexpr int kLsN = 64, kLsK = 32, kLsStages = 4, kLsThreads = 128;
+constexpr int kLsN = 64, kLsK = 32, kLsStages = 4;
 constexpr int kSrListRows = 16;                  // entries per tile of the list product (8 measured slower)
+constexpr int kSrListThreads = 128;              // two entries x 4 columns per thread (256 threads, one entry each: slower)
 constexpr int kLsLdA = kLsK + 4, kLsLdB = kLsN + 4;
 
-// kLsM entries per tile (8 or 16): RPT = kLsM / 8 entries per thread.
-template <bool VEC, int kLsM>
+// kLsM entries per tile, kLsThreads threads: 16 column groups x kLsThreads / 16
+// row groups, RPT = kLsM * 16 / kLsThreads entries per thread.
+template <bool VEC, int kLsM, int kLsThreads>
 __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
-  constexpr int RPT = kLsM / 8;
+  constexpr int RPT = kLsM * 16 / kLsThreads;
+  static_assert(RPT == 1 || RPT == 2, "one or two entries per thread");
   constexpr int kLsLdT = kLsM + 4;
   const GenParams& p = sp.g;
   __shared__ __align__(16) float Araw[kLsStages][kLsM][kLsLdA];
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
   __shared__ __align__(16) float Bsh[kLsStages][kLsK][kLsLdB];
   __shared__ __align__(16) float At[kLsK][kLsLdT];
   __shared__ const float* rowp[kLsM];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // ty: 0..7, rows RPT ty .. RPT ty + RPT - 1
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // rows RPT ty .. RPT ty + RPT - 1
   const int n0 = blockIdx.x * kLsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
@@ -611,11 +614,11 @@ cudaError_t launch_sr_trial(int xo, int /*vidx*/, const SrParams& sp, int /*bloc
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
   const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
   if (mode == 2) {
-    constexpr int M = kSrListRows;
+    constexpr int M = kSrListRows, T = kSrListThreads;
     const int tiles = (max_rows + M - 1) / M;
     const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 128)));
-    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true, M><<<grid, kLsThreads, 0, s>>>(sp);
-    else sr_gemm_fp32_list_kernel<false, M><<<grid, kLsThreads, 0, s>>>(sp);
+    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true, M, T><<<grid, T, 0, s>>>(sp);
+    else sr_gemm_fp32_list_kernel<false, M, T><<<grid, T, 0, s>>>(sp);
     return cudaGetLastError();
   }
   const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
