@@ -274,3 +274,34 @@ def test_batch_autotune_keeps_state_and_results():
     finally:
         a.close()
         b.close()
+
+
+def test_batch_one_launch_generation_matches_the_three_launch_path():
+    """A batch whose instances are all on the staged kernel runs each
+    generation as one cooperative launch (plans, grid barrier, rows, close).
+    Moving one instance to the register kernel switches the batch to the
+    plan / rows / close launches; both paths sum fitness in one order, so the
+    trajectories are bit-identical, and the one-launch path matches the
+    oracle for a generation."""
+    specs = []
+    for k, (D, xo) in enumerate([(10, "nec"), (100, "exp"), (600, "nec"), (2000, "nec"), (33, "exp"), (1024, "nec")]):
+        obj = OBJS[k % 4]
+        specs.append(dict(N=50 + 7 * k, D=D, obj=obj, bounds=W.BOXES[obj], xo=xo, CR=0.9, F=0.5))
+    a = DE.Batch(specs, seed=9)
+    b = DE.Batch(specs, seed=9)
+    try:
+        assert all(g < 0 for g in a.groups())            # every instance staged: one launch per generation
+        b.set_groups([min_group(specs[0]["D"])] + [0] * (len(specs) - 1))
+        a.run(6)
+        b.run(6)
+        for k in range(len(specs)):
+            pa, fa = a.population(k)
+            pb, fb = b.population(k)
+            assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32)), k
+            assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32)), k
+            assert a.stats(k) == b.stats(k), k
+        for k in (0, 3, 4):
+            check_instance_step(a, k, specs[k], 9)
+    finally:
+        a.close()
+        b.close()
