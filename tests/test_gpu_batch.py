@@ -305,3 +305,34 @@ def test_batch_one_launch_generation_matches_the_three_launch_path():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("CR", [0.0, 1.0, 0.99])
+def test_batch_staged_edge_cases(CR):
+    """Staged-kernel edge cases against the oracle, one generation each: Cr = 0
+    (L = 1) and Cr = 1 (L = D), Cr = 0.99 (segments longer than the shared
+    donor area read their donors from global memory), the minimum N = 4, and
+    rows of exactly 512 float4 slots (D = 2048: one row per pass) next to
+    D = 2049 (over the limit: register tiles in the same batch)."""
+    specs = []
+    for k, (N, D, xo) in enumerate([(4, 2048, "nec"), (9, 2047, "exp"), (40, 3, "nec"), (23, 2049, "nec"),
+                                    (64, 777, "exp"), (5, 1, "nec")]):
+        obj = OBJS[k % 4]
+        specs.append(dict(N=N, D=D, obj=obj, bounds=W.BOXES[obj], xo=xo, CR=CR, F=0.7))
+    b = DE.Batch(specs, seed=13)
+    try:
+        g = b.groups()
+        assert g[3] > 0 and all(v < 0 for i, v in enumerate(g) if i != 3)
+        b.run(2)
+        for k in range(len(specs)):
+            check_instance_step(b, k, specs[k], 13)
+        # the same batch with every instance staged except the one that cannot be
+        only_staged = [s for s in specs if s["D"] <= 2048]
+        c = DE.Batch(only_staged, seed=13)
+        try:
+            for k in range(len(only_staged)):
+                check_instance_step(c, k, only_staged[k], 13)
+        finally:
+            c.close()
+    finally:
+        b.close()
