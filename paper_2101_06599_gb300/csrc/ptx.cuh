@@ -90,25 +90,6 @@ __device__ __forceinline__ float4 ld_shared_v4(const float* p) {
   return *reinterpret_cast<const float4*>(p);
 }
 
-}  // namespace de
-
-namespace de {
-
-// Bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned) from
-// this CTA's shared memory to global memory, in the issuing thread's current
-// bulk group.
-__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Every bulk group of this thread has finished reading its shared memory.
-__device__ __forceinline__ void bulk_wait_read_all() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-// Every bulk group of this thread has completed.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
 // 16-byte asynchronous copy global -> shared (cp.async, L2 only), committed
 // and awaited as one group per thread.
 __device__ __forceinline__ void ca16_g2s(uint32_t dst, const void* src) {
