@@ -138,3 +138,13 @@ def test_create_without_a_device_fails_cleanly(lib):
     with pytest.raises(DE.DEError) as e:
         DE.de_batch_create(specs, 1)
     assert e.value.code in (DE.DE_ENOMEM, DE.DE_ECUDA)
+
+
+def test_best_record_size_matches_the_header():
+    """de_best_async records: the header's size macro and the binding agree."""
+    text = open(os.path.join(ROOT, "include", "de.h")).read()
+    m = re.search(r"#define DE_BEST_RECORD_BYTES\(D\) \((\d+) \+ (\d+) \* \(size_t\)\(D\)\)", text)
+    assert m, "DE_BEST_RECORD_BYTES not found"
+    head, per = int(m.group(1)), int(m.group(2))
+    for D in (1, 7, 1000):
+        assert DE.best_record_bytes(D) == head + per * D
