@@ -231,11 +231,15 @@ typedef struct {
  * 2^24); instance k draws from Philox instance field k, so instance k of a
  * batch reproduces a single population whose draws use instance field k.
  * Each instance keeps its own population, fitness, counters and best. One
- * de_step / de_run step advances every instance by one generation in a few
- * launches over all instances (draws, rows, close): the rows of each
- * instance are cut into spans of up to 32 rows (taken by warps from a queue)
- * or, for D > 2048, into tiles of 256 / G rows; the row kernel of each
- * instance is set by de_batch_set_groups. Per-instance limits as de_create
+ * de_step / de_run step advances every instance by one generation: one
+ * cooperative kernel launch (draws, rows, close) when every instance is on
+ * the staged kernel (the default for exp / NEC rows of D <= 2048), else a
+ * few launches over all instances (draws, row kernels, close). The rows of
+ * each instance are cut into spans of up to 32 rows (taken by warps from a
+ * queue) or, for D > 2048, into tiles of 256 / G rows; the row kernel of
+ * each instance is set by de_batch_set_groups or de_batch_autotune. A device
+ * wait that gives up (1 s) is reported as DE_ETIMEOUT by the next
+ * synchronising call. Per-instance limits as de_create
  * with D <= 16384 and non-rotated objectives (Ackley constant 0.2). The
  * initial populations are drawn and evaluated before the call returns.
  * Single-population calls (de_best, de_get_population, de_set_population,
@@ -293,9 +297,8 @@ int de_batch_get_groups(de_ctx *ctx, int32_t *groups);
  * the row kernels of one generation of every instance, the other groups as
  * they stand, so that kernels which slow each other down when they run
  * together (instruction cache, occupancy) are judged together; the fastest
- * is kept. The trials reuse the draws
- * of the current generation and leave populations, fitness, counters and the
- * generation as they were, and the choice changes no result (every
+ * is kept. The trials reuse the draws of the current generation and leave
+ * populations, fitness, counters and the generation as they were, and the choice changes no result (every
  * candidate sums the fitness in one order). Synchronises; drops captured
  * graphs. groups_out (n_inst values, may be NULL) receives the choice as
  * de_batch_get_groups reports it. DE_ESTATE on a single population. */
