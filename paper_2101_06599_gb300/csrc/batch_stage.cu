@@ -549,8 +549,10 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
 size_t batch_stage_smem() { return (size_t)kPwWarps * sizeof(PassSmem); }
 static_assert(kBatchTableCap * 4 <= kPwWarps * (int)sizeof(PassSmem), "NEC table fits the CTA's shared memory");
 
-int g_stage_ctas_per_sm = 2;                         // resident CTAs per SM (set once by prepare)
-int g_fused_ctas_per_sm = 0;
+// resident CTAs per SM of the two instantiations (set by prepare_batch_stage,
+// the same value on every call for one device type)
+static int g_stage_ctas_per_sm = 2;
+static int g_fused_ctas_per_sm = 0;
 
 cudaError_t prepare_batch_stage() {
   cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
