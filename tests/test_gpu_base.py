@@ -123,7 +123,7 @@ def test_base_rules_batched():
                 bt.set_population(k, pop)
                 fit64 = O.evaluate(sp["obj"], pop)
                 st = bt.stats(k)
-                g, best = st["generation"], int(np.argmin(bt.population(k)[1]))
+                g, best = st["generation"], O.argmin(bt.population(k)[1])
                 trial, ft, acc, draws = bt.debug_step(k)
                 s = O.step(pop, fit64, sp["F"], sp["CR"], sp["xo"], sp["obj"], lo, hi, 7, g, inst=k, base=base,
                            best=best)

@@ -75,7 +75,7 @@ def test_batch_init_parity():
             f64 = O.evaluate(sp["obj"], ref)
             assert np.all(np.abs(fit - f64) <= tol(f64)), k
             x, f, idx, bg = b.best(k)
-            assert idx == int(np.argmin(fit)) and f == fit[idx] and bg == 0 and np.array_equal(x, pop[idx])
+            assert idx == O.argmin(fit) and f == fit[idx] and bg == 0 and np.array_equal(x, pop[idx])
     finally:
         b.close()
 
@@ -142,7 +142,7 @@ def test_batch_run_graph_stats_and_best():
             tot_acc += sk["accepts"]
             tot_msk += sk["masked_genes"]
             x, f, idx, bg = b.best(k)
-            assert idx == int(np.argmin(fb)) and f == fb[idx] and np.array_equal(x, pb[idx])
+            assert idx == O.argmin(fb) and f == fb[idx] and np.array_equal(x, pb[idx])
             assert f <= sk["best_f"] + 0.0 and 0 <= bg <= 7
             best = min(best, f)
         st = b.stats()

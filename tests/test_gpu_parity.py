@@ -91,7 +91,7 @@ def test_init_parity(N, D):
             assert np.array_equal(pop.view(np.uint32), ref.view(np.uint32))
             check_fitness(fit, O.evaluate(obj, ref), "initial fitness")
             x, f, idx, bg = opt.best()
-            assert idx == int(np.argmin(fit)) and f == fit[idx] and bg == 0
+            assert idx == O.argmin(fit) and f == fit[idx] and bg == 0
             assert np.array_equal(x, pop[idx])
         finally:
             opt.close()
@@ -173,7 +173,7 @@ def test_run_graph_matches_steps_and_stats():
         assert sa["accepts"] == sb["accepts"] == acc_total
         assert sa["masked_genes"] == sb["masked_genes"] == masked_total
         x, f, idx, bg = b.best()
-        assert idx == int(np.argmin(fb)) and f == fb[idx] and np.array_equal(x, pb[idx])
+        assert idx == O.argmin(fb) and f == fb[idx] and np.array_equal(x, pb[idx])
         assert 0 <= bg <= 12 and sb["best_gen"] == bg
     finally:
         a.close()
