@@ -25,6 +25,12 @@
  *    default stream). de_step/de_run only enqueue; errors raised by queued
  *    work surface at the next call that synchronises (de_best, de_stats,
  *    de_get_population, de_save, de_synchronize) as DE_ECUDA.
+ *  - Every wait inside a kernel is bounded. A wait that gives up records
+ *    DE_ETIMEOUT in the context's device state; de_synchronize, de_stats and
+ *    de_best (and their batched forms) report it. From the first call that
+ *    reports a device error on, the context refuses to launch generations:
+ *    de_step, de_run and the debug steps return DE_ESTATE. Populations can
+ *    still be read; de_destroy releases the context as usual.
  *  - A context is not thread-safe; use one host thread per context.
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key (seed low
@@ -159,8 +165,22 @@ int de_step(de_ctx *ctx);
  * once per distinct count into a CUDA graph and replayed. */
 int de_run(de_ctx *ctx, int32_t generations);
 
-/* Block until the context's stream is idle; DE_ECUDA if queued work failed. */
+/* Block until the context's stream is idle; DE_ECUDA if queued work failed,
+ * the device error code (DE_ETIMEOUT) if a kernel recorded one. */
 int de_synchronize(de_ctx *ctx);
+
+/* Limit, in nanoseconds of the GPU's global timer, of the device waits that
+ * guard no copy or tensor-core operation in flight: the grid barrier of the
+ * batched one-launch generation between its row plans and its rows. ns = 0
+ * restores the default (1 s); DE_EINVAL for ns < 0. A CTA whose barrier wait
+ * gives up records DE_ETIMEOUT and takes no rows; the CTAs the barrier
+ * released process every row between them, so the generation is still
+ * complete and identical to one without the timeout. The waits of the
+ * pipelined and tensor-core kernels, which guard bulk copies and MMAs in
+ * flight, keep their fixed 1 s limit. de_get_wait_limit reports the limit
+ * in force. Drops the context's captured graphs. */
+int de_set_wait_limit(de_ctx *ctx, int64_t ns);
+int de_get_wait_limit(de_ctx *ctx, int64_t *ns);
 
 /* ---- results ----------------------------------------------------------- */
 /* Best individual so far (synchronises). Any output pointer may be NULL.
@@ -215,6 +235,25 @@ int de_load(de_ctx *ctx, const void *buf, size_t len);
  * mask popcount for bin). Any output may be NULL. Synchronises. */
 int de_debug_step(de_ctx *ctx, float *trial_out, float *ftrial_out,
                   uint8_t *accept_out, int32_t *draws_out);
+
+/* Test hook for the draws of Eq. (9) and Alg. 8 at given random words.
+ * For each of the n words w[k] (host array; w / 2^32 is the uniform U of the
+ * row), with the Cr, D and NEC threshold table of the context (instance
+ * `inst` of a batch; 0 for a single population):
+ *   L_global[k]  NEC's segment length L = min(ceil(ln U / ln Cr), D), Eq. (9)
+ *                read exactly as L = smallest n >= 1 with Cr^n <= U (Cr^n the
+ *                FP64 product Cr * Cr * ... rounded at each step), capped at D;
+ *                U = 0 gives D, Cr = 0 gives 1, Cr = 1 gives D. Computed by the
+ *                lookup the generation kernels use, on the table in global memory;
+ *   L_shared[k]  the same through the copy of the table in shared memory that
+ *                the pipelined kernel and the batched plans use (when the
+ *                table has at most 4096 entries; else as L_global, as those
+ *                kernels then do);
+ *   exp_continue[k]  1 iff Alg. 8's walk continues on this word: U < Cr.
+ * Outputs are host arrays of n elements; any may be NULL. Synchronises.
+ * DE_EINVAL for n < 0, a NULL `words` with n > 0 or an invalid `inst`. */
+int de_debug_lengths(de_ctx *ctx, int32_t inst, const uint32_t *words, int32_t n,
+                     int32_t *L_global, int32_t *L_shared, uint8_t *exp_continue);
 
 /* ---- batched instances --------------------------------------------------- */
 /* One independent DE problem of a batch. */
@@ -387,15 +426,23 @@ int de_get_pipeline(de_ctx *ctx, int32_t *consumer_threads, int32_t *stages, int
  *   fit_in, fit_out: device, N floats (distinct buffers).
  *   Row i of pop_out / fit_out receives the trial and its FP32 fitness if the
  *   trial is strictly better than fit_in[i], else a copy of the parent row and
- *   fit_in[i]. Draws come from Philox with (seed, generation): the result
- *   equals what de_step computes at that generation from the same population.
+ *   fit_in[i]. Draws come from Philox with (seed, generation), as de_step's at
+ *   that generation. For D < 2048 the call runs the kernel de_step runs, so
+ *   pop_out and fit_out are bit-identical to what de_step computes from the
+ *   same population; for D >= 2048 de_step's pipelined kernel sums the FP32
+ *   fitness in another order, so fitness values may differ in the last bits
+ *   (within 1e-5 max(1, |f|)) and a selection whose two values lie that
+ *   close may differ; the trials themselves are identical.
  *   Objectives: sphere .. elliptic (Ackley constant 0.2); bounds as de_create.
  * Limits: 4 <= N <= 65536, 1 <= D <= 32768; larger sizes return DE_EINVAL.
  * Work is queued on `cuda_stream`. The first call on a device looks up the
  * scratch array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture. Every call reuses
- * the same scratch and clears what must start at zero; calls that overlap on
- * the GPU (different streams or host threads) race on it. */
+ * the same scratch and clears what must start at zero. The NEC thresholds are
+ * rebuilt only when (Cr, D) differ from the previous call's on the device:
+ * up to D - 1 dependent FP64 products on one GPU thread, the one call that
+ * pays it being slower. Calls that overlap on the GPU (different streams or
+ * host threads) race on the scratch and must be serialised by the caller. */
 int de_nec_step_noalloc(const float *pop_in, const float *fit_in, float *pop_out, float *fit_out,
                         int32_t N, int32_t D, int32_t pitch, float F, double CR, de_objective obj,
                         de_bounds b, uint64_t seed, int64_t generation, void *cuda_stream);

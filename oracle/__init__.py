@@ -62,6 +62,8 @@ def lib():
         L.or_donors.restype = None
         L.or_nec_length.argtypes = [C.c_uint32, C.c_double, C.c_int32]
         L.or_nec_length.restype = C.c_int32
+        L.or_exp_continues.argtypes = [C.c_uint32, C.c_double]
+        L.or_exp_continues.restype = C.c_int
         L.or_exp_length.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_int32, C.c_double, C.c_int32]
         L.or_exp_length.restype = C.c_int32
         L.or_mask.argtypes = [C.c_int32, C.c_double, C.c_int, C.c_uint64, C.c_uint32, C.c_int64,
@@ -145,6 +147,11 @@ def base_perm(N, seed, g, i, inst=0):
 
 def nec_length(w, Cr, D):
     return int(lib().or_nec_length(int(w) & 0xFFFFFFFF, float(Cr), int(D)))
+
+
+def exp_continues(w, Cr):
+    """Alg. 8's continuation test for one word: w / 2^32 < Cr."""
+    return bool(lib().or_exp_continues(int(w) & 0xFFFFFFFF, float(Cr)))
 
 
 def exp_length(seed, g, i, Cr, D, inst=0):

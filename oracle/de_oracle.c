@@ -230,6 +230,13 @@ int32_t or_nec_length(uint32_t w, double Cr, int32_t D)
   return n;
 }
 
+/* Alg. 8's test after each copied gene: continue iff rand < Cr, with
+ * rand = w / 2^32 compared with Cr in FP64 (both exact). */
+int or_exp_continues(uint32_t w, double Cr)
+{
+  return unit_from_word(w) < Cr;
+}
+
 /* Alg. 8: copy one gene, then keep copying while rand < Cr and L < D. The
  * k-th draw (k = 1, 2, ...) is word k-1 of stream EXP for this row. Only the
  * number of copied genes is returned; the genes are j_rand, j_rand+1, ...
@@ -242,9 +249,9 @@ int32_t or_exp_length(uint64_t seed, uint32_t inst, int64_t g, int32_t i,
   int again;
   do {
     L = L + 1;                   /* u_j <- v_j ; j <- (j+1) mod D ; L++ */
-    double rnd = unit_from_word(or_word(seed, inst, OR_STREAM_EXP, g, i, k));
+    uint32_t w = or_word(seed, inst, OR_STREAM_EXP, g, i, k);
     k++;
-    again = (rnd < Cr) && (L < D);
+    again = or_exp_continues(w, Cr) && (L < D);
   } while (again);
   return L;
 }

@@ -78,6 +78,9 @@ int32_t or_base_perm(int32_t N, uint64_t seed, uint32_t inst, int64_t g, int32_t
 /* Eq. (9) for one uniform word w (U = w / 2^32). */
 int32_t or_nec_length(uint32_t w, double Cr, int32_t D);
 
+/* Alg. 8's continuation test on one word: 1 iff w / 2^32 < Cr. */
+int or_exp_continues(uint32_t w, double Cr);
+
 /* Alg. 8: number of genes the classic exponential crossover copies for row i. */
 int32_t or_exp_length(uint64_t seed, uint32_t inst, int64_t g, int32_t i,
                       double Cr, int32_t D);

@@ -92,6 +92,12 @@ std::vector<uint32_t> nec_thresholds(double CR, int D) {
   return tm1;
 }
 
+// The NEC lookup's first-guess factor 1 / -log2(Cr) (0 outside 0 < Cr < 1,
+// where the table is not used).
+float nec_guess_factor(double CR) {
+  return (CR > 0.0 && CR < 1.0) ? (float)(1.0 / -std::log2(CR)) : 0.0f;
+}
+
 bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de_bounds b) {
   if (N < 4 || N > (1 << 29) || D < 1 || D > 32768) return false;
   if ((long long)N * (long long)D >= (1LL << 40)) return false;
@@ -184,6 +190,11 @@ int evaluate_population(de_ctx* c) {
   if (e == cudaSuccess) e = launch_eval(c->obj, c->vidx, c->p, c->block, c->stream);
   if (e == cudaSuccess) e = launch_close_eval(c->p, c->stream);
   return cuda_status(e);
+}
+
+int note_device_error(de_ctx* c, int err) {
+  if (err != DE_OK && !c->failed) c->failed = err;
+  return err;
 }
 
 int sync_stream(de_ctx* c) {
@@ -319,6 +330,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   p.inst = 0;
   p.ackley_b = (float)ackley_b;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
+  p.nec_k = nec_guess_factor(CR);
 
   c->rotated = is_rotated(obj);
   int dev = 0;
@@ -363,6 +375,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
 
 int de_step(de_ctx* c) {
   if (!c) return DE_EINVAL;
+  if (c->failed) return DE_ESTATE;
   const int rc = cuda_status(launch_generation(c, c->p));
   if (rc == DE_OK) c->host_gen++;
   return rc;
@@ -370,6 +383,7 @@ int de_step(de_ctx* c) {
 
 int de_run(de_ctx* c, int32_t generations) {
   if (!c || generations < 0) return DE_EINVAL;
+  if (c->failed) return DE_ESTATE;
   if (generations == 0) return DE_OK;
   if (generations == 1 || c->stream == nullptr) {
     for (int32_t k = 0; k < generations; ++k) {
@@ -405,7 +419,7 @@ int de_run(de_ctx* c, int32_t generations) {
 
 int de_synchronize(de_ctx* c) {
   if (!c) return DE_EINVAL;
-  if (c->batch) return sync_stream(c);
+  if (c->batch) return batch_device_error(c);
   if (cudaMemcpyAsync(c->host_pinned, &c->p.st->error, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream) !=
       cudaSuccess)
     return DE_ECUDA;
@@ -413,7 +427,7 @@ int de_synchronize(de_ctx* c) {
   if (rc != DE_OK) return rc;
   unsigned err;
   std::memcpy(&err, c->host_pinned, sizeof(err));
-  return err ? (int)err : DE_OK;
+  return note_device_error(c, (int)err);
 }
 
 int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* best_gen_out) {
@@ -429,7 +443,7 @@ int de_best(de_ctx* c, float* x_out, double* f_out, int32_t* idx_out, int64_t* b
   const unsigned char* h = static_cast<const unsigned char*>(c->host_pinned);
   int derr = 0;
   std::memcpy(&derr, h + 20, sizeof(int));
-  if (derr) return derr;
+  if (derr) return note_device_error(c, derr);
   if (f_out) std::memcpy(f_out, h, sizeof(double));
   if (best_gen_out) std::memcpy(best_gen_out, h + 8, sizeof(int64_t));
   if (idx_out) std::memcpy(idx_out, h + 16, sizeof(int32_t));
@@ -466,7 +480,7 @@ int de_stats(de_ctx* c, de_stats_t* out) {
   if (rc != DE_OK) return rc;
   DevState s;
   std::memcpy(&s, c->host_pinned, sizeof(s));
-  if (s.error) return (int)s.error;
+  if (s.error) return note_device_error(c, (int)s.error);
   out->generation = s.gen;
   out->accepts = s.accepts;
   out->masked_genes = s.masked;
@@ -593,6 +607,7 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
 
 int de_debug_step(de_ctx* c, float* trial_out, float* ftrial_out, uint8_t* accept_out, int32_t* draws_out) {
   if (!c) return DE_EINVAL;
+  if (c->failed) return DE_ESTATE;
   if (c->batch) return DE_ESTATE;
   GenParams p = c->p;
   float* dtrial = trial_out ? (float*)ctx_alloc(c, (size_t)c->N * c->pitch * sizeof(float)) : nullptr;
@@ -626,6 +641,49 @@ int de_debug_step(de_ctx* c, float* trial_out, float* ftrial_out, uint8_t* accep
   if (dacc) ctx_free(c, dacc);
   if (ddr) ctx_free(c, ddr);
   return rc;
+}
+
+int de_debug_lengths(de_ctx* c, int32_t inst, const uint32_t* words, int32_t n, int32_t* L_global,
+                     int32_t* L_shared, uint8_t* exp_continue) {
+  if (!c || n < 0 || (n > 0 && !words)) return DE_EINVAL;
+  if (c->batch ? (inst < 0 || inst >= c->n_inst) : inst != 0) return DE_EINVAL;
+  if (n == 0) return DE_OK;
+  const GenParams& p = c->batch ? c->bp[inst] : c->p;
+  uint32_t* dw = (uint32_t*)ctx_alloc(c, (size_t)n * sizeof(uint32_t));
+  int* dg = L_global ? (int*)ctx_alloc(c, (size_t)n * sizeof(int)) : nullptr;
+  int* ds = L_shared ? (int*)ctx_alloc(c, (size_t)n * sizeof(int)) : nullptr;
+  uint8_t* de = exp_continue ? (uint8_t*)ctx_alloc(c, (size_t)n) : nullptr;
+  int rc = DE_OK;
+  if (!dw || (L_global && !dg) || (L_shared && !ds) || (exp_continue && !de)) rc = DE_ENOMEM;
+  cudaError_t e = cudaSuccess;
+  if (rc == DE_OK) e = cudaMemcpyAsync(dw, words, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream);
+  if (rc == DE_OK && e == cudaSuccess) e = launch_debug_lengths(p, dw, n, dg, ds, de, c->stream);
+  if (rc == DE_OK && e == cudaSuccess && L_global)
+    e = cudaMemcpyAsync(L_global, dg, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK && e == cudaSuccess && L_shared)
+    e = cudaMemcpyAsync(L_shared, ds, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK && e == cudaSuccess && exp_continue)
+    e = cudaMemcpyAsync(exp_continue, de, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == DE_OK) rc = (e == cudaSuccess) ? sync_stream(c) : DE_ECUDA;
+  else cudaStreamSynchronize(c->stream);
+  if (dw) ctx_free(c, dw);
+  if (dg) ctx_free(c, dg);
+  if (ds) ctx_free(c, ds);
+  if (de) ctx_free(c, de);
+  return rc;
+}
+
+int de_set_wait_limit(de_ctx* c, int64_t ns) {
+  if (!c || ns < 0) return DE_EINVAL;
+  c->wait_ns = (unsigned long long)ns;
+  drop_graphs(c);
+  return DE_OK;
+}
+
+int de_get_wait_limit(de_ctx* c, int64_t* ns) {
+  if (!c || !ns) return DE_EINVAL;
+  *ns = c->wait_ns ? (int64_t)c->wait_ns : (int64_t)kWaitLimitNs;
+  return DE_OK;
 }
 
 int de_set_launch(de_ctx* c, int32_t threads, int32_t vec4) {

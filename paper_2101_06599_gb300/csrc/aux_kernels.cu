@@ -1,9 +1,41 @@
 // aux_kernels.cu — initial population, whole-population evaluation, best
 // tracking helpers and slot normalisation.
+#include <algorithm>
+
 #include "gen_kernel.cuh"
 #include "internal.h"
 
 namespace de {
+
+// Test hook: Eq. (9)'s L and Alg. 8's continuation test for caller-given
+// words, through the device functions the generation kernels use: the NEC
+// lookup on the table in global memory (row-per-CTA and streaming kernels)
+// and on the table staged in shared memory (pipelined kernel, batched plans),
+// when it fits kDebugTableCap entries, else through global memory as those
+// kernels then do.
+constexpr int kDebugTableCap = 4096;
+
+__global__ void debug_lengths_kernel(const __grid_constant__ GenParams p, const uint32_t* __restrict__ words, int n,
+                                     int* L_global, int* L_shared, uint8_t* exp_cont) {
+  __shared__ uint32_t tab[kDebugTableCap];
+  const bool staged = p.nT <= kDebugTableCap;
+  if (staged)
+    for (int k = threadIdx.x; k < p.nT; k += blockDim.x) tab[k] = p.nec_tm1[k];
+  __syncthreads();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t w = words[k];
+    if (L_global) L_global[k] = nec_length_of<false>(p, w, p.nec_tm1);
+    if (L_shared) L_shared[k] = staged ? nec_length_of<true>(p, w, tab) : nec_length_of<false>(p, w, p.nec_tm1);
+    if (exp_cont) exp_cont[k] = exp_continues(p, w) ? 1 : 0;
+  }
+}
+
+cudaError_t launch_debug_lengths(const GenParams& p, const uint32_t* words, int n, int* L_global, int* L_shared,
+                                 uint8_t* exp_cont, cudaStream_t s) {
+  const int grid = std::max(1, std::min(1024, (n + 255) / 256));
+  debug_lengths_kernel<<<grid, 256, 0, s>>>(p, words, n, L_global, L_shared, exp_cont);
+  return cudaGetLastError();
+}
 
 // Alg. 2, first lines: x_ij = clip(lo + (hi - lo) * u_ij), u_ij = (w >> 8) 2^-24,
 // with w = word j of the row's INIT stream; each operation rounded once.

@@ -150,6 +150,7 @@ static BatchWork batch_work(const de_ctx* c, int inst) {
   BatchWork w;
   std::memset(&w, 0, sizeof(w));
   w.ctr = c->d_span_ctr;
+  w.wait_ns = c->wait_ns;
   if (inst < 0) {
     for (int x = 0; x < 4; ++x) {
       w.spans[x] = c->d_spans[x];
@@ -202,6 +203,18 @@ int batch_set_base(de_ctx* c, int base) {
   return upload_insts(c);
 }
 
+int batch_device_error(de_ctx* c) {
+  std::vector<DevState> h((size_t)c->n_inst);
+  if (cudaMemcpyAsync(h.data(), c->d_states, h.size() * sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return DE_ECUDA;
+  const int rc = sync_stream(c);
+  if (rc != DE_OK) return rc;
+  for (int k = 0; k < c->n_inst; ++k)
+    if (h[k].error) return note_device_error(c, (int)h[k].error);
+  return DE_OK;
+}
+
 int batch_stats(de_ctx* c, de_stats_t* out) {
   std::vector<DevState> h((size_t)c->n_inst);
   if (cudaMemcpyAsync(h.data(), c->d_states, h.size() * sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=
@@ -215,7 +228,7 @@ int batch_stats(de_ctx* c, de_stats_t* out) {
   out->incumbent_gen = -1;
   out->generation = h.empty() ? 0 : h[0].gen;
   for (int k = 0; k < c->n_inst; ++k) {
-    if (h[k].error) return (int)h[k].error;
+    if (h[k].error) return note_device_error(c, (int)h[k].error);
     out->accepts += h[k].accepts;
     out->masked_genes += h[k].masked;
     out->reselected += h[k].reselected;
@@ -333,6 +346,7 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
     p.inst = (uint32_t)k;
     p.ackley_b = 0.2f;
     p.ell_k = (s.D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(s.D - 1)) : 0.0f;
+    p.nec_k = nec_guess_factor(s.CR);
     c->bobj[k] = (int)s.obj;
     c->bxo[k] = (int)s.xo;
     c->bgroup[k] = default_group(p.D4, (int)s.xo);
@@ -380,7 +394,7 @@ int de_batch_best(de_ctx* c, int32_t inst, float* x_out, double* f_out, int32_t*
   const unsigned char* h = static_cast<const unsigned char*>(c->host_pinned);
   int derr = 0;
   std::memcpy(&derr, h + 20, sizeof(int));
-  if (derr) return derr;
+  if (derr) return note_device_error(c, derr);
   if (f_out) std::memcpy(f_out, h, sizeof(double));
   if (best_gen_out) std::memcpy(best_gen_out, h + 8, sizeof(int64_t));
   if (idx_out) std::memcpy(idx_out, h + 16, sizeof(int32_t));
@@ -399,7 +413,7 @@ int de_batch_stats(de_ctx* c, int32_t inst, de_stats_t* out) {
   const int rc = sync_stream(c);
   if (rc != DE_OK) return rc;
   std::memcpy(&s, c->host_pinned, sizeof(s));
-  if (s.error) return (int)s.error;
+  if (s.error) return note_device_error(c, (int)s.error);
   out->generation = s.gen;
   out->accepts = s.accepts;
   out->masked_genes = s.masked;
@@ -454,7 +468,7 @@ int de_batch_set_population(de_ctx* c, int32_t inst, const float* pop, const flo
 int de_batch_debug_step(de_ctx* c, int32_t inst, float* trial_out, float* ftrial_out, uint8_t* accept_out,
                         int32_t* draws_out) {
   if (!c) return DE_EINVAL;
-  if (!c->batch) return DE_ESTATE;
+  if (!c->batch || c->failed) return DE_ESTATE;
   if (inst < 0 || inst >= c->n_inst) return DE_EINVAL;
   const GenParams& p0 = c->bp[inst];
   BatchInst bi = make_inst(c, inst);
@@ -528,7 +542,7 @@ int de_batch_get_groups(de_ctx* c, int32_t* groups) {
 
 int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
   if (!c) return DE_EINVAL;
-  if (!c->batch) return DE_ESTATE;
+  if (!c->batch || c->failed) return DE_ESTATE;
   if (reps < 1 || reps > 1000) return DE_EINVAL;
   int rc = sync_stream(c);
   if (rc != DE_OK) return rc;

@@ -375,7 +375,7 @@ cudaError_t launch_batch_generation(const BatchInst* insts, const BatchWork& w, 
   if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nspans[3] + w.nctiles <= 0) return cudaSuccess;
   if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nctiles == 0 && batch_fused_supported())
     return launch_batch_fused(insts, w.spans[3], w.nspans[3], ptiles, nptiles, plans, states, n_inst, w.ctr + 6,
-                              grid, s);
+                              grid, w.wait_ns, s);
   batch_plan_kernel<<<plan_grid(nptiles, grid), kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
   cudaError_t e = launch_spans(insts, w, plans, 0, grid, s);
   if (e != cudaSuccess) return e;

@@ -19,21 +19,11 @@ __device__ __forceinline__ void row_draws(const BatchInst& I, long long gen, int
   draw_donors(p, g, i, d);
   int L = 0;
   if (I.xo == kNec) {
-    if (p.cr_mode == kCrZero) L = 1;
-    else if (p.cr_mode == kCrOne) L = p.D;
-    else {
-      const uint32_t w = philox_block(p.key, kStreamLen, p.inst, g, (uint32_t)i, 0u).x;
-      if (w == 0u) {
-        L = p.D;
-      } else {
-        int lo = 0, hi = min(p.D - 1, p.nT);
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          const uint32_t tv = tab ? tab[mid - 1] : __ldg(p.nec_tm1 + (mid - 1));
-          if (w <= tv) lo = mid; else hi = mid - 1;
-        }
-        L = 1 + lo;
-      }
+    if (p.cr_mode != kCrGeneral) {
+      L = (p.cr_mode == kCrZero) ? 1 : p.D;
+    } else {
+      const uint32_t w = nec_word(p, g, i);
+      L = tab ? nec_length_of<true>(p, w, tab) : nec_length_of<false>(p, w, p.nec_tm1);
     }
   } else if (I.xo == kExp) {
     L = exp_walk_length(p, g, i);

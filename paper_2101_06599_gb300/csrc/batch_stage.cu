@@ -365,8 +365,10 @@ __device__ __forceinline__ void flush(const GenParams& p, Cnt& c, int eval_only)
 
 // Grid-wide barrier of a cooperative launch (every CTA resident): an arrival
 // counter and a sense word that flips once all CTAs have arrived. The wait is
-// bounded; false if it gave up.
-__device__ bool grid_barrier(unsigned* count, unsigned* sense, unsigned nblocks) {
+// bounded by limit_ns of %globaltimer; false if it gave up. Every CTA arrives
+// exactly once whether or not it gives up, so the last arrival always resets
+// the counter and flips the sense: both are ready for the next launch.
+__device__ bool grid_barrier(unsigned* count, unsigned* sense, unsigned nblocks, unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -380,7 +382,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* sense, unsigned nblocks)
     } else {
       const unsigned long long t0 = global_ns();
       while (atomicAdd(sense, 0u) == s0) {
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
           ok = 0;
           break;
         }
@@ -399,11 +401,17 @@ __device__ bool grid_barrier(unsigned* count, unsigned* sense, unsigned nblocks)
 // kernel): the plans of every row first (plan tiles of 256 rows, the NEC
 // table staged in the CTA's shared memory), a grid barrier (ctr[2], ctr[3]),
 // the rows, and the last warp to finish closes every instance.
+// A CTA whose barrier wait gives up (wait_ns) records DE_ETIMEOUT and takes
+// no spans. The generation is still whole: every CTA writes its plans before
+// it arrives, so the CTAs released by the barrier (the last to arrive always
+// is) see every plan and take every span from the queue between them, and by
+// the time the last warp finishes every CTA has arrived, so it closes the
+// generation whatever its own CTA's wait did.
 template <bool FUSED>
 __global__ void __launch_bounds__(kPwThreads, 3)
 batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restrict__ spans, int nspans,
                    RowPlan32* __restrict__ plans, unsigned* ctr, int eval_only, const BatchTile* __restrict__ ptiles,
-                   int nptiles, DevState* states, int n_inst) {
+                   int nptiles, DevState* states, int n_inst, unsigned long long wait_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PassSmem& w = reinterpret_cast<PassSmem*>(smem_raw)[warp];
@@ -446,7 +454,7 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
         plans[I.row_base + i0] = a;
       }
     }
-    go = grid_barrier(&ctr[2], &ctr[3], gridDim.x);
+    go = grid_barrier(&ctr[2], &ctr[3], gridDim.x, wait_ns);
     if (!go && threadIdx.x == 0) atomicExch(&states[0].error, 4u);   // DE_ETIMEOUT
   }
 
@@ -533,7 +541,7 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
   done = __shfl_sync(0xFFFFFFFFu, done, 0);
   if (done == gridDim.x * kPwWarps - 1u) {           // the last warp of the launch
     __threadfence();
-    if (FUSED && go)
+    if (FUSED)
       for (int k = lane; k < n_inst; k += 32) close_instance(states[k], 0);
     __syncwarp();
     if (lane == 0) {
@@ -576,7 +584,7 @@ cudaError_t launch_batch_stage(const BatchInst* insts, const BatchSpan* spans, i
                                unsigned* ctr, int eval_only, int grid, cudaStream_t s) {
   const int g = std::max(1, grid / 2) * g_stage_ctas_per_sm;
   batch_stage_kernel<false><<<g, kPwThreads, batch_stage_smem(), s>>>(
-      insts, spans, nspans, const_cast<RowPlan32*>(plans), ctr, eval_only, nullptr, 0, nullptr, 0);
+      insts, spans, nspans, const_cast<RowPlan32*>(plans), ctr, eval_only, nullptr, 0, nullptr, 0, 0ull);
   return cudaGetLastError();
 }
 
@@ -587,8 +595,9 @@ bool batch_fused_supported() { return g_fused_ctas_per_sm > 0; }
 // barrier arrivals, barrier sense).
 cudaError_t launch_batch_fused(const BatchInst* insts, const BatchSpan* spans, int nspans, const BatchTile* ptiles,
                                int nptiles, RowPlan32* plans, DevState* states, int n_inst, unsigned* ctr, int grid,
-                               cudaStream_t s) {
+                               unsigned long long wait_ns, cudaStream_t s) {
   if (g_fused_ctas_per_sm <= 0) return cudaErrorNotSupported;
+  if (wait_ns == 0ull) wait_ns = kWaitLimitNs;
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3((unsigned)(std::max(1, grid / 2) * g_fused_ctas_per_sm));
@@ -601,7 +610,7 @@ cudaError_t launch_batch_fused(const BatchInst* insts, const BatchSpan* spans, i
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, batch_stage_kernel<true>, insts, spans, nspans, plans, ctr, 0, ptiles, nptiles,
-                            states, n_inst);
+                            states, n_inst, wait_ns);
 }
 
 }  // namespace de

@@ -67,6 +67,7 @@ struct GenParams {
   uint32_t inst;
   float ackley_b;
   float ell_k;              // elliptic: exponent step 6 log2(10) / (D - 1)
+  float nec_k;              // 1 / -log2(Cr) for 0 < Cr < 1 (the NEC lookup's first guess), else 0
   // test hook outputs (device, may be null)
   float* dbg_trial;         // N x pitch
   float* dbg_ftrial;        // N

@@ -50,6 +50,10 @@ struct de_ctx {
   void* host_pinned = nullptr;   // host: staging copy and state reads
   size_t host_pinned_bytes = 0;
   long long host_gen = 0;
+  // a device error reported by a synchronising call (DE_ETIMEOUT, ...): from
+  // then on calls that would launch generations return DE_ESTATE
+  int failed = 0;
+  unsigned long long wait_ns = 0;   // batched grid-barrier limit (0: the 1 s default)
   // batched contexts (de_batch_create); the fields above then describe nothing
   bool batch = false;
   int n_inst = 0;
@@ -94,9 +98,15 @@ void ctx_free(de_ctx* c, void* p);
 void drop_graphs(de_ctx* c);
 void choose_launch(int D4, int& block, int& vidx);
 int sync_stream(de_ctx* c);
+// Record a device error seen by a synchronising call (the context then
+// refuses launches) and return it.
+int note_device_error(de_ctx* c, int err);
+// The first non-zero device error word over a batch's instances (synchronises).
+int batch_device_error(de_ctx* c);
 // NEC thresholds T_n - 1 = ceil(c_n 2^32) - 1, c_1 = Cr, c_n = fl(c_{n-1} Cr),
 // up to n = D - 1 or before the first T_n <= 1.
 std::vector<uint32_t> nec_thresholds(double CR, int D);
+float nec_guess_factor(double CR);
 // Validation shared by de_create and de_batch_create (non-rotated objectives).
 bool valid_problem(int32_t N, int32_t D, float F, double CR, int xo, int obj, de_bounds b);
 int batch_set_base(de_ctx* c, int base);

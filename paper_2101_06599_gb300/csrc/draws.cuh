@@ -14,10 +14,15 @@
 //    ceil(ln U / ln Cr) = 1 + #{n >= 1 : U < Cr^n}. With Cr^n taken as the
 //    FP64 product c_n = fl(c_{n-1} Cr) and T_n = ceil(c_n 2^32),
 //    U < c_n  <=>  w < T_n  <=>  w <= T_n - 1, and T_n does not increase
-//    with n, so L = 1 + (largest n <= D - 1 with w <= T_n - 1), found by
-//    binary search in a table of T_n - 1. The table stops before the first
-//    T_n <= 1 (no w >= 1 passes it); w = 0 is U = 0, where ln U = -inf and
-//    L = D. Cr = 0 gives L = 1 and Cr = 1 gives L = D.
+//    with n, so L = 1 + n*, n* = the largest n <= D - 1 with w <= T_n - 1
+//    (0 if none), read from a table of T_n - 1. The table stops before the
+//    first T_n <= 1 (no w >= 1 passes it); w = 0 is U = 0, where ln U = -inf
+//    and L = D. Cr = 0 gives L = 1 and Cr = 1 gives L = D.
+//    The lookup is O(1): the real-valued form of the same count, n* =
+//    ceil(x) - 1 with x = log2(U) / log2(Cr) = (32 - log2 w) / (-log2 Cr),
+//    gives a first guess, and the table entries on either side of the guess
+//    confirm it (one pair of loads) or move it to the exact count. The
+//    result is the table's, whatever the guess, so it stays bit-exact.
 //  - Classic exponential crossover (Alg. 8): after copying L genes the walk
 //    draws word L-1 of the row's EXP stream and continues iff w < ceil(Cr
 //    2^32) and L < D.
@@ -142,18 +147,52 @@ __device__ __forceinline__ void draw_donors(const GenParams& p, uint32_t g, int 
   d.jrand = randint_w(b.w, (uint32_t)p.D);
 }
 
-// NEC segment length of row i, Eq. (9) through the threshold table.
-__device__ __forceinline__ int nec_length(const GenParams& p, uint32_t g, int i) {
+// Eq. (9) from the LEN word w of a row: L = 1 + n*, n* = #{1 <= n <= nmax :
+// w <= tm1[n - 1]} (a prefix of n, the table being non-increasing), with
+// nmax = min(D - 1, nT) and kinv = 1 / -log2(Cr). kShared: tm1 is in shared
+// memory (else global, read through the read-only path).
+template <bool kShared>
+__device__ __forceinline__ uint32_t nec_tab_at(const uint32_t* tm1, int k) {
+  if constexpr (kShared) return tm1[k];
+  else return __ldg(tm1 + k);
+}
+
+template <bool kShared>
+__device__ __forceinline__ int nec_length_word(uint32_t w, const uint32_t* tm1, int nmax, int D, float kinv) {
+  if (w == 0u) return D;                                   // U = 0: ln U = -inf
+  const float x = (32.0f - __log2f((float)w)) * kinv;     // log2(U) / log2(Cr)
+  int n = (int)ceilf(x) - 1;                               // the guess of n*
+  n = max(0, min(n, nmax));
+  // n* = n iff n passes (n = 0 always does) and n + 1 does not (or n = nmax)
+  const uint32_t below = (n > 0) ? nec_tab_at<kShared>(tm1, n - 1) : 0xFFFFFFFFu;
+  const uint32_t above = (n < nmax) ? nec_tab_at<kShared>(tm1, n) : 0u;
+  if (w <= below && w > above) return 1 + n;
+  while (n < nmax && w <= nec_tab_at<kShared>(tm1, n)) ++n;        // guess too low
+  while (n > 0 && w > nec_tab_at<kShared>(tm1, n - 1)) --n;        // guess too high
+  return 1 + n;
+}
+
+// L of row i in generation g from its Cr mode and a given LEN word.
+template <bool kShared>
+__device__ __forceinline__ int nec_length_of(const GenParams& p, uint32_t w, const uint32_t* tm1) {
   if (p.cr_mode == kCrZero) return 1;
   if (p.cr_mode == kCrOne) return p.D;
-  const uint32_t w = philox_block(p.key, kStreamLen, p.inst, g, (uint32_t)i, 0u).x;
-  if (w == 0u) return p.D;
-  int lo = 0, hi = min(p.D - 1, p.nT);         // answer n* in [lo, hi]
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (w <= __ldg(p.nec_tm1 + (mid - 1))) lo = mid; else hi = mid - 1;
-  }
-  return 1 + lo;
+  return nec_length_word<kShared>(w, tm1, min(p.D - 1, p.nT), p.D, p.nec_k);
+}
+
+__device__ __forceinline__ uint32_t nec_word(const GenParams& p, uint32_t g, int i) {
+  return philox_block(p.key, kStreamLen, p.inst, g, (uint32_t)i, 0u).x;
+}
+
+// NEC segment length of row i, Eq. (9), through the table in global memory.
+__device__ __forceinline__ int nec_length(const GenParams& p, uint32_t g, int i) {
+  if (p.cr_mode != kCrGeneral) return p.cr_mode == kCrZero ? 1 : p.D;
+  return nec_length_of<false>(p, nec_word(p, g, i), p.nec_tm1);
+}
+
+// Alg. 8's continuation test for one EXP word: rand < Cr, i.e. w < ceil(Cr 2^32).
+__device__ __forceinline__ bool exp_continues(const GenParams& p, uint32_t w) {
+  return (unsigned long long)w < p.cr_t;
 }
 
 // Alg. 8's sequential walk: returns L.
@@ -165,7 +204,7 @@ __device__ __forceinline__ int exp_walk_length(const GenParams& p, uint32_t g, i
     if ((k & 3u) == 0u) blk = philox_block(p.key, kStreamExp, p.inst, g, (uint32_t)i, k >> 2);
     const uint32_t w = word_of(blk, k & 3u);
     ++k;
-    if (!((unsigned long long)w < p.cr_t)) break;
+    if (!exp_continues(p, w)) break;
     ++L;
   }
   return L;

@@ -5,8 +5,9 @@
 // One CTA owns one row i. Its T threads hold the row in registers as V
 // float4 slots each (slot q = t + k T, genes 4q .. 4q+3), so the parent row
 // is read from HBM exactly once with coalesced 128-bit loads. Per row:
-//   1. every thread issues its parent loads; thread 0 meanwhile draws r1,
-//      r2, r3, j_rand (and L for exp / NEC) and publishes the donor rows;
+//   1. every thread issues its parent loads; meanwhile thread 0 draws r1,
+//      r2, r3, j_rand and publishes the donor rows, and the first thread of
+//      the second warp draws L for exp / NEC (both at once);
 //   2. each thread computes the crossover mask of its genes in registers
 //      (binomial: one Philox block per slot; exp / NEC: the circular test
 //      ((j - j_rand) mod D) < L) and, only for slots holding a masked gene,
@@ -134,17 +135,23 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
     x[k] = (q < p.D4) ? ld_stream(xrow + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
 
-  // draws, once per row
+  // draws, once per row: the donors on thread 0 and, at the same time, the
+  // segment length on the first thread of the second warp (thread 0 as well
+  // when the CTA is a single warp)
+  const int tlen = (T >= 64) ? 32 : 0;
   if (t == 0) {
     RowDraws d;
     draw_donors(p, g, i, d);
-    if constexpr (XO == kNec) d.L = nec_length(p, g, i);
-    else if constexpr (XO == kExp) d.L = exp_walk_length(p, g, i);
-    else d.L = 0;
-    sh.r1 = d.r1; sh.r2 = d.r2; sh.r3 = d.r3; sh.jrand = d.jrand; sh.L = d.L;
+    sh.r1 = d.r1; sh.r2 = d.r2; sh.r3 = d.r3; sh.jrand = d.jrand;
     sh.d1 = reinterpret_cast<const float4*>((slot_in[d.r1] ? p.pop1 : p.pop0) + (size_t)d.r1 * p.pitch);
     sh.d2 = reinterpret_cast<const float4*>((slot_in[d.r2] ? p.pop1 : p.pop0) + (size_t)d.r2 * p.pitch);
     sh.d3 = reinterpret_cast<const float4*>((slot_in[d.r3] ? p.pop1 : p.pop0) + (size_t)d.r3 * p.pitch);
+  }
+  if (t == tlen) {
+    int L = 0;
+    if constexpr (XO == kNec) L = nec_length(p, g, i);
+    else if constexpr (XO == kExp) L = exp_walk_length(p, g, i);
+    sh.L = L;
   }
   __syncthreads();
 

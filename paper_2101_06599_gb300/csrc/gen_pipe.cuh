@@ -82,17 +82,9 @@ __host__ __device__ inline PipeLayout pipe_layout(int S, int tcap, int stage_flo
 
 __device__ __forceinline__ int nec_length_tab(const GenParams& p, const uint32_t* tab, bool in_smem,
                                               uint32_t g, int i) {
-  if (p.cr_mode == kCrZero) return 1;
-  if (p.cr_mode == kCrOne) return p.D;
-  const uint32_t w = philox_block(p.key, kStreamLen, p.inst, g, (uint32_t)i, 0u).x;
-  if (w == 0u) return p.D;
-  int lo = 0, hi = min(p.D - 1, p.nT);
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    const uint32_t t = in_smem ? tab[mid - 1] : __ldg(p.nec_tm1 + (mid - 1));
-    if (w <= t) lo = mid; else hi = mid - 1;
-  }
-  return 1 + lo;
+  if (p.cr_mode != kCrGeneral) return p.cr_mode == kCrZero ? 1 : p.D;
+  const uint32_t w = nec_word(p, g, i);
+  return in_smem ? nec_length_of<true>(p, w, tab) : nec_length_of<false>(p, w, p.nec_tm1);
 }
 
 __device__ __forceinline__ void pipe_flag_error(const GenParams& p, volatile int* abort_flag) {

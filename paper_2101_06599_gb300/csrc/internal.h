@@ -29,6 +29,10 @@ cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s
 // Move every row held in slot buffer 1 to slot buffer 0 and clear its slot
 // bit, so that buffer 0 holds the whole population.
 cudaError_t launch_normalize(const GenParams& p, cudaStream_t s);
+// Test hook: L of Eq. (9) (table in global and in shared memory) and Alg. 8's
+// continuation test for n caller-given words (device arrays).
+cudaError_t launch_debug_lengths(const GenParams& p, const uint32_t* words, int n, int* L_global, int* L_shared,
+                                 uint8_t* exp_cont, cudaStream_t s);
 
 // Pipelined generation kernel (exp / NEC); PipeParams in gen_pipe.cuh.
 struct PipeParams;
@@ -74,6 +78,7 @@ struct BatchWork {
   const BatchSpan* spans[4];   // register kernel for bin, exp, NEC; staged kernel (exp and NEC)
   int nspans[4];
   unsigned* ctr;               // 12 counters (2 per register list; 4 for the staged list)
+  unsigned long long wait_ns;  // limit of the one-launch generation's grid barrier (0: 1 s)
   const BatchTile* ctiles;
   int nctiles;
 };
@@ -101,7 +106,7 @@ cudaError_t launch_batch_stage(const BatchInst*, const BatchSpan*, int, const Ro
 bool batch_fused_supported();
 cudaError_t launch_batch_fused(const BatchInst* insts, const BatchSpan* spans, int nspans, const BatchTile* ptiles,
                                int nptiles, RowPlan32* plans, DevState* states, int n_inst, unsigned* ctr, int grid,
-                               cudaStream_t s);
+                               unsigned long long wait_ns, cudaStream_t s);
 // the span row kernel alone, one per crossover (batch_span_*.cu)
 cudaError_t launch_batch_span_bin(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
                                   cudaStream_t);

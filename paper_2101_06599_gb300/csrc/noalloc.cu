@@ -13,8 +13,12 @@
 //   [0, 256)                 generation state (counters, best key, CTA-done counter)
 //   [256, 256 + 2*65536)     slot bytes, two halves of N
 //   [.., + 4*32768)          NEC thresholds T_n - 1, n = 1 .. D - 1
-// Every call overwrites it; calls that overlap on the GPU (two streams, or
-// two host threads) race on it and must be serialised by the caller.
+// Every call overwrites the state and the slot bytes; the thresholds are
+// rewritten only when (Cr, D) differ from the last call's on that device
+// (a host-side record per device), since building them takes up to D - 1
+// dependent FP64 products on one thread. Calls that overlap on the GPU (two
+// streams, or two host threads) race on the array and must be serialised by
+// the caller.
 #include <cmath>
 
 #include "../../include/de.h"
@@ -43,13 +47,16 @@ namespace de {
 // device current (a host-side name of the array is not a device address).
 static void* g_scratch_addr[kNoallocMaxDevices];
 static bool g_scratch_ready[kNoallocMaxDevices];
+// (Cr, D) of the thresholds the array holds, per device ordinal.
+static double g_table_cr[kNoallocMaxDevices];
+static int g_table_d[kNoallocMaxDevices];   // 0: no table built yet
 
 // Clears what must start at zero (state, the input half of the slot bytes),
 // writes the NEC thresholds: zeros for n beyond the last T_n > 1 (no word
 // w >= 1 passes them), then T_n - 1 = ceil(c_n 2^32) - 1 with c_1 = Cr,
 // c_n = fl(c_{n-1} Cr) in FP64, exactly as de_create computes them.
 __global__ void noalloc_setup_kernel(unsigned char* scratch, int N, int D, double CR, int cr_mode,
-                                     long long gen) {
+                                     long long gen, int build_table) {
   DevState* st = reinterpret_cast<DevState*>(scratch);
   uint8_t* slots = scratch + kNoallocStateBytes;
   uint32_t* tab = reinterpret_cast<uint32_t*>(scratch + kNoallocStateBytes + kNoallocSlotBytes);
@@ -65,6 +72,7 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, int N, int D, doubl
     st->best_f = __int_as_float(0x7F800000);
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) slots[(size_t)(gen & 1) * N + i] = 0;
+  if (!build_table) return;
   for (int k = threadIdx.x; k < D - 1; k += blockDim.x) tab[k] = 0u;
   __syncthreads();
   if (threadIdx.x == 0 && cr_mode == kCrGeneral) {
@@ -157,11 +165,18 @@ extern "C" int de_nec_step_noalloc(const float* pop_in, const float* fit_in, flo
   p.inst = 0;
   p.ackley_b = 0.2f;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
+  p.nec_k = (CR > 0.0 && CR < 1.0) ? (float)(1.0 / -std::log2(CR)) : 0.0f;
 
   int block = 32, vidx = 0;
   noalloc_shape(p.D4, block, vidx);
-  noalloc_setup_kernel<<<1, 256, 0, s>>>(scratch, N, D, CR, p.cr_mode, (long long)generation);
+  const bool build_table = !(g_table_d[dev] == D && g_table_cr[dev] == CR);
+  noalloc_setup_kernel<<<1, 256, 0, s>>>(scratch, N, D, CR, p.cr_mode, (long long)generation, build_table ? 1 : 0);
   cudaError_t e = cudaGetLastError();
+  if (build_table) {
+    // recorded only once the build is queued; a failed launch builds it again next time
+    g_table_d[dev] = (e == cudaSuccess) ? D : 0;
+    g_table_cr[dev] = CR;
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(fit_out, fit_in, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = launch_gen_nec((int)obj, vidx, p, block, s);
   if (e == cudaSuccess) {

@@ -92,7 +92,10 @@ def load_library(build_if_missing: bool = True):
         "de_save": ([vp, vp, C.POINTER(C.c_size_t)], C.c_int),
         "de_load": ([vp, vp, C.c_size_t], C.c_int),
         "de_debug_step": ([vp, vp, vp, vp, vp], C.c_int),
+        "de_debug_lengths": ([vp, i32, vp, i32, vp, vp, vp], C.c_int),
         "de_set_launch": ([vp, i32, i32], C.c_int),
+        "de_set_wait_limit": ([vp, i64], C.c_int),
+        "de_get_wait_limit": ([vp, C.POINTER(i64)], C.c_int),
         "de_get_launch": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "de_set_kernel": ([vp, i32], C.c_int),
         "de_get_kernel": ([vp, C.POINTER(i32)], C.c_int),
@@ -300,6 +303,30 @@ def de_debug_step(ctx, trial_out=None, ftrial_out=None, accept_out=None, draws_o
         _host_ptr(accept_out, np.uint8, 1, True), _host_ptr(draws_out, np.int32, 1, True)), "de_debug_step")
 
 
+def de_debug_lengths(ctx, words, inst=0):
+    """Eq. (9)'s L (table in global and in shared memory) and Alg. 8's
+    continuation flag for each given 32-bit word (see include/de.h)."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    n = int(w.size)
+    Lg = np.empty(n, dtype=np.int32)
+    Ls = np.empty(n, dtype=np.int32)
+    ec = np.empty(n, dtype=np.uint8)
+    _check(load_library().de_debug_lengths(C.c_void_p(ctx), int(inst), C.c_void_p(w.ctypes.data), n,
+                                           C.c_void_p(Lg.ctypes.data), C.c_void_p(Ls.ctypes.data),
+                                           C.c_void_p(ec.ctypes.data)), "de_debug_lengths")
+    return Lg, Ls, ec.astype(bool)
+
+
+def de_set_wait_limit(ctx, ns):
+    _check(load_library().de_set_wait_limit(C.c_void_p(ctx), int(ns)), "de_set_wait_limit")
+
+
+def de_get_wait_limit(ctx):
+    v = C.c_int64()
+    _check(load_library().de_get_wait_limit(C.c_void_p(ctx), C.byref(v)), "de_get_wait_limit")
+    return v.value
+
+
 def de_set_launch(ctx, threads, vec4):
     _check(load_library().de_set_launch(C.c_void_p(ctx), int(threads), int(vec4)), "de_set_launch")
 
@@ -486,6 +513,15 @@ class Batch:
     def set_base(self, base):
         de_set_base(self.ctx, base)
 
+    def debug_lengths(self, inst, words):
+        return de_debug_lengths(self.ctx, words, inst)
+
+    def set_wait_limit(self, ns):
+        de_set_wait_limit(self.ctx, ns)
+
+    def wait_limit(self):
+        return de_get_wait_limit(self.ctx)
+
     def groups(self):
         return de_batch_get_groups(self.ctx)
 
@@ -562,6 +598,9 @@ class Optimizer:
         dr = np.empty((self.N, 5), dtype=np.int32)
         de_debug_step(self.ctx, trial, ft, acc, dr)
         return trial, ft, acc.astype(bool), dr
+
+    def debug_lengths(self, words):
+        return de_debug_lengths(self.ctx, words, 0)
 
     def save(self):
         return de_save(self.ctx)

@@ -7,6 +7,8 @@
   geometric law of Eqs. (3)-(4) at D = 10 with 10^6 draws (the design of the
   paper's Fig. 2), and against each other.
 - Eq. (9)'s special cases Cr = 0 and Cr = 1.
+- Alg. 8's continuation test rand < Cr at the words on either side of the
+  exact threshold ceil(Cr 2^32).
 - The NEC segment against brute force Alg. 9 for every (D, j_rand, L), D <= 12.
 - Binomial mask rate Cr + (1 - Cr) / D and the forced j_rand gene (Eq. 2).
 """
@@ -69,6 +71,16 @@ def test_nec_length_special_cases(D):
         assert O.nec_length(w, 1.0, D) == D
         assert 1 <= O.nec_length(w, 0.7, D) <= D
     assert O.nec_length(0, 0.3, D) == D          # U = 0: ln U = -inf
+
+
+@pytest.mark.parametrize("Cr", [0.0, 1e-12, 0.1, 0.3, 0.5, 0.9, 0.99, 0.9999, 1.0 - 2.0**-40, 1.0])
+def test_exp_continuation_at_its_threshold(Cr):
+    """Alg. 8 continues iff rand < Cr: with rand = w / 2^32 that is w < T for
+    T = ceil(Cr 2^32) computed exactly from the FP64 value of Cr."""
+    T = math.ceil(Fraction(Cr) * 2**32)
+    for w in (T - 2, T - 1, T, T + 1, 0, 1, 2**32 - 1):
+        if 0 <= w < 2**32:
+            assert O.exp_continues(w, Cr) == (w < T), (Cr, w, T)
 
 
 @pytest.mark.parametrize("Cr", [0.1, 0.2, 0.5, 0.9])
