@@ -470,13 +470,113 @@ def replica_seed(rank):
     return SEED + rank
 
 
-def oracle_generation_rate(N, D, obj, xo, budget_s, rows_per_step=None, steps=None, warmup=0):
-    """Time the CPU oracle (single thread) on generations of the same workload.
-    Returns (ind_dims_per_s, rows_per_step, steps_timed, seconds)."""
+def headline_config(N, D, obj, xo, world):
+    """The workload description shared by the GPU line and the reference arm."""
+    return {"workload": WORKLOAD if (N, D) == (N_DEF, D_DEF) and obj in ("rosenbrock", "ackley")
+            else "%s_N%d_D%d" % (obj, N, D),
+            "objective": obj, "crossover": xo, "N": N, "D": D,
+            "F": F_DEF, "CR": CR_DEF, "parallelism": "replicas" if world > 1 else "single",
+            "l2": ("inputs larger than L2 (two %.2f GB population buffers), no flush" % (4e-9 * N * D)
+                   if 4.0 * N * D > 129e6 else
+                   "population of %.1f MB fits in L2 (L2-resident case, no flush)" % (4e-6 * N * D))}
+
+
+# ---- the CPU oracle on the host cores -----------------------------------------
+# All-cores leg: P worker processes (spawned, so that none inherits a CUDA
+# context) each run the single-threaded oracle on their own block of rows of
+# the same generation; the population and fitness live in shared memory.
+_W = {}
+
+
+def _oracle_worker_init(shm_pop, shm_fit, N, D):
+    from multiprocessing import shared_memory
+    import oracle as O
+    a = shared_memory.SharedMemory(name=shm_pop)
+    b = shared_memory.SharedMemory(name=shm_fit)
+    _W["shm"] = (a, b)
+    _W["pop"] = np.ndarray((N, D), dtype=np.float32, buffer=a.buf)
+    _W["fit"] = np.ndarray((N,), dtype=np.float64, buffer=b.buf)
+    _W["O"] = O
+    O.lib()
+
+
+def _oracle_worker_rows(task):
+    obj, xo, g, i0, i1 = task
+    O = _W["O"]
+    lo, hi = BOXES[obj]
+    t0 = time.perf_counter()
+    O.step(_W["pop"], _W["fit"], F_DEF, CR_DEF, xo, obj, lo, hi, SEED, g, rows=(i0, i1), want_trial=False)
+    return time.perf_counter() - t0
+
+
+def oracle_generation_rate_all_cores(pop, fit, obj, xo, rows_per_proc, steps, procs, budget_s=None):
+    """Wall-clock rate of generations of the oracle over procs x rows_per_proc
+    rows, one block of rows per process, every process a single-threaded
+    oracle: `steps` generations, or (steps None) as many as fill budget_s.
+    The generation index advances each step; the population is not advanced
+    (each step starts from the same parents), which changes neither the work
+    nor its cost. Returns (rate, seconds, steps)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    N, D = pop.shape
+    a = shared_memory.SharedMemory(create=True, size=pop.nbytes)
+    b = shared_memory.SharedMemory(create=True, size=fit.nbytes)
+    try:
+        np.ndarray(pop.shape, dtype=np.float32, buffer=a.buf)[:] = pop
+        np.ndarray(fit.shape, dtype=np.float64, buffer=b.buf)[:] = fit
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(a.name, b.name, N, D)) as pool:
+            pool.map(_oracle_worker_rows, [(obj, xo, 0, 0, 1)] * procs)           # start-up, not timed
+            t0 = time.perf_counter()
+            g = 0
+            while (g < steps) if steps else (g == 0 or time.perf_counter() - t0 < budget_s):
+                tasks = [(obj, xo, g, k * rows_per_proc, (k + 1) * rows_per_proc) for k in range(procs)]
+                pool.map(_oracle_worker_rows, tasks, chunksize=1)
+                g += 1
+            secs = time.perf_counter() - t0
+    finally:
+        a.close(); a.unlink()
+        b.close(); b.unlink()
+    return procs * rows_per_proc * D * g / secs, secs, g
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_legs(N, D, obj, xo, budget_s, steps=None, warmup=0):
+    """The oracle as it stands, single-threaded and on all host cores, on the
+    same workload: returns the cpu_baseline object (all cores) with the
+    single-thread figure beside it."""
     import oracle as O
     lo, hi = BOXES[obj]
     pop = O.init(N, D, lo, hi, SEED)
     fit = O.evaluate(obj, pop)
+    rate1, rows1, timed1, secs1 = oracle_generation_rate(N, D, obj, xo, budget_s / 2, steps=steps, warmup=warmup,
+                                                         pop=pop, fit=fit)
+    procs = max(1, min(host_cores(), N))
+    rows_p = max(1, min(rows1, N // procs))             # rows per process and step
+    rate_p, secs_p, steps_p = oracle_generation_rate_all_cores(pop, fit, obj, xo, rows_p, steps, procs,
+                                                               budget_s=budget_s / 2)
+    return {"value": rate_p, "unit": UNIT, "cores": procs, "kind": "oracle", "ms_per_step": 1e3 * secs_p / steps_p,
+            "sample": "%d generation(s) of the CPU oracle, %d processes x rows [k %d, (k+1) %d) of the same "
+                      "N=%d x D=%d %s/%s workload (donors from all N rows), %.1f s wall, one single-threaded "
+                      "oracle per process" % (steps_p, procs, rows_p, rows_p, N, D, obj, xo.upper(), secs_p),
+            "single_thread": {"value": rate1, "cores": 1,
+                              "sample": "%d generation(s) over rows [0, %d), %.1f s" % (timed1, rows1, secs1)}}
+
+
+def oracle_generation_rate(N, D, obj, xo, budget_s, rows_per_step=None, steps=None, warmup=0, pop=None, fit=None):
+    """Time the CPU oracle (single thread) on generations of the same workload.
+    Returns (ind_dims_per_s, rows_per_step, steps_timed, seconds)."""
+    import oracle as O
+    lo, hi = BOXES[obj]
+    if pop is None:
+        pop = O.init(N, D, lo, hi, SEED)
+        fit = O.evaluate(obj, pop)
     if rows_per_step is None:
         t0 = time.perf_counter()
         O.step(pop, fit, F_DEF, CR_DEF, xo, obj, lo, hi, SEED, 0, rows=(0, 64), want_trial=False)
@@ -508,19 +608,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     steps, warmup = args.steps, args.warmup
-    budget = 150.0
-    rate, rows, timed, secs = oracle_generation_rate(N_DEF, D_DEF, "rosenbrock", "nec", budget,
-                                                     steps=steps, warmup=warmup)
-    sample = ("%d oracle generations over rows [0, %d) of the N=%d, D=%d Rosenbrock population "
-              "(donors from all N rows), NEC, F=0.5, Cr=0.9; single thread" % (timed, rows, N_DEF, D_DEF))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    cpu = cpu_baseline_legs(N_DEF, D_DEF, "rosenbrock", "nec", 120.0, steps=steps, warmup=warmup)
+    rate = cpu["value"]
     line = {
-        "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": timed,
-        "warmup": warmup, "ms_per_step": 1e3 * secs / timed, "higher_is_better": True,
+        "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+        "warmup": warmup, "ms_per_step": cpu["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 mutation, f64 fitness", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "objective": "rosenbrock", "crossover": "nec", "N": N_DEF,
-                   "D": D_DEF, "F": F_DEF, "CR": CR_DEF},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": headline_config(N_DEF, D_DEF, "rosenbrock", "nec", world),
+        "cpu_baseline": cpu,
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -671,24 +768,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, rows, timed, secs = oracle_generation_rate(N, D, "rosenbrock", "nec", 12.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d generation(s) of the CPU oracle over rows [0, %d) of the same N=%d x D=%d "
-                         "Rosenbrock/NEC workload (donors from all N rows), %.1f s, single thread"
-                         % (timed, rows, N, D, secs)}
+        cpu = cpu_baseline_legs(N, D, args.obj, args.xo, 24.0)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if (N, D) == (N_DEF, D_DEF) and args.obj in ("rosenbrock", "ackley")
-                       else "%s_N%d_D%d" % (args.obj, N, D),
-                       "objective": args.obj, "crossover": args.xo, "N": N, "D": D,
-                       "F": F_DEF, "CR": CR_DEF, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": ("inputs larger than L2 (two %.2f GB population buffers), no flush" % (4e-9 * N * D)
-                              if 4.0 * N * D > 129e6 else
-                              "population of %.1f MB fits in L2 (L2-resident case, no flush)" % (4e-6 * N * D))},
+            "config": headline_config(N, D, args.obj, args.xo, world),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
             "clocks": clk.summary(), "variants": variants, "batched": batched, "rotated": rotated,
             "small_configs": small, "crossover_table1": xgrid, "paper_table2": table2,
