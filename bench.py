@@ -189,11 +189,14 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         raise
 
 
-def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
+def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None, kernels="tuned"):
     """The 512-instance workload (D log-uniform in [10, 2000], N = min(10 D,
     4096), sphere/Rastrigin/Ackley/Rosenbrock round-robin, NEC, F = 0.5,
     Cr = 0.9), one generation of every instance per step. n_inst keeps the
-    first n_inst instances (a smaller case of the same mix, for profiling)."""
+    first n_inst instances (a smaller case of the same mix, for profiling).
+    kernels: "tuned" (de_batch_autotune picks the row kernel per class of
+    instances), or every instance on the streaming ("flow") or the staged
+    ("staged") kernel."""
     from paper_2101_06599_gb300 import workloads as Wk
     specs = [dict(N=s.N, D=s.D, obj=s.objective, bounds=Wk.BOXES[s.objective], xo="nec", CR=CR_DEF, F=F_DEF)
              for s in Wk.batched_specs()]
@@ -204,9 +207,15 @@ def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
     b = DE.Batch(specs, seed=seed + 4)
     try:
         t_tune = time.time()
-        groups = b.autotune(reps=3)
+        if kernels == "tuned":
+            groups = b.autotune(reps=3)
+        else:
+            b.set_groups([2 if kernels == "flow" else 1] * len(specs))
+            groups = b.groups()
         t_tune = time.time() - t_tune
-        kinds = sorted({"staged" if g < 0 else ("register" if g <= 32 else "cta") for g in groups})
+        def kind(g):
+            return "staged" if g < 0 else ("streaming" if g == 2 else ("register" if g <= 32 else "cta"))
+        kinds = sorted({kind(g) for g in groups})
         b.run(warmup)
         b.synchronize()
         st0 = b.stats()
@@ -234,10 +243,10 @@ def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None):
             "instances": len(specs), "ind_dims_per_step": units,
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_gen": ms / steps,
             "hbm_gbs": gbs, "frac": gbs / peak,
-            # every instance on the staged kernel: one cooperative launch per generation
-            "launches_per_step": 1 if kinds == ["staged"] else 2 + len(kinds),
-            "row_kernels": {kd: sum(1 for g in groups if ("staged" if g < 0 else ("register" if g <= 32 else "cta")) == kd)
-                            for kd in kinds},
+            # every instance on the staged, or every one on the streaming kernel: one
+            # cooperative launch per generation
+            "launches_per_step": 1 if kinds in (["staged"], ["streaming"]) else 2 + len(kinds),
+            "row_kernels": {kd: sum(1 for g in groups if kind(g) == kd) for kd in kinds},
             "autotune_s": round(t_tune, 3),
             "a_acceptance": d_acc / (rows * steps), "m_masked_fraction": d_msk / (units * steps)}
 
@@ -638,6 +647,8 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=0,
                     help="batched leg: keep the first K of the 512 instances (profiling)")
+    ap.add_argument("--batch-kernels", default="tuned", choices=["tuned", "flow", "staged"],
+                    help="batched leg: row kernels picked by the autotuner, or one kernel for every instance")
     ap.add_argument("--no-crossover", action="store_true")
     ap.add_argument("--no-table2", action="store_true")
     ap.add_argument("--only", choices=["rotated", "small", "batched", "crossover", "table2"],
@@ -679,7 +690,8 @@ def main():
         elif args.only == "table2":
             res = time_paper_table2(DE, torch)
         else:
-            res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0], args.batch_instances)
+            res = time_batched(DE, torch, K, W, seed, measured_hbm_peak()[0], args.batch_instances,
+                               args.batch_kernels)
         if rank == 0:
             print(json.dumps({"only": args.only, "steps": K, "warmup": W, "result": res}))
         if _dist is not None:
@@ -748,7 +760,7 @@ def main():
 
     batched = None
     if not args.no_batched:
-        batched = time_batched(DE, torch, K, W, seed, peak)
+        batched = time_batched(DE, torch, K, W, seed, peak, kernels=args.batch_kernels)
 
     rotated = None
     if not args.no_rotated:

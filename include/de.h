@@ -314,6 +314,9 @@ int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftri
  *              pass of up to 32 rows / 8 KB into registers while it
  *              processes the previous one from shared memory;
  *   1          the staged pipeline with its default G (32);
+ *   2          the streaming kernel (exp and NEC only, any D): one warp per
+ *              row, the row read in chunks of 512 genes straight into
+ *              registers while the previous chunk is processed;
  *   G = 4..256 (a power of two with ceil(ceil(D/4) / G) <= 16) register
  *              tiles of G threads per row (one warp of 32 / G rows for
  *              G <= 32, a CTA of 256 / G rows above);
@@ -321,8 +324,8 @@ int de_batch_debug_step(de_ctx *ctx, int32_t inst, float *trial_out, float *ftri
  *              smallest such G.
  * de_batch_get_groups reports staged instances as -G. Draws are unchanged by
  * the choice, and so are fitness values, selections and trajectories for
- * every choice with at most 32 threads per row (staged, and G = 4..32):
- * those kernels sum the FP32 fitness in one fixed order. G > 32 (needed only
+ * every choice with at most 32 threads per row (staged, streaming, and
+ * G = 4..32): those kernels sum the FP32 fitness in one fixed order. G > 32 (needed only
  * for D > 2048) sums in another order. Returns DE_EINVAL for an invalid
  * value; the context is unchanged then. */
 int de_batch_set_groups(de_ctx *ctx, const int32_t *groups);

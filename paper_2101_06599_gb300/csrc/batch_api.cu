@@ -45,6 +45,7 @@ static int default_group(int D4, int xo) {
 
 static bool valid_group(int G, int D4, int xo) {
   if (G == kBatchStaged) return xo != kBin && D4 <= kStageMaxD4;
+  if (G == kBatchFlow) return xo != kBin;
   if (G < 4 || G > kBatchMaxGroup || (G & (G - 1)) != 0) return false;
   return (D4 + G - 1) / G <= kBatchMaxD4PerLane;
 }
@@ -75,6 +76,14 @@ static int upload_insts(de_ctx* c) {
   return sync_stream(c);
 }
 
+// The span list of instance k: register kernel per crossover, staged (3) or
+// streaming (4).
+static int list_of(const de_ctx* c, int k) {
+  if (c->bgroup[k] == kBatchStaged) return 3;
+  if (c->bgroup[k] == kBatchFlow) return 4;
+  return c->bxo[k];
+}
+
 static size_t span_cost(const de_ctx* c, int k) {
   return (size_t)std::min(c->bp[k].N, kSpanRows) * (size_t)c->bp[k].D4;
 }
@@ -97,7 +106,7 @@ static int build_tiles(de_ctx* c) {
   // first, so that the warps at the head of the queue share one
   // specialisation as long as possible
   auto cls = [&](int k) {
-    const int kind = c->bgroup[k] == kBatchStaged ? 1024 + c->blanes[k] : c->bgroup[k];
+    const int kind = c->bgroup[k] == kBatchStaged ? 1024 + c->blanes[k] : c->bgroup[k];   // flow: 2
     return (c->bobj[k] * 3 + c->bxo[k]) * 2048 + kind;
   };
   std::map<int, double> work;
@@ -107,14 +116,14 @@ static int build_tiles(de_ctx* c) {
     if (ca != cb) return work[ca] != work[cb] ? work[ca] > work[cb] : ca < cb;
     return span_cost(c, a) > span_cost(c, b);
   });
-  std::vector<BatchSpan> sp[4];
+  std::vector<BatchSpan> sp[kBatchLists];
   std::vector<BatchTile> ct;
   c->bt0.assign((size_t)c->n_inst, 0);
   c->bt1.assign((size_t)c->n_inst, 0);
   for (int k : order) {
     const int N = c->bp[k].N;
     if (c->bgroup[k] <= 32) {
-      std::vector<BatchSpan>& v = sp[c->bgroup[k] == kBatchStaged ? 3 : c->bxo[k]];
+      std::vector<BatchSpan>& v = sp[list_of(c, k)];
       c->bt0[k] = (int)v.size();
       for (int r = 0; r < N; r += kSpanRows) {
         BatchSpan s;
@@ -134,7 +143,7 @@ static int build_tiles(de_ctx* c) {
     }
   }
   int rc = DE_OK;
-  for (int x = 0; x < 4 && rc == DE_OK; ++x) {
+  for (int x = 0; x < kBatchLists && rc == DE_OK; ++x) {
     rc = upload(c, (void**)&c->d_spans[x], sp[x].data(), sp[x].size() * sizeof(BatchSpan));
     c->nspans[x] = (int)sp[x].size();
   }
@@ -152,14 +161,14 @@ static BatchWork batch_work(const de_ctx* c, int inst) {
   w.ctr = c->d_span_ctr;
   w.wait_ns = c->wait_ns;
   if (inst < 0) {
-    for (int x = 0; x < 4; ++x) {
+    for (int x = 0; x < kBatchLists; ++x) {
       w.spans[x] = c->d_spans[x];
       w.nspans[x] = c->nspans[x];
     }
     w.ctiles = c->d_ctiles;
     w.nctiles = c->nctiles;
   } else if (c->bgroup[inst] <= 32) {
-    const int x = c->bgroup[inst] == kBatchStaged ? 3 : c->bxo[inst];
+    const int x = list_of(c, inst);
     w.spans[x] = c->d_spans[x] + c->bt0[inst];
     w.nspans[x] = c->bt1[inst] - c->bt0[inst];
   } else {
@@ -266,7 +275,7 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   c->batch_grid = std::max(1, c->sm_count) * 2;
-  if (prepare_batch_stage() != cudaSuccess) {
+  if (prepare_batch_stage() != cudaSuccess || prepare_batch_flow() != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return DE_ECUDA;
@@ -317,8 +326,9 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
     rows += specs[k].N;
   }
   c->d_plans = (RowPlan32*)ctx_alloc(c, (size_t)rows * sizeof(RowPlan32));
-  c->d_span_ctr = (unsigned*)ctx_alloc(c, 12 * sizeof(unsigned));
-  if (!c->d_plans || !c->d_span_ctr || cudaMemsetAsync(c->d_span_ctr, 0, 12 * sizeof(unsigned), c->stream) != cudaSuccess) {
+  c->d_span_ctr = (unsigned*)ctx_alloc(c, kBatchCounters * sizeof(unsigned));
+  if (!c->d_plans || !c->d_span_ctr ||
+      cudaMemsetAsync(c->d_span_ctr, 0, kBatchCounters * sizeof(unsigned), c->stream) != cudaSuccess) {
     de_destroy(c);
     return DE_ENOMEM;
   }
@@ -516,6 +526,11 @@ int de_batch_set_groups(de_ctx* c, const int32_t* groups) {
     int G = groups[k];
     const int D4 = c->bp[k].D4;
     if (G == 0) G = default_group(D4, c->bxo[k]);
+    if (G == kBatchFlow) {
+      if (!valid_group(G, D4, c->bxo[k])) return DE_EINVAL;
+      g[k] = G;
+      continue;
+    }
     if (G == kBatchStaged) {
       l[k] = default_lanes(D4);
     } else if (G < 0) {                              // staged, -G lanes per row
@@ -593,12 +608,12 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
   };
   // start from the fastest of a few whole-batch choices: as they stand, the
   // fewest register lanes, 32 register lanes, the staged kernel with its
-  // default lanes where allowed
+  // default lanes where allowed, the streaming kernel where allowed
   if (rc == DE_OK) {
     std::vector<int> bg = c->bgroup, bl = c->blanes;
     float best_t = 0.0f;
     rc = trial(best_t);
-    for (int rule = 0; rule < 3 && rc == DE_OK; ++rule) {
+    for (int rule = 0; rule < 4 && rc == DE_OK; ++rule) {
       std::vector<int> g0 = c->bgroup, l0 = c->blanes;
       for (const auto& cl : classes)
         for (int k : cl.second) {
@@ -609,6 +624,7 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
             c->bgroup[k] = kBatchStaged;
             c->blanes[k] = default_lanes(D4);
           }
+          if (rule == 3 && valid_group(kBatchFlow, D4, xo)) c->bgroup[k] = kBatchFlow;
           if (!valid_group(c->bgroup[k], D4, xo)) c->bgroup[k] = g0[k];
         }
       float ms = 0.0f;
@@ -624,7 +640,9 @@ int de_batch_autotune(de_ctx* c, int32_t reps, int32_t* groups_out) {
     c->bgroup = bg;
     c->blanes = bl;
   }
-  // coordinate descent: one class at a time, the others as they stand
+  // coordinate descent: one class at a time, the others as they stand (the
+  // streaming kernel is tried for the whole batch only: a mix with the staged
+  // kernel would cost the one-launch generation that either gives alone)
   for (auto it = classes.begin(); it != classes.end() && rc == DE_OK; ++it) {
     const std::vector<int>& ks = it->second;
     const int xo = c->bxo[ks[0]];

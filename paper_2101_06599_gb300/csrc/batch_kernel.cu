@@ -358,6 +358,8 @@ static cudaError_t launch_spans(const BatchInst* insts, const BatchWork& w, cons
     e = launch_batch_span_nec(insts, w.spans[kNec], w.nspans[kNec], plans, w.ctr + 4, eval_only, grid, s);
   if (w.nspans[3] > 0 && e == cudaSuccess)
     e = launch_batch_stage(insts, w.spans[3], w.nspans[3], plans, w.ctr + 6, eval_only, grid, s);
+  if (w.nspans[4] > 0 && e == cudaSuccess)
+    e = launch_batch_flow(insts, w.spans[4], w.nspans[4], plans, w.ctr + 12, eval_only, grid, s);
   return e;
 }
 
@@ -372,10 +374,16 @@ cudaError_t launch_batch_rows(const BatchInst* insts, const BatchWork& w, const 
 cudaError_t launch_batch_generation(const BatchInst* insts, const BatchWork& w, const BatchTile* ptiles,
                                     int nptiles, RowPlan32* plans, DevState* states, int n_inst, int grid,
                                     cudaStream_t s) {
-  if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nspans[3] + w.nctiles <= 0) return cudaSuccess;
-  if (w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nctiles == 0 && batch_fused_supported())
+  const int reg = w.nspans[0] + w.nspans[1] + w.nspans[2] + w.nctiles;
+  if (reg + w.nspans[3] + w.nspans[4] <= 0) return cudaSuccess;
+  // one cooperative launch when every instance is on the staged kernel, or
+  // every instance on the streaming kernel
+  if (reg + w.nspans[4] == 0 && batch_fused_supported())
     return launch_batch_fused(insts, w.spans[3], w.nspans[3], ptiles, nptiles, plans, states, n_inst, w.ctr + 6,
                               grid, w.wait_ns, s);
+  if (reg + w.nspans[3] == 0 && batch_flow_fused_supported())
+    return launch_batch_flow_fused(insts, w.spans[4], w.nspans[4], ptiles, nptiles, plans, states, n_inst,
+                                   w.ctr + 12, grid, w.wait_ns, s);
   batch_plan_kernel<<<plan_grid(nptiles, grid), kBatchThreads, 0, s>>>(insts, ptiles, nptiles, plans);
   cudaError_t e = launch_spans(insts, w, plans, 0, grid, s);
   if (e != cudaSuccess) return e;

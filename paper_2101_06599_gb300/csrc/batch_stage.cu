@@ -363,39 +363,6 @@ __device__ __forceinline__ void flush(const GenParams& p, Cnt& c, int eval_only)
   c.accepts = 0u;
 }
 
-// Grid-wide barrier of a cooperative launch (every CTA resident): an arrival
-// counter and a sense word that flips once all CTAs have arrived. The wait is
-// bounded by limit_ns of %globaltimer; false if it gave up. Every CTA arrives
-// exactly once whether or not it gives up, so the last arrival always resets
-// the counter and flips the sense: both are ready for the next launch.
-__device__ bool grid_barrier(unsigned* count, unsigned* sense, unsigned nblocks, unsigned long long limit_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned s0 = atomicAdd(sense, 0u);
-    __threadfence();
-    if (atomicAdd(count, 1u) == nblocks - 1u) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicExch(sense, s0 ^ 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (atomicAdd(sense, 0u) == s0) {
-        if (global_ns() - t0 > limit_ns) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // ctr[0]: next span to take; ctr[1]: warps finished (the last one resets both).
 // FUSED (a whole generation in one cooperative launch, every instance on this
 // kernel): the plans of every row first (plan tiles of 256 rows, the NEC
@@ -419,41 +386,9 @@ batch_stage_kernel(const BatchInst* __restrict__ insts, const BatchSpan* __restr
   float4 nx[kPassVec];
   bool go = true;
   if constexpr (FUSED) {
-    uint32_t* tab = reinterpret_cast<uint32_t*>(smem_raw);   // the pass buffers are free until the rows
-    int cached = -1;
-    // a contiguous run of plan tiles per CTA (tiles are in instance order), so
-    // the instance's table is staged once or twice, not per tile
-    const int per = (nptiles + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int t_end = min(nptiles, ((int)blockIdx.x + 1) * per);
-    for (int tile = (int)blockIdx.x * per; tile < t_end; ++tile) {
-      const BatchTile tl = ptiles[tile];
-      const BatchInst& I = insts[tl.inst];
-      const bool tab_smem = (I.xo == kNec) && I.g.nT <= kBatchTableCap;
-      if (tl.inst != cached) {                       // uniform over the CTA
-        __syncthreads();
-        if (tab_smem)
-          for (int k = threadIdx.x; k < I.g.nT; k += kPwThreads) tab[k] = I.g.nec_tm1[k];
-        __syncthreads();
-        cached = tl.inst;
-      }
-      // two rows per thread: both rows' draws, then both rows' gathers, so the
-      // loads of the two are in flight together
-      static_assert(kBatchThreadsHost == 2 * kPwThreads, "two plan rows per thread");
-      const long long gen = I.g.st->gen;
-      const int i0 = tl.row0 + threadIdx.x, i1 = i0 + kPwThreads;
-      RowDraws d0, d1;
-      int L0 = 0, L1 = 0;
-      if (i0 < I.g.N) row_draws(I, gen, i0, tab_smem ? tab : nullptr, d0, L0);
-      if (i1 < I.g.N) row_draws(I, gen, i1, tab_smem ? tab : nullptr, d1, L1);
-      if (i0 < I.g.N) {
-        const RowPlan32 a = row_plan(I.g, gen, i0, d0, L0);
-        if (i1 < I.g.N) {
-          const RowPlan32 b2 = row_plan(I.g, gen, i1, d1, L1);
-          plans[I.row_base + i1] = b2;
-        }
-        plans[I.row_base + i0] = a;
-      }
-    }
+    // the pass buffers are free until the rows: the NEC tables go there
+    static_assert(kBatchThreadsHost == 2 * kPwThreads, "two plan rows per thread");
+    plan_phase<kPwThreads>(insts, ptiles, nptiles, plans, reinterpret_cast<uint32_t*>(smem_raw));
     go = grid_barrier(&ctr[2], &ctr[3], gridDim.x, wait_ns);
     if (!go && threadIdx.x == 0) atomicExch(&states[0].error, 4u);   // DE_ETIMEOUT
   }

@@ -64,8 +64,8 @@ struct de_ctx {
   std::vector<float> bF;
   std::vector<de_bounds> bb;
   de::BatchInst* d_insts = nullptr;
-  de::BatchSpan* d_spans[4] = {nullptr, nullptr, nullptr, nullptr};   // register kernel per crossover, staged
-  int nspans[4] = {0, 0, 0, 0};
+  de::BatchSpan* d_spans[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // register kernel per crossover, staged, streaming
+  int nspans[5] = {0, 0, 0, 0, 0};
   unsigned* d_span_ctr = nullptr;        // 2 queue counters per span list
   de::BatchTile* d_ctiles = nullptr;     // CTA tiles (G > 32)
   de::BatchTile* d_ptiles = nullptr;  // plan tiles: 256 rows of one instance

@@ -75,9 +75,9 @@ constexpr int kBatchMaxD4PerLane = 16;
 // their queue counters (2 per list, zero between launches) and the CTA tiles
 // of the instances with G > 32.
 struct BatchWork {
-  const BatchSpan* spans[4];   // register kernel for bin, exp, NEC; staged kernel (exp and NEC)
-  int nspans[4];
-  unsigned* ctr;               // 12 counters (2 per register list; 4 for the staged list)
+  const BatchSpan* spans[5];   // register kernel for bin, exp, NEC; staged kernel, streaming kernel (exp and NEC)
+  int nspans[5];
+  unsigned* ctr;               // 16 counters (2 per register list; 4 for the staged and the streaming lists)
   unsigned long long wait_ns;  // limit of the one-launch generation's grid barrier (0: 1 s)
   const BatchTile* ctiles;
   int nctiles;
@@ -107,6 +107,18 @@ bool batch_fused_supported();
 cudaError_t launch_batch_fused(const BatchInst* insts, const BatchSpan* spans, int nspans, const BatchTile* ptiles,
                                int nptiles, RowPlan32* plans, DevState* states, int n_inst, unsigned* ctr, int grid,
                                unsigned long long wait_ns, cudaStream_t s);
+// the streaming row kernel for exp / NEC rows of any D (batch_flow.cu)
+constexpr int kBatchFlow = 2;            // group value that selects it
+constexpr int kBatchLists = 5;           // span lists: register bin, exp, NEC; staged; streaming
+constexpr int kBatchCounters = 16;
+cudaError_t prepare_batch_flow();
+cudaError_t launch_batch_flow(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
+                              cudaStream_t);
+bool batch_flow_fused_supported();
+cudaError_t launch_batch_flow_fused(const BatchInst* insts, const BatchSpan* spans, int nspans,
+                                    const BatchTile* ptiles, int nptiles, RowPlan32* plans, DevState* states,
+                                    int n_inst, unsigned* ctr, int grid, unsigned long long wait_ns,
+                                    cudaStream_t s);
 // the span row kernel alone, one per crossover (batch_span_*.cu)
 cudaError_t launch_batch_span_bin(const BatchInst*, const BatchSpan*, int, const RowPlan32*, unsigned*, int, int,
                                   cudaStream_t);

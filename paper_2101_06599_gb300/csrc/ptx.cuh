@@ -97,5 +97,7 @@ __device__ __forceinline__ void ca16_g2s(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void ca_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void ca_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Every group but the most recently committed one complete.
+__device__ __forceinline__ void ca_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 }  // namespace de

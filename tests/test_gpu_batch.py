@@ -187,10 +187,10 @@ def test_batched_512_instance_workload_sampled():
 
 
 def test_batch_group_choice_is_bit_invariant():
-    """For rows of at most one warp (register tiles of G = 4 .. 32 lanes, or
-    the staged kernel) the fitness is summed in one order whatever the
-    kernel, so every valid choice gives the same fitness bits, selections and
-    trajectories."""
+    """For rows of at most one warp (register tiles of G = 4 .. 32 lanes, the
+    staged kernel, or the streaming kernel) the fitness is summed in one order
+    whatever the kernel, so every valid choice gives the same fitness bits,
+    selections and trajectories."""
     specs = []
     k = 0
     for D in (1, 3, 10, 64, 130, 257, 600, 1000, 2000):
@@ -199,10 +199,10 @@ def test_batch_group_choice_is_bit_invariant():
             specs.append(dict(N=37 + 3 * k, D=D, obj=obj, bounds=W.BOXES[obj], xo=xo, CR=0.9, F=0.5))
             k += 1
     ref = None
-    for G in (0, -4, -8, -16, -32, 4, 8, 16, 32):
+    for G in (0, -4, -8, -16, -32, 4, 8, 16, 32, 2):
         b = DE.Batch(specs, seed=11)
         try:
-            if G <= 0:          # the staged kernel with -G lanes per row for exp / NEC
+            if G <= 0 or G == 2:   # the staged kernel with -G lanes per row, or the streaming kernel (exp / NEC)
                 b.set_groups([G if sp["xo"] != "bin" else 0 for sp in specs])
             else:
                 b.set_groups([max(min_group(sp["D"]), G) for sp in specs])
@@ -226,8 +226,8 @@ def test_batch_groups_validation_and_defaults():
     default = [-32, -32, min_group(2049), min_group(300), min_group(5000)]
     try:
         assert b.groups() == default
-        for bad in ([1, 1, 1, 0, 0], [0, 0, 0, 1, 0], [0, 2, 0, 0, 0], [0, 0, 0, 12, 0], [0, 4, 0, 0, 0],
-                    [-2, 0, 0, 0, 0], [-64, 0, 0, 0, 0], [0, 0, -32, 0, 0], [0, 0, 0, -8, 0]):
+        for bad in ([1, 1, 1, 0, 0], [0, 0, 0, 1, 0], [0, 0, 0, 2, 0], [0, 0, 0, 0, 2], [0, 0, 0, 12, 0],
+                    [0, 4, 0, 0, 0], [-2, 0, 0, 0, 0], [-64, 0, 0, 0, 0], [0, 0, -32, 0, 0], [0, 0, 0, -8, 0]):
             with pytest.raises(DE.DEError):
                 b.set_groups(bad)
             assert b.groups() == default
@@ -237,6 +237,8 @@ def test_batch_groups_validation_and_defaults():
         assert b.groups() == [-8, -16, min_group(2049), min_group(300), min_group(5000)]
         b.set_groups([1, 1, 0, 0, 0])           # the staged kernel with its default lanes
         assert b.groups() == default
+        b.set_groups([2, 2, 2, 0, 0])           # the streaming kernel: exp / NEC rows of any D
+        assert b.groups() == [2, 2, 2, min_group(300), min_group(5000)]
         b.set_groups([0, 0, 0, 0, 0])
         assert b.groups() == default
     finally:
@@ -334,5 +336,85 @@ def test_batch_staged_edge_cases(CR):
                 check_instance_step(c, k, only_staged[k], 13)
         finally:
             c.close()
+    finally:
+        b.close()
+
+
+FLOW = 2                                  # the streaming row kernel's group value
+
+
+@pytest.mark.parametrize("CR", [0.9, 0.0, 1.0, 0.99])
+def test_batch_streaming_kernel_matches_oracle(CR):
+    """The streaming row kernel (one warp per row, chunks of 512 genes) on
+    every instance: one cooperative launch per generation, each instance's
+    generation against the oracle. Rows of one chunk and of several (D = 513, 1025,
+    2049, 5000 and 10000: the trial of an accepted row is re-read and stored
+    chunk by chunk), segments that wrap, Cr = 0 (L = 1), Cr = 1 (L = D) and
+    Cr = 0.99 (segments of more than 32 slots take the per-slot path), the
+    minimum N = 4, every objective."""
+    specs = []
+    for k, (N, D, xo) in enumerate([(4, 1, "nec"), (9, 3, "exp"), (40, 10, "nec"), (23, 129, "exp"),
+                                    (64, 1024, "nec"), (17, 1025, "nec"), (8, 513, "exp"), (6, 2049, "exp"), (5, 5000, "nec"),
+                                    (4, 10000, "nec"), (33, 777, "exp"), (12, 4097, "nec"), (50, 64, "nec")]):
+        obj = OBJS[k % len(OBJS)]
+        specs.append(dict(N=N, D=D, obj=obj, bounds=W.BOXES[obj], xo=xo, CR=CR, F=0.6))
+    b = DE.Batch(specs, seed=17)
+    try:
+        b.set_groups([FLOW] * len(specs))
+        assert b.groups() == [FLOW] * len(specs)
+        b.run(2)
+        for k in range(len(specs)):
+            check_instance_step(b, k, specs[k], 17)
+    finally:
+        b.close()
+
+
+def test_batch_streaming_one_launch_matches_multi_launch_and_staged():
+    """Every instance on the streaming kernel runs a generation as one
+    cooperative launch; moving one instance to register tiles switches the
+    batch to plan / rows / close launches, and the staged kernel sums in the
+    same order: all three trajectories are bit-identical."""
+    specs = []
+    for k, (D, xo) in enumerate([(10, "nec"), (100, "exp"), (600, "nec"), (2000, "nec"), (33, "exp"),
+                                 (1024, "nec"), (1500, "exp")]):
+        obj = OBJS[k % 4]
+        specs.append(dict(N=60 + 7 * k, D=D, obj=obj, bounds=W.BOXES[obj], xo=xo, CR=0.9, F=0.5))
+    runs = []
+    for mode in ("flow_fused", "flow_multi", "staged"):
+        b = DE.Batch(specs, seed=19)
+        try:
+            if mode == "flow_fused":
+                b.set_groups([FLOW] * len(specs))
+            elif mode == "flow_multi":
+                b.set_groups([min_group(specs[0]["D"])] + [FLOW] * (len(specs) - 1))
+            b.run(7)
+            runs.append([(b.population(k), b.stats(k)) for k in range(len(specs))])
+        finally:
+            b.close()
+    for k in range(len(specs)):
+        (p0, f0), s0 = runs[0][k]
+        for r in runs[1:]:
+            (p1, f1), s1 = r[k]
+            assert np.array_equal(p0.view(np.uint32), p1.view(np.uint32)), k
+            assert np.array_equal(f0.view(np.uint32), f1.view(np.uint32)), k
+            assert s0 == s1, k
+
+
+def test_batch_streaming_evaluation_matches_oracle():
+    """Parent evaluation (set_population without fitness) on the streaming
+    kernel: the FP32 fitness of every row within tolerance of the oracle."""
+    specs = [dict(N=30 + k, D=D, obj=OBJS[k % len(OBJS)], bounds=W.BOXES[OBJS[k % len(OBJS)]], xo="nec", CR=0.9,
+                  F=0.5) for k, D in enumerate([1, 7, 300, 1024, 1030, 3333])]
+    b = DE.Batch(specs, seed=23)
+    try:
+        b.set_groups([FLOW] * len(specs))
+        for k, s in enumerate(specs):
+            pop = W.population(s["N"], s["D"], *s["bounds"], 300 + k)
+            b.set_population(k, pop)
+            _, f = b.population(k)
+            f64 = O.evaluate(s["obj"], pop)
+            assert np.all(np.abs(f - f64) <= tol(f64)), k
+            x, fb, idx, _ = b.best(k)
+            assert idx == O.argmin(f) and fb == f[idx]
     finally:
         b.close()
