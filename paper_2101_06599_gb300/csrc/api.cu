@@ -326,7 +326,10 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   p.hi = b.hi;
   p.cr_mode = (CR <= 0.0) ? kCrZero : (CR >= 1.0 ? kCrOne : kCrGeneral);
   p.cr_t = (unsigned long long)std::ceil(CR * 4294967296.0);
+  p.cr_lt = (uint32_t)std::min<unsigned long long>(p.cr_t, 0xFFFFFFFFull);
+  p.cr_all = p.cr_t > 0xFFFFFFFFull ? 1 : 0;
   p.key = Key2{(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32)};
+  p.rk = philox_round_keys(p.key);
   p.inst = 0;
   p.ackley_b = (float)ackley_b;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
@@ -342,6 +345,11 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   cudaGetLastError();
   configure_pipe(c);
   resolve_kernel(c);
+  if (!c->rotated && prepare_gen_stream(c->xo, c->obj) != cudaSuccess) {
+    cudaGetLastError();
+    de_destroy(c);
+    return DE_ECUDA;
+  }
 
   DevState s0;
   std::memset(&s0, 0, sizeof(s0));

@@ -352,7 +352,10 @@ int de_batch_create(de_ctx** out, int32_t n_inst, const de_instance_spec* specs,
     p.hi = s.b.hi;
     p.cr_mode = (s.CR <= 0.0) ? kCrZero : (s.CR >= 1.0 ? kCrOne : kCrGeneral);
     p.cr_t = (unsigned long long)std::ceil(s.CR * 4294967296.0);
+    p.cr_lt = (uint32_t)std::min<unsigned long long>(p.cr_t, 0xFFFFFFFFull);
+    p.cr_all = p.cr_t > 0xFFFFFFFFull ? 1 : 0;
     p.key = Key2{(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32)};
+    p.rk = philox_round_keys(p.key);
     p.inst = (uint32_t)k;
     p.ackley_b = 0.2f;
     p.ell_k = (s.D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(s.D - 1)) : 0.0f;

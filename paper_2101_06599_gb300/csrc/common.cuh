@@ -63,6 +63,8 @@ struct GenParams {
   int cr_mode;
   int base;                 // base index rule (kBaseDistinct .. kBaseBest)
   unsigned long long cr_t;  // ceil(Cr * 2^32): rand < Cr  <=>  w < cr_t
+  uint32_t cr_lt;           // min(cr_t, 2^32 - 1): w < cr_lt as a 32-bit test when cr_all is 0
+  int cr_all;               // cr_t = 2^32: every word passes
   Key2 key;
   uint32_t inst;
   float ackley_b;
@@ -73,6 +75,7 @@ struct GenParams {
   float* dbg_ftrial;        // N
   uint8_t* dbg_accept;      // N
   int* dbg_draws;           // N x 5
+  RoundKeys rk;             // key's Philox round keys (kernels drawing a block per few genes)
 };
 
 // FP32 -> uint32 whose unsigned order is the float order; NaN maps above +inf.

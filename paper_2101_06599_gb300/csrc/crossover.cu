@@ -13,6 +13,7 @@
 // threshold table: L = 1 + #{n >= 1 : w < c_n 2^32} with c_1 = Cr and
 // c_n = fl(c_{n-1} Cr) in FP64 (a plain IEEE multiply, the same numbers the
 // table holds), counted until the first n that fails (c_n decreases).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -176,7 +177,10 @@ GenParams xo_params(int32_t N, int32_t D, double CR, uint64_t seed, uint32_t ins
   p.D4 = (D + 3) / 4;
   p.cr_mode = (CR <= 0.0) ? kCrZero : (CR >= 1.0 ? kCrOne : kCrGeneral);
   p.cr_t = (unsigned long long)std::ceil(CR * 4294967296.0);
+  p.cr_lt = (uint32_t)std::min<unsigned long long>(p.cr_t, 0xFFFFFFFFull);
+  p.cr_all = p.cr_t > 0xFFFFFFFFull ? 1 : 0;
   p.key = Key2{(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32)};
+  p.rk = philox_round_keys(p.key);
   p.inst = instance;
   return p;
 }

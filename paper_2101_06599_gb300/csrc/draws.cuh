@@ -190,6 +190,17 @@ __device__ __forceinline__ int nec_length(const GenParams& p, uint32_t g, int i)
   return nec_length_of<false>(p, nec_word(p, g, i), p.nec_tm1);
 }
 
+// Binomial mask bits of slot q (genes 4q .. 4q+3, bit e = gene 4q + e) from
+// the slot's BIN block w (Eq. 2): word e < ceil(Cr 2^32), and the gene j_rand
+// always. Padding genes are the caller's to clear.
+__device__ __forceinline__ unsigned bin_mask(const GenParams& p, const uint4 w, int q, int jrand) {
+  unsigned m = (w.x < p.cr_lt ? 1u : 0u) | (w.y < p.cr_lt ? 2u : 0u) | (w.z < p.cr_lt ? 4u : 0u) |
+               (w.w < p.cr_lt ? 8u : 0u);
+  if (p.cr_all) m = 0xFu;
+  if (q == (jrand >> 2)) m |= 1u << (jrand & 3);
+  return m;
+}
+
 // Alg. 8's continuation test for one EXP word: rand < Cr, i.e. w < ceil(Cr 2^32).
 __device__ __forceinline__ bool exp_continues(const GenParams& p, uint32_t w) {
   return (unsigned long long)w < p.cr_t;

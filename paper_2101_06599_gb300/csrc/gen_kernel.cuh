@@ -168,11 +168,7 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
       const int j0 = 4 * q;
       unsigned m = 0u;
       if constexpr (XO == kBin) {
-        const uint4 w = philox_block(p.key, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q);
-        m |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == jrand) ? 1u : 0u;
-        m |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == jrand) ? 2u : 0u;
-        m |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == jrand) ? 4u : 0u;
-        m |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == jrand) ? 8u : 0u;
+        m = bin_mask(p, philox_block_rk(p.rk, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q), q, jrand);
       } else {
         int dd = j0 - jrand;
         if (dd < 0) dd += p.D;                      // (j0 - j_rand) mod D

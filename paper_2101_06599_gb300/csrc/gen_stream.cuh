@@ -8,7 +8,9 @@
 // registers. The warp reduces them, selects (strict '<', NaN as +inf), and
 // only a row that wins recomputes its trial in pass 2 and stores it to the
 // other slot buffer; donors are never written during a generation, so pass 2
-// reproduces pass 1 exactly. This suits the binomial crossover at large D:
+// reproduces pass 1 exactly. Binomial masks (one Philox block per slot) are
+// kept in shared memory by pass 1, one byte per slot of the warp's row, so
+// pass 2 reads them instead of drawing them again. This suits the binomial crossover at large D:
 // nearly every donor gene is needed (m ~ Cr), so the row-per-CTA kernel's
 // registers hold four rows' worth of loads per row and few rows fit per SM,
 // while here 16 rows per SM stream with all their loads in flight.
@@ -31,9 +33,11 @@ struct StreamRow {
 };
 
 // The trial slots q = q0 + lane + 32 u of row r; m[u] gets the mask bits.
-template <int XO>
+// Binomial: the masks are drawn and written to mc[q] (pass 1, kCached false)
+// or read back from it (pass 2).
+template <int XO, bool kCached>
 __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const StreamRow& r, int q0, int lane,
-                                                   float4 (&v)[kStreamU], unsigned (&m)[kStreamU]) {
+                                                   float4 (&v)[kStreamU], unsigned (&m)[kStreamU], uint8_t* mc) {
 #pragma unroll
   for (int u = 0; u < kStreamU; ++u) {
     const int q = q0 + lane + 32 * u;
@@ -45,12 +49,10 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
     unsigned mm = 0u;
     if (q < p.D4) {
       const int j0 = 4 * q;
-      if constexpr (XO == kBin) {
-        const uint4 w = philox_block(p.key, kStreamBin, p.inst, r.g, (uint32_t)r.i, (uint32_t)q);
-        mm |= ((unsigned long long)w.x < p.cr_t || j0 + 0 == r.jrand) ? 1u : 0u;
-        mm |= ((unsigned long long)w.y < p.cr_t || j0 + 1 == r.jrand) ? 2u : 0u;
-        mm |= ((unsigned long long)w.z < p.cr_t || j0 + 2 == r.jrand) ? 4u : 0u;
-        mm |= ((unsigned long long)w.w < p.cr_t || j0 + 3 == r.jrand) ? 8u : 0u;
+      if constexpr (XO == kBin && kCached) {
+        mm = mc[q];
+      } else if constexpr (XO == kBin) {
+        mm = bin_mask(p, philox_block_rk(p.rk, kStreamBin, p.inst, r.g, (uint32_t)r.i, (uint32_t)q), q, r.jrand);
       } else {
         int dd = j0 - r.jrand;
         if (dd < 0) dd += p.D;                      // (j0 - j_rand) mod D
@@ -62,6 +64,7 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
         }
       }
       mm &= (1u << min(4, p.D - j0)) - 1u;          // padding genes never cross
+      if constexpr (XO == kBin && !kCached) mc[q] = (uint8_t)mm;
     }
     m[u] = mm;
   }
@@ -91,14 +94,15 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
 // chains) reduced over the warp; every lane returns the value (NaN as +inf).
 // cnt gets the binomial mask's popcount. Writes the trial to p.dbg_trial when set.
 template <int XO, int OBJ>
-__device__ __forceinline__ float stream_row_value(const GenParams& p, const StreamRow& r, int lane, int& cnt) {
+__device__ __forceinline__ float stream_row_value(const GenParams& p, const StreamRow& r, int lane, int& cnt,
+                                                  uint8_t* mc) {
   Acc s{0.0f, 0.0f, 0.0f}, s2{0.0f, 0.0f, 0.0f};
   cnt = 0;
   float carry = 0.0f;                              // Rosenbrock: last gene of the previous chunk
   for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
     float4 v[kStreamU];
     unsigned m[kStreamU];
-    stream_trial_chunk<XO>(p, r, q0, lane, v, m);
+    stream_trial_chunk<XO, false>(p, r, q0, lane, v, m, mc);
     if (p.dbg_trial) {
       float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)r.i * p.pitch);
 #pragma unroll
@@ -153,11 +157,12 @@ __device__ __forceinline__ float stream_row_value(const GenParams& p, const Stre
 
 // Pass 2 of a winning row: its trial again, chunk by chunk, stored to `out`.
 template <int XO>
-__device__ __forceinline__ void stream_row_store(const GenParams& p, const StreamRow& r, int lane, float4* out) {
+__device__ __forceinline__ void stream_row_store(const GenParams& p, const StreamRow& r, int lane, float4* out,
+                                                 uint8_t* mc) {
   for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
     float4 v[kStreamU];
     unsigned m[kStreamU];
-    stream_trial_chunk<XO>(p, r, q0, lane, v, m);
+    stream_trial_chunk<XO, true>(p, r, q0, lane, v, m, mc);
 #pragma unroll
     for (int u = 0; u < kStreamU; ++u) {
       const int q = q0 + lane + 32 * u;
@@ -171,7 +176,9 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
   __shared__ unsigned long long s_key[kStreamWarps];
   __shared__ int s_cnt[kStreamWarps];
   __shared__ int s_acc[kStreamWarps];
+  extern __shared__ uint8_t s_masks[];             // binomial: D4 mask bytes per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* mc = (XO == kBin) ? s_masks + (size_t)warp * p.D4 : nullptr;
   const int i = blockIdx.x * kStreamWarps + warp;
   const long long gen = p.st->gen;
   const uint32_t g = (uint32_t)gen;
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
     r.d3 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd3, 0));
 
     int cnt = 0;
-    const float f = stream_row_value<XO, OBJ>(p, r, lane, cnt);
+    const float f = stream_row_value<XO, OBJ>(p, r, lane, cnt, mc);
     acc = (f < p.fit[i]) ? 1 : 0;
     __syncwarp();                                    // every lane has read fit[i] before lane 0 writes it
     Lrow = (XO == kBin) ? cnt : r.L;
@@ -221,7 +228,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
       key = best_key_of(f, i);
       // pass 2: the winning trial again, into the other slot buffer
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
-      stream_row_store<XO>(p, r, lane, out);
+      __syncwarp();                                  // every lane's mask bytes are written
+      stream_row_store<XO>(p, r, lane, out, mc);
     }
   }
   if (lane == 0) {
@@ -261,11 +269,36 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
   }
 }
 
+// Dynamic shared memory of a launch: the binomial mask bytes, kStreamWarps x
+// D4 (at most 64 KB, D <= 32768; prepare_stream_obj allows that much).
+constexpr int kStreamMaskSmemMax = kStreamWarps * 8192;
+
+template <int XO, int OBJ>
+cudaError_t prepare_stream_obj() {
+  if (XO != kBin) return cudaSuccess;
+  return cudaFuncSetAttribute(gen_stream_kernel<XO, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kStreamMaskSmemMax);
+}
+
 template <int XO, int OBJ>
 cudaError_t launch_stream_obj(const GenParams& p, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.N + kStreamWarps - 1) / kStreamWarps);
-  gen_stream_kernel<XO, OBJ><<<grid, kStreamWarps * 32, 0, s>>>(p);
+  const size_t smem = (XO == kBin) ? (size_t)kStreamWarps * (size_t)p.D4 : 0;
+  gen_stream_kernel<XO, OBJ><<<grid, kStreamWarps * 32, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int XO>
+cudaError_t prepare_stream_xo(int obj) {
+  switch (obj) {
+    case kSphere: return prepare_stream_obj<XO, kSphere>();
+    case kRastrigin: return prepare_stream_obj<XO, kRastrigin>();
+    case kAckley: return prepare_stream_obj<XO, kAckley>();
+    case kRosenbrock: return prepare_stream_obj<XO, kRosenbrock>();
+    case kGriewank: return prepare_stream_obj<XO, kGriewank>();
+    case kElliptic: return prepare_stream_obj<XO, kElliptic>();
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int XO>

@@ -10,6 +10,7 @@ namespace de {
 // kVecChoices (float4 slots per thread: 1, 2, 4, 8, 16).
 cudaError_t launch_gen_bin(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
 cudaError_t launch_gen_stream(int xo, int obj, const GenParams& p, cudaStream_t s);
+cudaError_t prepare_gen_stream(int xo, int obj);
 cudaError_t launch_gen_exp(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
 cudaError_t launch_gen_nec(int obj, int vidx, const GenParams& p, int block, cudaStream_t s);
 
@@ -42,7 +43,7 @@ cudaError_t launch_gen_pipe(int xo, int obj, const PipeParams& pp, int grid, int
 
 // Batched instances (batch_kernel.cu): one descriptor per instance and a
 // tile list; a tile is 256 / group rows of one instance.
-struct BatchInst {
+struct alignas(16) BatchInst {  // copied into shared memory 16 bytes at a time
   GenParams g;
   int obj, xo;
   int group;                 // lanes per row of the register kernels, or kBatchStaged

@@ -19,6 +19,7 @@
 // dependent FP64 products on one thread. Calls that overlap on the GPU (two
 // streams, or two host threads) race on the array and must be serialised by
 // the caller.
+#include <algorithm>
 #include <cmath>
 
 #include "../../include/de.h"
@@ -161,7 +162,10 @@ extern "C" int de_nec_step_noalloc(const float* pop_in, const float* fit_in, flo
   p.hi = b.hi;
   p.cr_mode = (CR <= 0.0) ? kCrZero : (CR >= 1.0 ? kCrOne : kCrGeneral);
   p.cr_t = (unsigned long long)std::ceil(CR * 4294967296.0);
+  p.cr_lt = (uint32_t)std::min<unsigned long long>(p.cr_t, 0xFFFFFFFFull);
+  p.cr_all = p.cr_t > 0xFFFFFFFFull ? 1 : 0;
   p.key = Key2{(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32)};
+  p.rk = philox_round_keys(p.key);
   p.inst = 0;
   p.ackley_b = 0.2f;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;

@@ -445,3 +445,25 @@ def test_best_async_record_matches_best():
         assert fs[0] >= fs[1] >= fs[2]
     finally:
         opt.close()
+
+
+@pytest.mark.parametrize("kernel", [1, 3])
+@pytest.mark.parametrize("CR", [1.0 - 2.0**-40, 2.0**-33, 0.5, 1.0 - 2.0**-32])
+def test_binomial_threshold_extremes(kernel, CR):
+    """The binomial test w < ceil(Cr 2^32) at the ends of its range, on the
+    row-per-CTA kernel (1) and the streaming kernel (3): Cr within 2^-32 of
+    1 makes the threshold 2^32 (every word passes, the 32-bit comparison
+    cannot say so), Cr = 2^-33 makes it 1 (only the word 0 passes), Cr = 0.5
+    is a power of two. Masks, trials and selections against the oracle."""
+    F, seed, obj = 0.6, 29, "sphere"
+    for (N, D) in ((40, 130), (9, 1001)):
+        opt, lo, hi = make(N, D, "bin", obj, CR=CR, F=F, seed=seed)
+        try:
+            opt.set_kernel(kernel)
+            s, acc, _ = one_step_parity(opt, lo, hi, "bin", obj, F, CR, seed)
+            if CR > 1.0 - 2.0**-32:
+                assert np.all(s.L == D)
+            if CR < 2.0**-32:
+                assert np.all(s.L <= 2)                # j_rand, and a word 0 with probability 2^-32 per gene
+        finally:
+            opt.close()
