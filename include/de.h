@@ -95,9 +95,16 @@ typedef enum { DE_PREC_FP32 = 0, DE_PREC_TF32 = 1, DE_PREC_BF16 = 2 } de_precisi
 typedef enum { DE_BOUND_PROBABILISTIC = 0, DE_BOUND_WORST_CASE = 1 } de_bound_kind;
 
 /* Search box, the same for every dimension (Section 4 gives one interval
- * per function). Requires lo < hi, both finite. Trial genes are clipped to
- * [lo, hi] (bound repair; the paper names none). */
+ * per function). Requires lo < hi, both finite. Mutant genes outside it are
+ * repaired (de_repair; the paper names no rule). */
 typedef struct { float lo, hi; } de_bounds;
+
+/* Bound repair of a mutant gene v outside [lo, hi], the paper being silent:
+ * CLIP sets it to the violated bound; MIDPOINT to the midpoint between the
+ * violated bound and the target (parent) gene x of the same row and column,
+ * fl(fl(bound + x) 0.5) in FP32, which lies in the box because x does. Only
+ * genes the crossover takes from the mutant are repaired. */
+typedef enum { DE_REPAIR_CLIP = 0, DE_REPAIR_MIDPOINT = 1 } de_repair;
 
 /* Optional objective parameters; pass NULL for the defaults. */
 typedef struct {
@@ -111,6 +118,7 @@ typedef struct {
   double margin_sigmas;     /* PROBABILISTIC bound: margin in standard deviations (0 selects
                                8; the model's failure probability per decision is at most
                                2 exp(-m^2 / 2))                                             */
+  de_repair repair;         /* bound repair (CLIP when zero); batched instances always clip  */
 } de_objparams;
 
 /* Counters kept on the device and read by de_stats. */
@@ -254,6 +262,16 @@ int de_debug_step(de_ctx *ctx, float *trial_out, float *ftrial_out,
  * DE_EINVAL for n < 0, a NULL `words` with n > 0 or an invalid `inst`. */
 int de_debug_lengths(de_ctx *ctx, int32_t inst, const uint32_t *words, int32_t n,
                      int32_t *L_global, int32_t *L_shared, uint8_t *exp_continue);
+
+/* Test hook: the crossover mask (Eq. 2, Alg. 8, Alg. 9) that the next
+ * generation of the context (instance `inst` of a batch; 0 for a single
+ * population) uses: mask_out (host, N x D bytes, row-major) gets 1 where
+ * gene j of row i is taken from the mutant, 0 where it is the parent's.
+ * Computed by the draw functions of the generation kernels (j_rand from the
+ * row's IDX block under the base rule in force, L from Eq. (9) or Alg. 8,
+ * the binomial words from the row's BIN blocks); the population is not
+ * touched. Synchronises. DE_EINVAL for a NULL mask_out or an invalid inst. */
+int de_debug_mask(de_ctx *ctx, int32_t inst, uint8_t *mask_out);
 
 /* ---- batched instances --------------------------------------------------- */
 /* One independent DE problem of a batch. */

@@ -83,7 +83,7 @@ def lib():
         L.or_step.restype = C.c_int
         L.or_argmin.argtypes = [C.c_int32, C.c_void_p]
         L.or_argmin.restype = C.c_int32
-        L.or_step_base.argtypes = L.or_step.argtypes + [C.c_int, C.c_int32]
+        L.or_step_base.argtypes = L.or_step.argtypes + [C.c_int, C.c_int32, C.c_int]
         L.or_step_base.restype = C.c_int
         L.or_donors_base.argtypes = [C.c_int32, C.c_int32, C.c_uint64, C.c_uint32, C.c_int64, C.c_int32,
                                      C.c_int, C.c_int32, C.c_void_p, C.c_void_p]
@@ -126,6 +126,7 @@ def donors(N, D, seed, g, i, inst=0):
 
 
 BASE = {"distinct": 0, "random": 1, "offset": 2, "permutation": 3, "best": 4}
+REPAIR = {"clip": 0, "midpoint": 1}
 
 
 def donors_base(N, D, seed, g, i, base, best=0, inst=0):
@@ -212,10 +213,12 @@ class StepResult:
 
 
 def step(pop, fit, F, Cr, xo, obj, lo, hi, seed, g, inst=0, ackley_b=0.2,
-         shift=None, rot=None, rows=None, want_trial=True, want_mask=False, base="distinct", best=None):
+         shift=None, rot=None, rows=None, want_trial=True, want_mask=False, base="distinct", best=None,
+         repair="clip"):
     """One generation of Alg. 1 (rows `rows` = (i0, i1), default all) with a
-    base index rule; `best` (the best row at the start of the generation, for
-    the "best" rule) defaults to the argmin of `fit`."""
+    base index rule and a bound repair ("clip" or "midpoint"); `best` (the best
+    row at the start of the generation, for the "best" rule) defaults to the
+    argmin of `fit`."""
     pop = _f32(pop)
     fit = np.ascontiguousarray(fit, dtype=np.float64)
     N, D = pop.shape
@@ -235,7 +238,8 @@ def step(pop, fit, F, Cr, xo, obj, lo, hi, seed, g, inst=0, ackley_b=0.2,
                             float(lo), float(hi), int(seed), int(inst), int(g), float(ackley_b),
                             _ptr(shift), _ptr(rot), _ptr(pop), _ptr(fit), _ptr(pop_out), _ptr(fit_out),
                             i0, i1, _ptr(draws), _ptr(trial), _ptr(ftrial), _ptr(accept), _ptr(msk),
-                            BASE[base] if isinstance(base, str) else int(base), int(best))
+                            BASE[base] if isinstance(base, str) else int(base), int(best),
+                            REPAIR[repair] if isinstance(repair, str) else int(repair))
     if rc != 0:
         raise ValueError("oracle step rejected its arguments")
     return StepResult(pop_out, fit_out, draws, trial, ftrial, accept.astype(bool), msk)

@@ -27,7 +27,8 @@
  *  - random words: Philox4x32-10 with counter (block, i, g, stream<<24|inst)
  *    and key (seed lo, seed hi); rand(0,1) = w / 2^32 compared in FP64;
  *  - randint(m) = (w * m) >> 32 (multiply-shift, no rejection);
- *  - bound repair: clip to [lo, hi] (the paper names none);
+ *  - bound repair (the paper names none): clip to [lo, hi], or the midpoint
+ *    between the violated bound and the target gene;
  *  - NaN fitness counts as +inf; ties keep the parent (strict '<', Alg. 1);
  *  - Alg. 10's mask formula as printed never wraps; the segment of Alg. 9
  *    (circular, starting at j_rand) is used instead.
@@ -405,6 +406,24 @@ void or_init(int32_t N, int32_t D, float lo, float hi, uint64_t seed,
     }
 }
 
+/* Bound repair of a mutant gene v whose target gene is x (x in the box):
+ * mode 0 clips to the violated bound; mode 1 takes the midpoint of that bound
+ * and x, (bound + x) / 2 with each operation rounded once in FP32. */
+static float repair_gene(float v, float x, float lo, float hi, int mode)
+{
+  if (v < lo) {
+    if (!mode) return lo;
+    float t = lo + x;
+    return t * 0.5f;
+  }
+  if (v > hi) {
+    if (!mode) return hi;
+    float t = hi + x;
+    return t * 0.5f;
+  }
+  return v;
+}
+
 static int fit_less(double a, double b)
 {
   /* strict '<' with NaN read as +inf */
@@ -434,7 +453,7 @@ int or_step(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
 {
   return or_step_base(N, D, F, Cr, xo, obj, lo, hi, seed, inst, g, ackley_b, shift, rot,
                       pop_in, fit_in, pop_out, fit_out, i0, i1, draws, trial, ftrial,
-                      accept, mask_out, OR_BASE_DISTINCT, 0);
+                      accept, mask_out, OR_BASE_DISTINCT, 0, 0);
 }
 
 int or_step_base(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
@@ -443,9 +462,10 @@ int or_step_base(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
                  const float *pop_in, const double *fit_in,
                  float *pop_out, double *fit_out, int32_t i0, int32_t i1,
                  int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
-                 uint8_t *mask_out, int base, int32_t best)
+                 uint8_t *mask_out, int base, int32_t best, int repair)
 {
   if (N < 4 || D < 1 || i0 < 0 || i1 > N || i0 > i1) return -1;
+  if (repair != 0 && repair != 1) return -1;
   if (base < OR_BASE_DISTINCT || base > OR_BASE_BEST || best < 0 || best >= N) return -1;
   if (!(Cr >= 0.0 && Cr <= 1.0)) return -1;
   if (xo < OR_XO_BIN || xo > OR_XO_NEC) return -1;
@@ -472,7 +492,7 @@ int or_step_base(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
       float diff = x2[j] - x3[j];
       float scaled = F * diff;
       float vj = x1[j] + scaled;
-      v[j] = clip(vj, lo, hi);
+      v[j] = repair_gene(vj, xi[j], lo, hi, repair);
     }
 
     /* recombination: u starts as x_i; masked genes come from v */

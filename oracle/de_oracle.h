@@ -113,14 +113,16 @@ int or_step(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
             int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
             uint8_t *mask);
 
-/* or_step with a base index rule; `best` is read by OR_BASE_BEST only. */
+/* or_step with a base index rule (`best` is read by OR_BASE_BEST only) and a
+ * bound repair: 0 clips a mutant gene outside [lo, hi] to the violated
+ * bound, 1 takes the midpoint between that bound and the target gene. */
 int or_step_base(int32_t N, int32_t D, float F, double Cr, int xo, int obj,
                  float lo, float hi, uint64_t seed, uint32_t inst, int64_t g,
                  double ackley_b, const float *shift, const float *rot,
                  const float *pop_in, const double *fit_in,
                  float *pop_out, double *fit_out, int32_t i0, int32_t i1,
                  int32_t *draws, float *trial, double *ftrial, uint8_t *accept,
-                 uint8_t *mask, int base, int32_t best);
+                 uint8_t *mask, int base, int32_t best, int repair);
 
 /* Argmin of fit[0..N) with the lowest index winning ties; NaN counts as +inf. */
 int32_t or_argmin(int32_t N, const double *fit);

@@ -213,7 +213,7 @@ struct SaveHeader {
   double CR, ackley_b;
   int32_t xo, obj;
   uint64_t seed;
-  uint32_t inst, pad1;
+  uint32_t inst, repair;       // repair: 0 in checkpoints written before the field (clip)
   DevState st;
 };
 
@@ -265,6 +265,11 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
     if (!std::isfinite(prm->margin_sigmas) || prm->margin_sigmas < 0.0) return DE_EINVAL;
     if (prm->prec != DE_PREC_FP32 && prm->prec != DE_PREC_BF16) return DE_EUNSUPPORTED;
     if (prm->prec == DE_PREC_BF16 && !sr_tc_supported(D)) return DE_EUNSUPPORTED;
+  }
+  int repair = DE_REPAIR_CLIP;
+  if (prm) {
+    if (prm->repair != DE_REPAIR_CLIP && prm->repair != DE_REPAIR_MIDPOINT) return DE_EINVAL;
+    repair = (int)prm->repair;
   }
   double ackley_b = 0.2;
   if (prm && prm->ackley_b != 0.0) {
@@ -334,6 +339,7 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
   p.ackley_b = (float)ackley_b;
   p.ell_k = (D > 1) ? (float)(6.0 * std::log2(10.0) / (double)(D - 1)) : 0.0f;
   p.nec_k = nec_guess_factor(CR);
+  p.repair = repair;
 
   c->rotated = is_rotated(obj);
   int dev = 0;
@@ -564,6 +570,7 @@ int de_save(de_ctx* c, void* buf, size_t* len) {
   h.obj = c->obj;
   h.seed = c->seed;
   h.inst = c->inst;
+  h.repair = (uint32_t)c->p.repair;
   int rc = de_get_population(c, reinterpret_cast<float*>(o + sizeof(SaveHeader)),
                              reinterpret_cast<float*>(o + sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float)));
   if (rc != DE_OK) return rc;
@@ -587,7 +594,8 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
   const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
   if (h.magic != kSaveMagic || h.version != kSaveVersion || len < need) return DE_EINVAL;
   if (h.N != c->N || h.D != c->D || h.F != c->F || h.CR != c->CR || h.xo != c->xo || h.obj != c->obj ||
-      h.lo != c->b.lo || h.hi != c->b.hi || h.seed != c->seed || h.inst != c->inst || h.ackley_b != c->ackley_b)
+      h.lo != c->b.lo || h.hi != c->b.hi || h.seed != c->seed || h.inst != c->inst || h.ackley_b != c->ackley_b ||
+      h.repair != (uint32_t)c->p.repair)
     return DE_EINVAL;
   if (h.st.gen < 0 || h.st.best_gen < 0 || h.st.best_gen > h.st.gen ||
       (h.st.best_key & 0xFFFFFFFFull) >= (unsigned long long)c->N)
@@ -678,6 +686,22 @@ int de_debug_lengths(de_ctx* c, int32_t inst, const uint32_t* words, int32_t n, 
   if (dg) ctx_free(c, dg);
   if (ds) ctx_free(c, ds);
   if (de) ctx_free(c, de);
+  return rc;
+}
+
+int de_debug_mask(de_ctx* c, int32_t inst, uint8_t* mask_out) {
+  if (!c || !mask_out) return DE_EINVAL;
+  if (c->batch ? (inst < 0 || inst >= c->n_inst) : inst != 0) return DE_EINVAL;
+  const GenParams& p = c->batch ? c->bp[inst] : c->p;
+  const int xo = c->batch ? c->bxo[inst] : c->xo;
+  const size_t bytes = (size_t)p.N * (size_t)p.D;
+  uint8_t* dm = (uint8_t*)ctx_alloc(c, bytes);
+  if (!dm) return DE_ENOMEM;
+  cudaError_t e = launch_debug_mask(p, xo, dm, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mask_out, dm, bytes, cudaMemcpyDeviceToHost, c->stream);
+  const int rc = (e == cudaSuccess) ? sync_stream(c) : DE_ECUDA;
+  if (rc != DE_OK) cudaStreamSynchronize(c->stream);
+  ctx_free(c, dm);
   return rc;
 }
 

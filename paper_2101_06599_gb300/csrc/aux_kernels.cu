@@ -30,6 +30,51 @@ __global__ void debug_lengths_kernel(const __grid_constant__ GenParams p, const 
   }
 }
 
+// Test hook: the crossover mask of every row for the generation the context
+// is at (the one the next step makes), from the draw functions the
+// generation kernels use: j_rand from the row's IDX block, L from the NEC
+// lookup or Alg. 8's walk, the binomial bits from the row's BIN blocks. One
+// warp per row; mask is N x D bytes, 1 where gene j crosses.
+__global__ void debug_mask_kernel(const __grid_constant__ GenParams p, int xo, uint8_t* __restrict__ mask) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+  const uint32_t g = (uint32_t)p.st->gen;
+  for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < p.N; i += warps) {
+    int jrand = 0, L = 0;
+    if (lane == 0) {
+      RowDraws d;
+      draw_donors(p, g, i, d);
+      jrand = d.jrand;
+      if (xo == kNec) L = nec_length(p, g, i);
+      else if (xo == kExp) L = exp_walk_length(p, g, i);
+    }
+    jrand = __shfl_sync(0xFFFFFFFFu, jrand, 0);
+    L = __shfl_sync(0xFFFFFFFFu, L, 0);
+    for (int q = lane; q < p.D4; q += 32) {
+      const int j0 = 4 * q;
+      unsigned m = 0u;
+      if (xo == kBin) {
+        m = bin_mask(p, philox_block_rk(p.rk, kStreamBin, p.inst, g, (uint32_t)i, (uint32_t)q), q, jrand);
+      } else {
+        int dd = j0 - jrand;
+        if (dd < 0) dd += p.D;
+        for (int e = 0; e < 4; ++e) {
+          int de = dd + e;
+          if (de >= p.D) de -= p.D;
+          m |= (de < L) ? (1u << e) : 0u;
+        }
+      }
+      for (int e = 0; e < 4 && j0 + e < p.D; ++e) mask[(size_t)i * p.D + j0 + e] = (uint8_t)((m >> e) & 1u);
+    }
+  }
+}
+
+cudaError_t launch_debug_mask(const GenParams& p, int xo, uint8_t* mask, cudaStream_t s) {
+  const int grid = std::max(1, std::min(4096, (p.N + 7) / 8));
+  debug_mask_kernel<<<grid, 256, 0, s>>>(p, xo, mask);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_debug_lengths(const GenParams& p, const uint32_t* words, int n, int* L_global, int* L_shared,
                                  uint8_t* exp_cont, cudaStream_t s) {
   const int grid = std::max(1, std::min(1024, (n + 255) / 256));

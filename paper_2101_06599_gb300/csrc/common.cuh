@@ -62,6 +62,7 @@ struct GenParams {
   float F, lo, hi;
   int cr_mode;
   int base;                 // base index rule (kBaseDistinct .. kBaseBest)
+  int repair;               // bound repair: 0 clip, 1 midpoint between the violated bound and the target
   unsigned long long cr_t;  // ceil(Cr * 2^32): rand < Cr  <=>  w < cr_t
   uint32_t cr_lt;           // min(cr_t, 2^32 - 1): w < cr_lt as a 32-bit test when cr_all is 0
   int cr_all;               // cr_t = 2^32: every word passes
@@ -120,6 +121,15 @@ __device__ __forceinline__ float& lane_of(float4& v, int e) {
 // Bound repair: clip to [lo, hi] (exact).
 __device__ __forceinline__ float clip_box(float v, float lo, float hi) {
   return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Bound repair of a mutant gene v whose target (parent) gene is x, itself in
+// the box: clip to [lo, hi], or (repair = 1) the midpoint between the
+// violated bound and x, fl(fl(bound + x) 0.5), which stays in the box.
+__device__ __forceinline__ float repair_gene(float v, float x, const GenParams& p) {
+  if (v < p.lo) return p.repair ? __fmul_rn(__fadd_rn(p.lo, x), 0.5f) : p.lo;
+  if (v > p.hi) return p.repair ? __fmul_rn(__fadd_rn(p.hi, x), 0.5f) : p.hi;
+  return v;
 }
 
 // Eq. (1) for one gene, each operation rounded once: x1 + F (x2 - x3).

@@ -244,7 +244,7 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
         } else {
           a1 = __ldg(m.dsrc[0] + j); a2 = __ldg(m.dsrc[1] + j); a3 = __ldg(m.dsrc[2] + j);
         }
-        row[j] = clip_box(mutate(a1, a2, a3, p.F), p.lo, p.hi);
+        row[j] = repair_gene(mutate(a1, a2, a3, p.F), row[j], p);
       }
       for (int j = ct; j < wrap; j += NC) {
         patched = true;
@@ -255,7 +255,7 @@ gen_pipe_kernel(const __grid_constant__ PipeParams pp) {
         } else {
           a1 = __ldg(m.dsrc[0] + j); a2 = __ldg(m.dsrc[1] + j); a3 = __ldg(m.dsrc[2] + j);
         }
-        row[j] = clip_box(mutate(a1, a2, a3, p.F), p.lo, p.hi);
+        row[j] = repair_gene(mutate(a1, a2, a3, p.F), row[j], p);
       }
       if (patched) fence_proxy_async_smem();      // patches precede the stage's next bulk fill
       named_bar_sync(2, NC);                      // patched genes visible to every consumer

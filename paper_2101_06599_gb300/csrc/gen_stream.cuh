@@ -81,10 +81,10 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
 #pragma unroll
   for (int u = 0; u < kStreamU; ++u) {
     if (m[u]) {
-      if (m[u] & 1u) v[u].x = clip_box(mutate(a1[u].x, a2[u].x, a3[u].x, p.F), p.lo, p.hi);
-      if (m[u] & 2u) v[u].y = clip_box(mutate(a1[u].y, a2[u].y, a3[u].y, p.F), p.lo, p.hi);
-      if (m[u] & 4u) v[u].z = clip_box(mutate(a1[u].z, a2[u].z, a3[u].z, p.F), p.lo, p.hi);
-      if (m[u] & 8u) v[u].w = clip_box(mutate(a1[u].w, a2[u].w, a3[u].w, p.F), p.lo, p.hi);
+      if (m[u] & 1u) v[u].x = repair_gene(mutate(a1[u].x, a2[u].x, a3[u].x, p.F), v[u].x, p);
+      if (m[u] & 2u) v[u].y = repair_gene(mutate(a1[u].y, a2[u].y, a3[u].y, p.F), v[u].y, p);
+      if (m[u] & 4u) v[u].z = repair_gene(mutate(a1[u].z, a2[u].z, a3[u].z, p.F), v[u].z, p);
+      if (m[u] & 8u) v[u].w = repair_gene(mutate(a1[u].w, a2[u].w, a3[u].w, p.F), v[u].w, p);
     }
   }
 }

@@ -30,6 +30,8 @@ cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s
 // Move every row held in slot buffer 1 to slot buffer 0 and clear its slot
 // bit, so that buffer 0 holds the whole population.
 cudaError_t launch_normalize(const GenParams& p, cudaStream_t s);
+// Test hook: the N x D crossover mask of the generation the context is at.
+cudaError_t launch_debug_mask(const GenParams& p, int xo, uint8_t* mask, cudaStream_t s);
 // Test hook: L of Eq. (9) (table in global and in shared memory) and Alg. 8's
 // continuation test for n caller-given words (device arrays).
 cudaError_t launch_debug_lengths(const GenParams& p, const uint32_t* words, int n, int* L_global, int* L_shared,

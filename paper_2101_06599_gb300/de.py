@@ -22,6 +22,7 @@ OBJECTIVE = {"sphere": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "griewan
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
 BOUND = {"probabilistic": 0, "worst_case": 1}
 BASE = {"distinct": 0, "random": 1, "offset": 2, "permutation": 3, "best": 4}
+REPAIR = {"clip": 0, "midpoint": 1}
 
 
 class DEError(RuntimeError):
@@ -37,7 +38,7 @@ class de_bounds(C.Structure):
 class de_objparams(C.Structure):
     _fields_ = [("ackley_b", C.c_double), ("shift", C.c_void_p), ("rotation", C.c_void_p),
                 ("prec", C.c_int), ("incumbent_every", C.c_int32), ("bound", C.c_int),
-                ("margin_sigmas", C.c_double)]
+                ("margin_sigmas", C.c_double), ("repair", C.c_int)]
 
 
 class de_stats_t(C.Structure):
@@ -93,6 +94,7 @@ def load_library(build_if_missing: bool = True):
         "de_load": ([vp, vp, C.c_size_t], C.c_int),
         "de_debug_step": ([vp, vp, vp, vp, vp], C.c_int),
         "de_debug_lengths": ([vp, i32, vp, i32, vp, vp, vp], C.c_int),
+        "de_debug_mask": ([vp, i32, vp], C.c_int),
         "de_set_launch": ([vp, i32, i32], C.c_int),
         "de_set_wait_limit": ([vp, i64], C.c_int),
         "de_get_wait_limit": ([vp, C.POINTER(i64)], C.c_int),
@@ -204,7 +206,8 @@ def de_create(N, D, F, CR, xo, obj, bounds, seed, params=None, stream=None):
                           PRECISION.get(params.get("prec", "fp32"), 0),
                           int(params.get("incumbent_every", 0)),
                           BOUND[params.get("bound", "probabilistic")],
-                          float(params.get("margin_sigmas", 0.0)))
+                          float(params.get("margin_sigmas", 0.0)),
+                          REPAIR[params.get("repair", "clip")])
     xo_i = XOVER[xo] if isinstance(xo, str) else int(xo)
     obj_i = OBJECTIVE[obj] if isinstance(obj, str) else int(obj)
     rc = L.de_create(C.byref(h), int(N), int(D), float(F), float(CR), xo_i, obj_i,
@@ -315,6 +318,13 @@ def de_debug_lengths(ctx, words, inst=0):
                                            C.c_void_p(Lg.ctypes.data), C.c_void_p(Ls.ctypes.data),
                                            C.c_void_p(ec.ctypes.data)), "de_debug_lengths")
     return Lg, Ls, ec.astype(bool)
+
+
+def de_debug_mask(ctx, N, D, inst=0):
+    """The N x D crossover mask (uint8, 1 = from the mutant) of the next generation."""
+    m = np.empty((N, D), dtype=np.uint8)
+    _check(load_library().de_debug_mask(C.c_void_p(ctx), int(inst), C.c_void_p(m.ctypes.data)), "de_debug_mask")
+    return m
 
 
 def de_set_wait_limit(ctx, ns):
@@ -516,6 +526,9 @@ class Batch:
     def debug_lengths(self, inst, words):
         return de_debug_lengths(self.ctx, words, inst)
 
+    def debug_mask(self, inst):
+        return de_debug_mask(self.ctx, self.specs[inst]["N"], self.specs[inst]["D"], inst)
+
     def set_wait_limit(self, ns):
         de_set_wait_limit(self.ctx, ns)
 
@@ -601,6 +614,9 @@ class Optimizer:
 
     def debug_lengths(self, words):
         return de_debug_lengths(self.ctx, words, 0)
+
+    def debug_mask(self):
+        return de_debug_mask(self.ctx, self.N, self.D, 0)
 
     def save(self):
         return de_save(self.ctx)

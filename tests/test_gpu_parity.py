@@ -43,7 +43,7 @@ def check_fitness(f32, f64, what):
     assert not bad.any(), "%s: %d rows off, e.g. %r vs %r" % (what, bad.sum(), f32[bad][:3], f64[bad][:3])
 
 
-def one_step_parity(opt, lo, hi, xo, obj, F, CR, seed, pop=None):
+def one_step_parity(opt, lo, hi, xo, obj, F, CR, seed, pop=None, repair="clip"):
     """Shared parent population -> one GPU debug step and one oracle step."""
     N, D = opt.N, opt.D
     if pop is None:
@@ -55,7 +55,7 @@ def one_step_parity(opt, lo, hi, xo, obj, F, CR, seed, pop=None):
     check_fitness(gpu_fit, fit64, "parent fitness")
     g = opt.stats()["generation"]
     trial, ft, acc, draws = opt.debug_step()
-    s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g)
+    s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g, repair=repair)
     assert np.array_equal(draws, s.draws), "draws differ"
     assert np.array_equal(trial.view(np.uint32), s.trial.view(np.uint32)), "trials differ"
     check_fitness(ft, s.ftrial, "trial fitness")
@@ -467,3 +467,85 @@ def test_binomial_threshold_extremes(kernel, CR):
                 assert np.all(s.L <= 2)                # j_rand, and a word 0 with probability 2^-32 per gene
         finally:
             opt.close()
+
+
+@pytest.mark.parametrize("xo,kernel", [("bin", 1), ("exp", 1), ("nec", 1), ("exp", 2), ("nec", 2), ("bin", 3),
+                                       ("nec", 3)])
+def test_midpoint_repair_parity(xo, kernel):
+    """DE_REPAIR_MIDPOINT: a mutant gene outside the box becomes the midpoint
+    of the violated bound and the target gene, in each kernel (row per CTA,
+    pipelined, streaming), bit for bit with the oracle; F = 0.9 puts many
+    mutants outside the box."""
+    F, CR, seed, obj = 0.9, 0.9, 31, "rastrigin"
+    for (N, D) in ((40, 130), (12, 4100)):
+        if kernel == 2 and D < 2048:
+            continue                                    # the pipelined kernel is for long rows
+        lo, hi = W.BOXES[obj]
+        opt = DE.Optimizer(N, D, F=F, CR=CR, xo=xo, obj=obj, bounds=(lo, hi), seed=seed,
+                           params={"repair": "midpoint"})
+        try:
+            opt.set_kernel(kernel)
+            s, acc, _ = one_step_parity(opt, lo, hi, xo, obj, F, CR, seed, repair="midpoint")
+            c = O.step(W.population(N, D, lo, hi, seed + 100), np.full(N, np.inf), F, CR, xo, obj, lo, hi, seed,
+                       0, repair="clip")
+            assert not np.array_equal(s.trial, c.trial)  # some genes were repaired differently from clipping
+        finally:
+            opt.close()
+
+
+def test_repair_mode_in_checkpoints():
+    """A checkpoint records the repair mode; loading it into a context with the
+    other mode is refused."""
+    a = DE.Optimizer(20, 30, F=0.9, CR=0.9, xo="nec", obj="sphere", bounds=(-1.0, 1.0), seed=3,
+                     params={"repair": "midpoint"})
+    b = DE.Optimizer(20, 30, F=0.9, CR=0.9, xo="nec", obj="sphere", bounds=(-1.0, 1.0), seed=3)
+    try:
+        a.run(3)
+        blob = a.save()
+        with pytest.raises(DE.DEError) as e:
+            b.load(blob)
+        assert e.value.code == DE.DE_EINVAL
+        a.load(blob)
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+@pytest.mark.parametrize("base", ["distinct", "random"])
+def test_debug_mask_matches_oracle(xo, base):
+    """de_debug_mask: the N x D mask of the next generation from the kernels'
+    draw functions, row by row against the oracle's mask (Eq. 2, Alg. 8,
+    Alg. 9 with Eq. 9) with the oracle's j_rand."""
+    for (N, D, CR) in ((50, 37, 0.3), (20, 1001, 0.9), (8, 5, 1.0), (9, 64, 0.0)):
+        opt, lo, hi = make(N, D, xo, "sphere", CR=CR, seed=41)
+        try:
+            opt.set_base(base)
+            opt.run(2)
+            g = opt.stats()["generation"]
+            best = O.argmin(opt.population()[1])
+            m = opt.debug_mask()
+            for i in range(N):
+                _, jr = O.donors_base(N, D, 41, g, i, base, best=best)
+                ref, _ = O.mask(D, CR, xo, 41, g, i, jr)
+                assert np.array_equal(m[i], ref), (xo, base, N, D, CR, i)
+        finally:
+            opt.close()
+
+
+def test_debug_mask_batched_instance():
+    specs = [dict(N=30 + 5 * k, D=D, F=0.5, CR=CR, xo=xo, obj="sphere", bounds=(-1.0, 1.0))
+             for k, (D, CR, xo) in enumerate([(17, 0.9, "nec"), (300, 0.5, "bin"), (64, 0.8, "exp"),
+                                             (2500, 0.9, "nec")])]
+    bt = DE.Batch(specs, seed=43)
+    try:
+        bt.run(3)
+        for k, s in enumerate(specs):
+            g = bt.stats(k)["generation"]
+            m = bt.debug_mask(k)
+            for i in range(s["N"]):
+                _, jr = O.donors(s["N"], s["D"], 43, g, i, inst=k)
+                ref, _ = O.mask(s["D"], s["CR"], s["xo"], 43, g, i, jr, inst=k)
+                assert np.array_equal(m[i], ref), (k, i)
+    finally:
+        bt.close()

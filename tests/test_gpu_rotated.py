@@ -37,7 +37,7 @@ def make(N, D, xo, obj, prec="fp32", CR=0.9, F=0.5, seed=1, every=0, **extra):
     return opt, o, R
 
 
-def one_step(opt, o, R, xo, obj, F, CR, seed):
+def one_step(opt, o, R, xo, obj, F, CR, seed, repair="clip"):
     N, D = opt.N, opt.D
     lo, hi = W.BOXES[obj]
     pop = W.population(N, D, lo, hi, seed + 100)
@@ -47,7 +47,7 @@ def one_step(opt, o, R, xo, obj, F, CR, seed):
     assert np.all(np.abs(gfit - fit64) <= tol(fit64)), "parent fitness"
     g = opt.stats()["generation"]
     trial, ft, acc, draws = opt.debug_step()
-    s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g, shift=o, rot=R)
+    s = O.step(pop, fit64, F, CR, xo, obj, lo, hi, seed, g, shift=o, rot=R, repair=repair)
     assert np.array_equal(draws, s.draws), "draws"
     assert np.array_equal(trial.view(np.uint32), s.trial.view(np.uint32)), "trials"
     assert np.all(np.abs(ft - s.ftrial) <= tol(s.ftrial)), "trial fitness"
@@ -254,3 +254,15 @@ def test_rotated_bf16_lockstep_full_size(obj):
     finally:
         a.close()
         b.close()
+
+
+def test_rotated_midpoint_repair():
+    """The shifted-rotated path's trial kernel with DE_REPAIR_MIDPOINT (F = 1.4
+    sends many mutants out of the box): trials bit for bit with the oracle,
+    selections outside the ambiguity band (FP32 product)."""
+    N, D, xo, obj = 64, 256, "nec", "sr_rastrigin"
+    opt, o, R = make(N, D, xo, obj, prec="fp32", F=1.4, seed=5, repair="midpoint")
+    try:
+        one_step(opt, o, R, xo, obj, 1.4, 0.9, 5, repair="midpoint")
+    finally:
+        opt.close()

@@ -89,6 +89,43 @@ def test_mutation_clips_to_box():
         assert np.all(s.trial[i] == np.float32(expect))
 
 
+@pytest.mark.parametrize("xo", ["bin", "nec"])
+def test_midpoint_repair_on_integer_population(xo):
+    """Midpoint repair: a mutant gene below lo becomes the point halfway
+    between lo and the target gene (equal distances, exact on this integer
+    population), above hi halfway between hi and the target; genes whose
+    mutant is inside the box are the mutant, genes outside the mask are the
+    parent, and the only differences from clipping are at the repaired
+    genes."""
+    N, D, lo, hi, F = 10, 12, 0.0, 9.0, 3.0
+    pop = np.repeat(np.arange(N, dtype=np.float32)[:, None], D, axis=1)   # row k is all k
+    pop[:, ::3] = (9 - np.arange(N, dtype=np.float32))[:, None]           # a second column pattern
+    fit = np.full(N, np.inf)
+    s = O.step(pop, fit, F, 0.7, xo, "sphere", lo, hi, seed=4, g=0, want_mask=True, repair="midpoint")
+    c = O.step(pop, fit, F, 0.7, xo, "sphere", lo, hi, seed=4, g=0, want_mask=True, repair="clip")
+    assert np.array_equal(s.mask, c.mask) and np.array_equal(s.draws, c.draws)
+    below = above = 0
+    for i in range(N):
+        r1, r2, r3 = s.r[i]
+        for j in range(D):
+            u, x = float(s.trial[i, j]), float(pop[i, j])
+            if not s.mask[i, j]:
+                assert u == x
+                continue
+            v = float(pop[r1, j]) + F * (float(pop[r2, j]) - float(pop[r3, j]))   # Eq. 1, exact here
+            if v < lo:
+                below += 1
+                assert u - lo == x - u and lo <= u <= x
+                assert float(c.trial[i, j]) == lo
+            elif v > hi:
+                above += 1
+                assert hi - u == u - x and x <= u <= hi
+                assert float(c.trial[i, j]) == hi
+            else:
+                assert u == v == float(c.trial[i, j])
+    assert below > 0 and above > 0
+
+
 def test_cr_one_and_zero_identities():
     N, D, obj = 16, 25, "rastrigin"
     pop, fit, lo, hi = _setup(N, D, obj)
