@@ -52,12 +52,17 @@ static bool g_scratch_ready[kNoallocMaxDevices];
 static double g_table_cr[kNoallocMaxDevices];
 static int g_table_d[kNoallocMaxDevices];   // 0: no table built yet
 
-// Clears what must start at zero (state, the input half of the slot bytes),
-// writes the NEC thresholds: zeros for n beyond the last T_n > 1 (no word
-// w >= 1 passes them), then T_n - 1 = ceil(c_n 2^32) - 1 with c_1 = Cr,
-// c_n = fl(c_{n-1} Cr) in FP64, exactly as de_create computes them.
+// Clears what must start at zero (state, the input half of the slot bytes)
+// and, when build_table is set, writes the NEC thresholds T_n - 1 =
+// ceil(c_n 2^32) - 1 with c_1 = Cr, c_n = fl(c_{n-1} Cr) in FP64, exactly as
+// de_create computes them, and 0 from the first T_n <= 1 on (no word w >= 1
+// passes those). The products are a chain: thread 0 forms them, a chunk at a
+// time, into shared memory, and all threads turn each chunk into thresholds.
+constexpr int kNoallocChunk = 256;
+
 __global__ void noalloc_setup_kernel(unsigned char* scratch, int N, int D, double CR, int cr_mode,
                                      long long gen, int build_table) {
+  __shared__ double cbuf[kNoallocChunk];
   DevState* st = reinterpret_cast<DevState*>(scratch);
   uint8_t* slots = scratch + kNoallocStateBytes;
   uint32_t* tab = reinterpret_cast<uint32_t*>(scratch + kNoallocStateBytes + kNoallocSlotBytes);
@@ -74,16 +79,31 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, int N, int D, doubl
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) slots[(size_t)(gen & 1) * N + i] = 0;
   if (!build_table) return;
-  for (int k = threadIdx.x; k < D - 1; k += blockDim.x) tab[k] = 0u;
+  __shared__ int s_ended;                           // every entry from this chunk on is 0
+  double cn = CR;                                   // c_(base + 1), thread 0's running product
+  if (threadIdx.x == 0) s_ended = (cr_mode != kCrGeneral);
   __syncthreads();
-  if (threadIdx.x == 0 && cr_mode == kCrGeneral) {
-    double cn = CR;
-    for (int n = 1; n <= D - 1; ++n) {
-      const double Tn = ceil(__dmul_rn(cn, 4294967296.0));
-      if (Tn <= 1.0) break;
-      tab[n - 1] = (uint32_t)(Tn - 1.0);
-      cn = __dmul_rn(cn, CR);
+  for (int base = 0; base < D - 1; base += kNoallocChunk) {
+    const int len = min(kNoallocChunk, D - 1 - base);
+    const bool ended = s_ended != 0;
+    if (threadIdx.x == 0 && !ended) {
+      for (int k = 0; k < len; ++k) {
+        cbuf[k] = cn;
+        cn = __dmul_rn(cn, CR);
+      }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+      uint32_t t = 0u;
+      if (!ended) {
+        const double Tn = ceil(__dmul_rn(cbuf[k], 4294967296.0));
+        t = (Tn > 1.0) ? (uint32_t)(Tn - 1.0) : 0u;   // T_n <= 1: no word w >= 1 passes
+      }
+      tab[base + k] = t;
+    }
+    // the products only decrease: once one is at most 2^-32, every later T_n is at most 1
+    if (threadIdx.x == 0 && !ended && cbuf[len - 1] <= 0x1p-32) s_ended = 1;
+    __syncthreads();
   }
 }
 

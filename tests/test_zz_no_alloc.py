@@ -105,7 +105,8 @@ def test_noalloc_step_matches_context_twice(obj, N, D, CR):
         opt.close()
 
 
-@pytest.mark.parametrize("obj,N,D,CR", [("ackley", 40, 130, 0.9), ("griewank", 33, 29, 0.1)])
+@pytest.mark.parametrize("obj,N,D,CR", [("ackley", 40, 130, 0.9), ("griewank", 33, 29, 0.1),
+                                        ("elliptic", 6, 4099, 0.9999)])
 def test_noalloc_step_matches_oracle(obj, N, D, CR):
     torch = _cuda()
     F, seed, g = 0.5, 9, 3
