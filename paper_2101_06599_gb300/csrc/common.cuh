@@ -12,6 +12,7 @@
 //   nec_tm1  : NEC thresholds T_n - 1 (uint32, n = 1 .. nT), see draws.cuh.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "philox.cuh"
@@ -78,6 +79,34 @@ struct GenParams {
   int* dbg_draws;           // N x 5
   RoundKeys rk;             // key's Philox round keys (kernels drawing a block per few genes)
 };
+
+// Programmatic dependent launch. A kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream is still running (once
+// every CTA of that kernel has called griddep_launch_dependents or exited):
+// its launch overlaps the previous kernel's tail instead of following it.
+// griddep_wait blocks until the previous kernel has completed and its memory
+// is visible; every kernel launched this way calls it before it reads or
+// writes anything. Both are no-ops for a kernel launched without it.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // FP32 -> uint32 whose unsigned order is the float order; NaN maps above +inf.
 __device__ __forceinline__ uint32_t ordered_bits(float f) {

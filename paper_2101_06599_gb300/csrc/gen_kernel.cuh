@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
   __shared__ float red[4][32];
   __shared__ float s_first[(OBJ == kRosenbrock) ? V : 1][32];
 
+  griddep_wait();                                  // the previous generation has closed
+  griddep_launch_dependents();
   const int i = blockIdx.x;
   const int t = threadIdx.x, T = blockDim.x;
   const long long gen = p.st->gen;
@@ -258,14 +260,13 @@ template <int XO, int OBJ>
 cudaError_t launch_gen_obj(int vidx, const GenParams& p, int block, cudaStream_t s) {
   const dim3 grid((unsigned)p.N), blk((unsigned)block);
   switch (vidx) {
-    case 0: gen_kernel<XO, OBJ, 1><<<grid, blk, 0, s>>>(p); break;
-    case 1: gen_kernel<XO, OBJ, 2><<<grid, blk, 0, s>>>(p); break;
-    case 2: gen_kernel<XO, OBJ, 4><<<grid, blk, 0, s>>>(p); break;
-    case 3: gen_kernel<XO, OBJ, 8><<<grid, blk, 0, s>>>(p); break;
-    case 4: gen_kernel<XO, OBJ, 16><<<grid, blk, 0, s>>>(p); break;
+    case 0: return launch_pdl(gen_kernel<XO, OBJ, 1>, grid, blk, 0, s, p);
+    case 1: return launch_pdl(gen_kernel<XO, OBJ, 2>, grid, blk, 0, s, p);
+    case 2: return launch_pdl(gen_kernel<XO, OBJ, 4>, grid, blk, 0, s, p);
+    case 3: return launch_pdl(gen_kernel<XO, OBJ, 8>, grid, blk, 0, s, p);
+    case 4: return launch_pdl(gen_kernel<XO, OBJ, 16>, grid, blk, 0, s, p);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <int XO>

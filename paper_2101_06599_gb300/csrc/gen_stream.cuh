@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
   __shared__ int s_cnt[kStreamWarps];
   __shared__ int s_acc[kStreamWarps];
   extern __shared__ uint8_t s_masks[];             // binomial: D4 mask bytes per warp
+  griddep_wait();                                  // the previous generation has closed
+  griddep_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* mc = (XO == kBin) ? s_masks + (size_t)warp * p.D4 : nullptr;
   const int i = blockIdx.x * kStreamWarps + warp;
@@ -284,8 +286,7 @@ template <int XO, int OBJ>
 cudaError_t launch_stream_obj(const GenParams& p, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.N + kStreamWarps - 1) / kStreamWarps);
   const size_t smem = (XO == kBin) ? (size_t)kStreamWarps * (size_t)p.D4 : 0;
-  gen_stream_kernel<XO, OBJ><<<grid, kStreamWarps * 32, smem, s>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(gen_stream_kernel<XO, OBJ>, dim3(grid), dim3(kStreamWarps * 32), smem, s, p);
 }
 
 template <int XO>

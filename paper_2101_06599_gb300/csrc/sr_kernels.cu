@@ -37,6 +37,8 @@ constexpr int kTrialWarps = 8, kTrialUnroll = 4;
 
 template <int XO>
 __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid_constant__ SrParams sp) {
+  griddep_wait();                                  // the previous kernel of the generation is done
+  griddep_launch_dependents();
   const GenParams& p = sp.g;
   __shared__ int wcnt[kTrialWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -215,6 +217,8 @@ constexpr int kGbM = 128, kGbN = 128, kGbK = 16, kGbLd = kGbM + 4;
 
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_constant__ SrParams sp, int mode) {
+  griddep_wait();                                  // the previous kernel of the generation is done
+  griddep_launch_dependents();
   const GenParams& p = sp.g;
   __shared__ __align__(16) float As[2][kGbK][kGbLd];
   __shared__ __align__(16) float Bs[2][kGbK][kGbLd];
@@ -333,6 +337,8 @@ constexpr int kLsLdA = kLsK + 4, kLsLdB = kLsN + 4;
 // row groups, RPT = kLsM * 16 / kLsThreads entries per thread.
 template <bool VEC, int kLsM, int kLsThreads>
 __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
+  griddep_wait();                                  // the previous kernel of the generation is done
+  griddep_launch_dependents();
   constexpr int RPT = kLsM * 16 / kLsThreads;
   static_assert(RPT == 1 || RPT == 2, "one or two entries per thread");
   constexpr int kLsLdT = kLsM + 4;
@@ -517,6 +523,8 @@ __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, floa
 }
 
 __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bnd) {
+  griddep_wait();                                  // the previous kernel of the generation is done
+  griddep_launch_dependents();
   const GenParams& p = sp.g;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
@@ -559,6 +567,8 @@ __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bn
 
 // Ambiguous rows: decide with FP32-path values of the trial (and the parent).
 __global__ void sr_resolve_kernel(const __grid_constant__ SrParams sp) {
+  griddep_wait();                                  // the previous kernel of the generation is done
+  griddep_launch_dependents();
   const GenParams& p = sp.g;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
@@ -605,10 +615,9 @@ __global__ void sr_store_eval_kernel(const __grid_constant__ SrParams sp) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_sr_trial(int xo, int /*vidx*/, const SrParams& sp, int /*block*/, cudaStream_t s) {
   const unsigned grid = (unsigned)((sp.g.N + kTrialWarps - 1) / kTrialWarps);
-  if (xo == kBin) sr_trial_kernel<kBin><<<grid, kTrialWarps * 32, 0, s>>>(sp);
-  else if (xo == kExp) sr_trial_kernel<kExp><<<grid, kTrialWarps * 32, 0, s>>>(sp);
-  else sr_trial_kernel<kNec><<<grid, kTrialWarps * 32, 0, s>>>(sp);
-  return cudaGetLastError();
+  if (xo == kBin) return launch_pdl(sr_trial_kernel<kBin>, dim3(grid), dim3(kTrialWarps * 32), 0, s, sp);
+  if (xo == kExp) return launch_pdl(sr_trial_kernel<kExp>, dim3(grid), dim3(kTrialWarps * 32), 0, s, sp);
+  return launch_pdl(sr_trial_kernel<kNec>, dim3(grid), dim3(kTrialWarps * 32), 0, s, sp);
 }
 
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
@@ -617,24 +626,20 @@ cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cuda
     constexpr int M = kSrListRows, T = kSrListThreads;
     const int tiles = (max_rows + M - 1) / M;
     const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 128)));
-    if (sp.g.D % 4 == 0) sr_gemm_fp32_list_kernel<true, M, T><<<grid, T, 0, s>>>(sp);
-    else sr_gemm_fp32_list_kernel<false, M, T><<<grid, T, 0, s>>>(sp);
-    return cudaGetLastError();
+    if (sp.g.D % 4 == 0) return launch_pdl(sr_gemm_fp32_list_kernel<true, M, T>, grid, dim3(T), 0, s, sp);
+    return launch_pdl(sr_gemm_fp32_list_kernel<false, M, T>, grid, dim3(T), 0, s, sp);
   }
   const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
-  if (sp.g.D % 4 == 0) sr_gemm_fp32_kernel<true><<<grid, 256, 0, s>>>(sp, mode);
-  else sr_gemm_fp32_kernel<false><<<grid, 256, 0, s>>>(sp, mode);
-  return cudaGetLastError();
+  if (sp.g.D % 4 == 0) return launch_pdl(sr_gemm_fp32_kernel<true>, grid, dim3(256), 0, s, sp, mode);
+  return launch_pdl(sr_gemm_fp32_kernel<false>, grid, dim3(256), 0, s, sp, mode);
 }
 
 cudaError_t launch_sr_select(const SrParams& sp, const SrBound& b, cudaStream_t s) {
-  sr_select_kernel<<<(sp.g.N + 255) / 256, 256, 0, s>>>(sp, b);
-  return cudaGetLastError();
+  return launch_pdl(sr_select_kernel, dim3((sp.g.N + 255) / 256), dim3(256), 0, s, sp, b);
 }
 
 cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s) {
-  sr_resolve_kernel<<<(2 * sp.g.N + 255) / 256, 256, 0, s>>>(sp);
-  return cudaGetLastError();
+  return launch_pdl(sr_resolve_kernel, dim3((2 * sp.g.N + 255) / 256), dim3(256), 0, s, sp);
 }
 
 cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s) {
@@ -675,6 +680,8 @@ constexpr int kIncWarps = 8;
 
 __global__ void __launch_bounds__(kIncWarps * 32) sr_finish_kernel(const __grid_constant__ SrParams sp, int every,
                                                                   int close) {
+  griddep_wait();                                  // the previous kernel of the generation is done
+  griddep_launch_dependents();
   const GenParams& p = sp.g;
   const long long gen = p.st->gen;
   const long long gnext = close ? gen + 1 : gen;
@@ -742,8 +749,7 @@ __global__ void __launch_bounds__(kIncWarps * 32) sr_finish_kernel(const __grid_
 
 cudaError_t launch_sr_finish(const SrParams& sp, int every, bool close, cudaStream_t s) {
   const unsigned grid = (unsigned)((sp.g.D + kIncWarps - 1) / kIncWarps);
-  sr_finish_kernel<<<grid, kIncWarps * 32, 0, s>>>(sp, every, close ? 1 : 0);
-  return cudaGetLastError();
+  return launch_pdl(sr_finish_kernel, dim3(grid), dim3(kIncWarps * 32), 0, s, sp, every, close ? 1 : 0);
 }
 
 }  // namespace de

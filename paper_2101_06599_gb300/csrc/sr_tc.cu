@@ -94,6 +94,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) sr_tc_kernel(const __grid_constant__ TcParams tp) {
+  griddep_wait();                                  // the trial kernel has written the operands
+  griddep_launch_dependents();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sA = smem;
@@ -260,8 +262,7 @@ cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s) {
       !encode_bf16_2d(&tp.tr_lo, sp.rot_lo, (uint64_t)D, (uint64_t)D, kTcBN))
     return cudaErrorInvalidValue;
   const dim3 grid((unsigned)(D / kTcBN), (unsigned)((N + kTcBM - 1) / kTcBM));
-  sr_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(tp);
-  return cudaGetLastError();
+  return launch_pdl(sr_tc_kernel, grid, dim3(kTcThreads), kTcSmem, s, tp);
 }
 
 }  // namespace de
