@@ -254,9 +254,10 @@ def time_batched(DE, torch, steps, warmup, seed, peak, n_inst=None, kernels="tun
 def time_rotated(DE, torch, steps, warmup):
     """Shifted-rotated Rastrigin and elliptic (N = 4096, D = 1024, box
     [-100, 100], o ~ U[-80, 80] seed 2, Gaussian-QR rotation seed 3, NEC,
-    F = 0.5, Cr = 0.9): the FP32-product path against the BF16 tensor-core
-    path with FP32 re-evaluation of uncertain selections; both runs start from
-    the same population, so equal accept counts mean equal selections."""
+    F = 0.5, Cr = 0.9): the FP32-product path against the BF16 and FP16
+    split-operand tensor-core paths with FP32 re-evaluation of uncertain
+    selections; the runs start from the same population, so equal accept
+    counts mean equal selections."""
     from paper_2101_06599_gb300 import workloads as Wk
     N, D = 4096, 1024
     o = Wk.shift_vector(D, seed=2)
@@ -265,7 +266,7 @@ def time_rotated(DE, torch, steps, warmup):
            "gemm_flop_per_gen": 2.0 * N * D * D}
     for obj in ("sr_rastrigin", "sr_elliptic"):
         r = {}
-        for prec in ("fp32", "bf16"):
+        for prec in ("fp32", "bf16", "fp16"):
             opt = DE.Optimizer(N, D, F=F_DEF, CR=CR_DEF, xo="nec", obj=obj, bounds=Wk.BOXES[obj], seed=SEED,
                                params={"shift": o, "rotation": R, "prec": prec, "incumbent_every": 50})
             try:
@@ -286,7 +287,8 @@ def time_rotated(DE, torch, steps, warmup):
                        "accepts": st1["accepts"] - st0["accepts"],
                        "reselected_frac": (st1["reselected"] - st0["reselected"]) / (N * steps)}
         r["speedup_bf16_over_fp32"] = r["fp32"]["ms_per_gen"] / r["bf16"]["ms_per_gen"]
-        r["same_selections"] = r["fp32"]["accepts"] == r["bf16"]["accepts"]
+        r["speedup_fp16_over_fp32"] = r["fp32"]["ms_per_gen"] / r["fp16"]["ms_per_gen"]
+        r["same_selections"] = r["fp32"]["accepts"] == r["bf16"]["accepts"] == r["fp16"]["accepts"]
         out[obj] = r
     return out
 

@@ -81,12 +81,23 @@ typedef enum {
   DE_OBJ_SR_ELLIPTIC = 7    /* elliptic of z = R (x - o)                           */
 } de_objective;
 
-/* Precision of the z = R (x - o) product of the shifted-rotated objectives. */
-typedef enum { DE_PREC_FP32 = 0, DE_PREC_TF32 = 1, DE_PREC_BF16 = 2 } de_precision;
+/* Precision of the z = R (x - o) product of the shifted-rotated objectives.
+ * FP32: SIMT FMA chains. BF16 and FP16: tensor-core products of split
+ * operands (a = a_hi + a_lo, R = R_hi + R_lo, three products), FP32
+ * accumulation, selections made certain by an error bound and the rest
+ * re-evaluated in FP32, so every decision is the FP32 path's. BF16 splits
+ * carry 16 bits of each operand; FP16 splits carry 22, scaled by powers of
+ * two (x - o by 2^s with max |x - o| 2^s below 2^15 from the box, R by 2^14
+ * over its largest entry) so that both halves stay normal, which makes the
+ * bound about 60 % narrower and sends fewer rows to the re-evaluation; the
+ * halves of components below ~2^-11 of the box's reach lose bits to FP16's
+ * subnormal range, which the bound counts. Both need D a multiple of 256 and
+ * a GB300 (sm_103); TF32 returns DE_EUNSUPPORTED. */
+typedef enum { DE_PREC_FP32 = 0, DE_PREC_TF32 = 1, DE_PREC_BF16 = 2, DE_PREC_FP16 = 3 } de_precision;
 
-/* Error bound that decides which BF16-path selections are certain (the rest
- * are re-evaluated with the FP32 product, so that decisions match the FP32
- * path). PROBABILISTIC: margin_sigmas standard deviations of |f_BF16 -
+/* Error bound that decides which BF16- or FP16-path selections are certain
+ * (the rest are re-evaluated with the FP32 product, so that decisions match
+ * the FP32 path). PROBABILISTIC: margin_sigmas standard deviations of |f_BF16 -
  * f_FP32| under the standard model of independent, zero-mean rounding errors
  * (Hoeffding's inequality), with the accumulation's partial sums taken as at
  * most 4 |x - o|_2 / sqrt(D) (rotations with delocalised rows, such as a
@@ -114,7 +125,7 @@ typedef struct {
   de_precision prec;        /* shifted-rotated objectives: product precision                */
   int32_t incumbent_every;  /* shifted-rotated: FP64 re-evaluation of the best every K
                                generations (0 selects 50)                                  */
-  de_bound_kind bound;      /* BF16 product: which error bound decides certain selections  */
+  de_bound_kind bound;      /* BF16/FP16 product: which error bound decides certain selections */
   double margin_sigmas;     /* PROBABILISTIC bound: margin in standard deviations (0 selects
                                8; the model's failure probability per decision is at most
                                2 exp(-m^2 / 2))                                             */

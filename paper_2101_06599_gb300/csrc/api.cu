@@ -263,8 +263,8 @@ int de_create(de_ctx** out, int32_t N, int32_t D, float F, double CR, de_crossov
     if (!prm || !prm->shift || !prm->rotation) return DE_EINVAL;
     if (prm->bound != DE_BOUND_PROBABILISTIC && prm->bound != DE_BOUND_WORST_CASE) return DE_EINVAL;
     if (!std::isfinite(prm->margin_sigmas) || prm->margin_sigmas < 0.0) return DE_EINVAL;
-    if (prm->prec != DE_PREC_FP32 && prm->prec != DE_PREC_BF16) return DE_EUNSUPPORTED;
-    if (prm->prec == DE_PREC_BF16 && !sr_tc_supported(D)) return DE_EUNSUPPORTED;
+    if (prm->prec != DE_PREC_FP32 && prm->prec != DE_PREC_BF16 && prm->prec != DE_PREC_FP16) return DE_EUNSUPPORTED;
+    if (prm->prec != DE_PREC_FP32 && !sr_tc_supported(D)) return DE_EUNSUPPORTED;
   }
   int repair = DE_REPAIR_CLIP;
   if (prm) {

@@ -139,13 +139,15 @@ cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cuda
 cudaError_t launch_sr_select(const SrParams& sp, const SrBound& b, cudaStream_t s);
 cudaError_t launch_sr_resolve(const SrParams& sp, cudaStream_t s);
 cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s);
-cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, cudaStream_t s);
+cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, bool fp16, float scale,
+                                     cudaStream_t s);
 cudaError_t launch_sr_transpose(const float* rot, float* rot_t, int D, cudaStream_t s);
 cudaError_t launch_sr_finish(const SrParams& sp, int every, bool close, cudaStream_t s);
 // tcgen05 BF16 product (split operands) with the fitness epilogue; requires
 // D % 256 == 0. sr_tc_supported tells whether this build and device have it.
 cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s);
 cudaError_t prepare_sr_tc();
+cudaError_t prepare_sr_list();
 bool sr_tc_supported(int D);
 
 constexpr size_t kStagingHeader = 32;

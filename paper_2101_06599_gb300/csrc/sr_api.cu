@@ -11,41 +11,53 @@ using namespace de_host;
 
 namespace de_host {
 
-// Bound constants of the BF16 path.
+// Bound constants of the split-operand paths (BF16, FP16).
 //
 // Both products see the same FP32 a = fl(u - o). The tensor-core product uses
-// a = a_hi + a_lo + e_a and R = R_hi + R_lo + E_R (BF16 roundings, unit
-// roundoff 2^-8 each, so |a_lo + e_a| <= 2^-8 |a|, |e_a| <= 2^-16 |a|, the
-// same for R entrywise) and keeps a_hi R_hi + a_lo R_hi + a_hi R_lo; its
-// z differs from R a by rho = -(R_hi e_a + R_lo (a_lo + e_a) + E_R a).
-// Accumulation: 3D FP32 additions on the tensor cores (unit 2^-23, which
-// allows truncating adds) and D FMAs on the FP32 path (unit 2^-24).
+// a = a_hi + a_lo + e_a and R = R_hi + R_lo + E_R, each half a rounding to a
+// format of unit roundoff u_s (BF16 2^-8; FP16 2^-11, on 2^sa a and 2^sr R),
+// so |a_lo + e_a| <= u_s |a|, |e_a| <= u_s^2 |a| + f_a and |E_R| <= u_s^2 |R|
+// + f_r entrywise, where f_a = 2^(-25-sa) and f_r = 2^(-25-sr) are the
+// absolute error of a remainder that lands in FP16's subnormal range (zero
+// for BF16, which has FP32's range). It keeps a_lo R_hi + a_hi R_lo + a_hi R_hi
+// (in that order) and its z differs from R a by
+// rho = -(R_hi e_a + R_lo (a_lo + e_a) + E_R a).
+// Accumulation: FP32 additions on the tensor cores (unit 2^-23, which allows
+// truncating adds): D of the leading product and 2D of the corrections,
+// whose partial sums are at most 2.01 u_s of the leading product's; D FMAs
+// on the FP32 path (unit 2^-24).
 //
-// Worst case: |z_bf16,k - z_fp32,k| <= c |a|_2 by Cauchy-Schwarz (rows of R
-// have norm 1), c = 3.05 2^-16 + gamma_3D(2^-23) + gamma_D(2^-24).
+// Worst case: |z_split,k - z_fp32,k| <= c |a|_2 + 1.005 f_a sqrt(D) by
+// Cauchy-Schwarz (rows of R have norm 1), c = 3.05 u_s^2 + f_r sqrt(D) +
+// gamma_3D(2^-23) (1 + 3 u_s) + gamma_D(2^-24).
 //
 // Probabilistic (Hoeffding's inequality over independent zero-mean rounding
 // errors): sum_k g'(z_k) rho_k has standard deviation at most
-// sqrt(3) 1.005 2^-16 max|a_j| |g'|_2 (each of the three residual vectors,
-// |R_hi|_2 <= 1.005); the accumulation terms at most
-// |g'|_2 c_rw |a|_2 sqrt(3 u_tc^2 + u^2) when the partial sums stay within
-// c_rw |a|_2 / sqrt(D), c_rw = 4; the g evaluations (<= 12 roundings each)
-// and the sums of D values and nct partials on both paths at most
-// u |f| (sqrt(2 (D + nct)) + 12) because every g is >= 0. The tensor cores'
-// accumulator truncates: 3D / 16 MMA steps (K = 16 each) round each z_k
-// toward zero by at most 2^-23 |z_k| (partial sums taken no larger than
-// |z_k|), a bias of at most (3D/16) 2^-23 sum_k |g'(z_k)| |z_k|, which is at
-// most n (2 n + 20 pi sqrt(D)) for Rastrigin and 2 |f| for the elliptic
-// function. The second-order term is bounded by max|g''| / 2 times twice the
-// mean of |dz|_2^2.
-static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas, double amax, int nct) {
+// sqrt(3) (1.005 u_s^2 max|a_j| + f_a + f_r sqrt(D) max|a_j|) |g'|_2 (each of
+// the three residual vectors, |R_hi|_2 <= 1.005); the accumulation terms at
+// most |g'|_2 c_rw |a|_2 sqrt(u_tc^2 (1 + 2 (2.01 u_s)^2) + u^2) when the
+// partial sums stay within c_rw |a|_2 / sqrt(D), c_rw = 4; the g evaluations
+// (<= 12 roundings each) and the sums of D values and nct partials on both
+// paths at most u |f| (sqrt(2 (D + nct)) + 12) because every g is >= 0. The
+// tensor cores' accumulator truncates: the leading product's D / 16 MMA
+// steps (K = 16 each) round each z_k toward zero by at most 2^-23 |z_k|
+// (partial sums taken no larger than |z_k|), a bias of at most
+// (D/16) 2^-23 sum_k |g'(z_k)| |z_k|, which is at most n (2 n + 20 pi sqrt(D))
+// for Rastrigin and 2 |f| for the elliptic function; the corrections' 2D / 16
+// steps, with partial sums within 2.01 u_s c_rw n / sqrt(D), add at most
+// (2D/16) 2^-23 2.01 u_s c_rw n |g'|_2. The second-order term is bounded by
+// max|g''| / 2 times twice the mean of |dz|_2^2.
+static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas, double amax, int nct, double us,
+                          double fa, double fr) {
   SrBound b{};
   const double u = std::ldexp(1.0, -24), utc = std::ldexp(1.0, -23);
+  const double us2 = us * us, sD = std::sqrt((double)D);
   b.mode = (kind == DE_BOUND_WORST_CASE) ? 1 : 0;
   const double n3 = 3.0 * D;
   const double g3 = n3 * utc / (1.0 - n3 * utc), g1 = D * u / (1.0 - D * u);
-  const double split = 3.05 * std::ldexp(1.0, -16);
-  b.delta_per_norm = (float)((split + g3 * (1.0 + 3.0 * std::ldexp(1.0, -8)) + g1) * 1.001);
+  const double split = 3.05 * us2 + fr * sD;
+  b.delta_per_norm = (float)((split + g3 * (1.0 + 3.0 * us) + g1) * 1.001);
+  b.delta_abs = (float)(1.005 * fa * sD * 1.001);
   // reductions of sum g: 64 terms per column tile plus the tiles, on both paths
   b.rel = (float)(2.0 * (64.0 + D / 64.0 + 8.0) * u + 1e-6);
   double sw = 0.0;
@@ -54,19 +66,32 @@ static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas,
   b.sum_w = (float)sw;
 
   const double pi = 3.14159265358979323846, c_rw = 4.0;
-  const double acc2 = 3.0 * utc * utc + u * u;
+  const double cs = 2.01 * us;                                       // corrections / leading product
+  const double acc2 = utc * utc * (1.0 + 2.0 * cs * cs) + u * u;
+  const double rep = 1.005 * us2 * amax + fa + fr * sD * amax;       // per-entry residual scale
   const double g2half = (obj == DE_OBJ_SR_ELLIPTIC) ? std::exp2((double)(D - 1) * ell_k)   // w_max
                                                      : 1.0 + 20.0 * pi * pi;               // (2 + 40 pi^2) / 2
   b.lambda = (float)(sigmas > 0.0 ? sigmas : 8.0);
-  b.rep_c = (float)(std::sqrt(3.0) * 1.005 * std::ldexp(1.0, -16) * amax * 1.001);
+  b.rep_c = (float)(std::sqrt(3.0) * rep * 1.001);
   b.acc_c = (float)(c_rw * std::sqrt(acc2) * 1.001);
   b.eval_c = (float)(u * (std::sqrt(2.0 * (D + nct)) + 12.0) * 1.001);
-  b.quad_a = (float)(g2half * 2.0 * D * 3.0 * std::ldexp(1.0, -32) * amax * amax);
+  b.quad_a = (float)(g2half * 2.0 * D * 3.0 * rep * rep);
   b.quad_b = (float)(g2half * 2.0 * D * acc2 * c_rw * c_rw);
-  b.hconst = (float)(20.0 * pi * std::sqrt((double)D));
-  b.bias_c = (float)((3.0 * D / 16.0) * utc * 1.001);
+  b.hconst = (float)(20.0 * pi * sD);
+  b.bias_c = (float)((D / 16.0) * utc * 1.001);
+  b.bias_c2 = (float)((2.0 * D / 16.0) * utc * cs * c_rw * 1.001);
   b.wmax = (float)((obj == DE_OBJ_SR_ELLIPTIC) ? std::exp2((double)(D - 1) * ell_k) * 1.0001 : 0.0);
   return b;
+}
+
+// The power of two s with m 2^s in [2^14, 2^15): FP16 halves of values up to m
+// stay below 2^15, and the remainders of values above m 2^-11 stay normal.
+static int fp16_scale_exp(double m) {
+  if (!(m > 0.0)) return 0;
+  int s = 14 - (int)std::floor(std::log2(m));
+  while (std::ldexp(m, s) >= 32768.0) --s;
+  while (std::ldexp(m, s) < 16384.0) ++s;
+  return s;
 }
 
 int sr_setup(de_ctx* c, const de_objparams* prm) {
@@ -75,7 +100,9 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
   std::memset(&sp, 0, sizeof(sp));
   c->rotated = true;
   sp.obj = c->obj;
-  sp.prec = (prm->prec == DE_PREC_BF16) ? 2 : 0;
+  sp.prec = (prm->prec == DE_PREC_BF16) ? 2 : (prm->prec == DE_PREC_FP16 ? 3 : 0);
+  sp.a_scale = 1.0f;
+  sp.z_scale = 1.0f;
   sp.nct2 = (D + kSrTile - 1) / kSrTile;
   sp.nct = sp.nct2;
   c->incumbent_every = prm->incumbent_every > 0 ? prm->incumbent_every : 50;
@@ -91,8 +118,10 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
   sp.part2_w = (float*)ctx_alloc(c, 2 * (size_t)N * sp.nct2 * sizeof(float));
   sp.inc_part = (double*)ctx_alloc(c, (size_t)D * sizeof(double));
   sp.inc_count = (unsigned*)ctx_alloc(c, sizeof(unsigned));
+  sp.finish_due = (int*)ctx_alloc(c, sizeof(int));
+  sp.inc_every = c->incumbent_every;
   if (!shift || !rot || !sp.part_g || !sp.part_w || !sp.norm2 || !sp.fit_err || !sp.amb || !sp.amb_count ||
-      !sp.part2_g || !sp.part2_w || !sp.inc_part || !sp.inc_count)
+      !sp.part2_g || !sp.part2_w || !sp.inc_part || !sp.inc_count || !sp.finish_due)
     return DE_ENOMEM;
   sp.shift = shift;
   sp.rot = rot;
@@ -102,6 +131,7 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.fit_err, 0, (size_t)N * sizeof(float), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.amb_count, 0, sizeof(unsigned), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(sp.inc_count, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sp.finish_due, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) {
     float* rot_t = (float*)ctx_alloc(c, (size_t)D * D * sizeof(float));
     if (!rot_t) return DE_ENOMEM;
@@ -109,7 +139,25 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
     e = launch_sr_transpose(rot, rot_t, D, c->stream);
   }
   if (e != cudaSuccess) return DE_ECUDA;
-  if (sp.prec == 2) {
+  double amax = 0.0;                     // max |u_j - o_j| over the box, rounded up
+  for (int j = 0; j < D; ++j)
+    amax = std::max(amax, std::max(std::fabs((double)c->b.lo - prm->shift[j]), std::fabs((double)c->b.hi - prm->shift[j])));
+  amax *= 1.0 + std::ldexp(1.0, -22);
+  double us = std::ldexp(1.0, -8), fa = 0.0, fr = 0.0;
+  int sa = 0, sr = 0;
+  if (sp.prec == 3) {
+    double rmax = 0.0;
+    for (size_t k = 0; k < (size_t)D * D; ++k) rmax = std::max(rmax, std::fabs((double)prm->rotation[k]));
+    sa = fp16_scale_exp(amax);
+    sr = fp16_scale_exp(rmax);
+    if (sa < -126 || sa > 127 || sa + sr < -126 || sa + sr > 126) return DE_EUNSUPPORTED;   // scales must be normal
+    us = std::ldexp(1.0, -11);
+    fa = std::ldexp(1.0, -25 - sa);
+    fr = std::ldexp(1.0, -25 - sr);
+    sp.a_scale = std::ldexp(1.0f, sa);
+    sp.z_scale = std::ldexp(1.0f, -(sa + sr));
+  }
+  if (sp.prec >= 2) {
     uint16_t* hi = (uint16_t*)ctx_alloc(c, (size_t)D * D * sizeof(uint16_t));
     uint16_t* lo = (uint16_t*)ctx_alloc(c, (size_t)D * D * sizeof(uint16_t));
     sp.a_hi = (uint16_t*)ctx_alloc(c, (size_t)N * D * sizeof(uint16_t));
@@ -117,15 +165,13 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
     if (!hi || !lo || !sp.a_hi || !sp.a_lo) return DE_ENOMEM;
     sp.rot_hi = hi;
     sp.rot_lo = lo;
-    if (launch_sr_split_rotation(rot, hi, lo, (size_t)D * D, c->stream) != cudaSuccess) return DE_ECUDA;
-    if (prepare_sr_tc() != cudaSuccess) return DE_ECUDA;
+    if (launch_sr_split_rotation(rot, hi, lo, (size_t)D * D, sp.prec == 3, std::ldexp(1.0f, sr), c->stream) !=
+        cudaSuccess)
+      return DE_ECUDA;
+    if (prepare_sr_tc() != cudaSuccess || prepare_sr_list() != cudaSuccess) return DE_ECUDA;
     sp.nct = D / 256;                    // one partial per 256-column tile of the tensor-core product
   }
-  double amax = 0.0;                     // max |u_j - o_j| over the box, rounded up
-  for (int j = 0; j < D; ++j)
-    amax = std::max(amax, std::max(std::fabs((double)c->b.lo - prm->shift[j]), std::fabs((double)c->b.hi - prm->shift[j])));
-  amax *= 1.0 + std::ldexp(1.0, -22);
-  c->sbound = make_bound(D, c->obj, (double)c->p.ell_k, (int)prm->bound, prm->margin_sigmas, amax, sp.nct);
+  c->sbound = make_bound(D, c->obj, (double)c->p.ell_k, (int)prm->bound, prm->margin_sigmas, amax, sp.nct, us, fa, fr);
   return sync_stream(c);                 // host shift / rotation consumed
 }
 

@@ -16,16 +16,18 @@ constexpr int kSrTile = 64;          // columns per partial sum of g (both FP32 
 struct SrParams {
   GenParams g;
   int obj;                 // kSrRastrigin or kSrElliptic
-  int prec;                // 0 = FP32, 2 = BF16 (split hi/lo operands)
+  int prec;                // 0 = FP32, 2 = BF16, 3 = FP16 (split hi/lo operands)
+  float a_scale;           // FP16: 2^sa applied to a = u - o before the split (1 otherwise)
+  float z_scale;           // FP16: 2^-(sa + sr), undoes both operand scalings on z (1 otherwise)
   int nct;                 // column tiles per row of part_g / part_w (the main product)
   int nct2;                // column tiles per entry of part2_g / part2_w (FP32 product)
   const float* shift;      // o, D floats
   const float* rot;        // R, D x D FP32 row-major (z_k = sum_j R[k][j] a_j)
-  const uint16_t* rot_hi;  // bf16(R), D x D
-  const uint16_t* rot_lo;  // bf16(R - bf16(R)), D x D
+  const uint16_t* rot_hi;  // hi(R) (BF16, or FP16 of 2^sr R), D x D
+  const uint16_t* rot_lo;  // lo(R): the rounded remainder, D x D
   const float* rot_t;      // R transposed (j-major, rot_t[j D + k] = R[k][j]), D x D
-  uint16_t* a_hi;          // bf16(u - o), N x D (BF16 path)
-  uint16_t* a_lo;          // bf16((u - o) - bf16(u - o)), N x D
+  uint16_t* a_hi;          // hi(u - o) (BF16, or FP16 of 2^sa (u - o)), N x D
+  uint16_t* a_lo;          // lo(u - o): the rounded remainder, N x D
   float* part_g;           // N x nct: sum of g(z) over the column tile
   float* part_w;           // N x nct: sum of w_k |z_k| (w = 1 Rastrigin, c_k elliptic)
   float* norm2;            // N: |u - o|^2 of the trial (FP32)
@@ -36,6 +38,8 @@ struct SrParams {
   float* part2_w;
   double* inc_part;        // D: FP64 g(z_k) of the incumbent re-evaluation
   unsigned* inc_count;     // CTAs of the incumbent re-evaluation done (last one sums)
+  int inc_every;           // FP64 incumbent every inc_every generations
+  int* finish_due;         // set by the selection kernel: the incumbent is due at this close
 };
 
 // Bound constants of the BF16 path (sr_select_kernel). For a row with a =
@@ -46,15 +50,19 @@ struct SrBound {
   int mode;               // 0 probabilistic, 1 worst case
   // worst case: |dz_k| <= delta_per_norm * n for every k
   float delta_per_norm;
+  float delta_abs;        // FP16: the subnormal halves' absolute part of |dz_k|
   float rel;              // relative bound of the reductions of sum g
   float sum_w;            // sum of the elliptic weights
   // probabilistic: lambda * sqrt(s_rep^2 + s_acc^2 + s_eval^2) + bias + quad
   float lambda;           // margin in standard deviations
-  float rep_c;            // s_rep = rep_c * H  (operand-split residuals, sqrt(3) 2^-16 max|a_j|)
+  float rep_c;            // s_rep = rep_c * H  (operand-split residuals, sqrt(3) u_s^2 max|a_j|)
   float acc_c;            // s_acc = acc_c * n * H (accumulation roundings of both products)
   float eval_c;           // s_eval = eval_c * |f| (g evaluation and the sums over k)
   float quad_a, quad_b;   // second-order term quad_a + quad_b * n^2
-  float bias_c;           // truncation bias: bias_c * sum_k |g'(z_k)| |z_k| (n H Rastrigin, 2|f| elliptic)
+  float bias_c;           // truncation bias of the leading product: bias_c * sum_k |g'(z_k)| |z_k|
+                          // (n H Rastrigin, 2|f| elliptic)
+  float bias_c2;          // truncation bias of the two correction products (and the subnormal
+                          // halves' absolute part): bias_c2 * n * H
   float hconst;           // Rastrigin: 20 pi sqrt(D)
   float wmax;             // elliptic: the largest weight
 };

@@ -22,6 +22,7 @@
 #include "sr_common.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace de {
 
@@ -126,12 +127,23 @@ __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid
         }
         if (sp.prec != 0) {                        // D % 256 == 0 on this path: 8-byte aligned
           uint32_t h[4], l[4];
+          if (sp.prec == 3) {                      // FP16 halves of 2^sa a (the scaling is exact)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(a[e]);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(a[e], __bfloat162float(hi)));
-            h[e] = __bfloat16_as_ushort(hi);
-            l[e] = __bfloat16_as_ushort(lo);
+            for (int e = 0; e < 4; ++e) {
+              const float as = a[e] * sp.a_scale;
+              const __half hi = __float2half_rn(as);
+              const __half lo = __float2half_rn(__fsub_rn(as, __half2float(hi)));
+              h[e] = __half_as_ushort(hi);
+              l[e] = __half_as_ushort(lo);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(a[e]);
+              const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(a[e], __bfloat162float(hi)));
+              h[e] = __bfloat16_as_ushort(hi);
+              l[e] = __bfloat16_as_ushort(lo);
+            }
           }
           *reinterpret_cast<uint2*>(sp.a_hi + (size_t)i * p.D + j0) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
           *reinterpret_cast<uint2*>(sp.a_lo + (size_t)i * p.D + j0) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
@@ -321,146 +333,123 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
   }
 }
 
-// The ambiguous entries (mode 2): 16 entries x 64 columns per tile, 128
-// threads, 2 rows x 4 columns each (16 lanes x 4 columns cover the 64-column
-// tile as in the kernel above). K in steps of 32 through a 4-stage ring of
-// asynchronous copies: the entries' rows and o as they are, R from its
-// transposed copy (contiguous 64-column rows of R^T); each stage's a = x - o
-// is formed in shared memory in K-major order before use. A fixed grid walks
+// The ambiguous entries (mode 2; split-operand paths only, so D % 256 == 0):
+// 16 entries x 64 columns per CTA, 4 warps of 4 entries, 2 entries x 4
+// columns per lane: lanes 0-15 take entries 0-1 of the warp, lanes 16-31
+// entries 2-3, and lane tx = lane & 15 columns 4 tx .. 4 tx + 3 of the
+// 64-column tile, the layout the tile reduction expects. The entries' rows of
+// x, o and rows of R^T land by cp.async in a 4-stage ring; once a stage has
+// landed, one pass forms a = fl(x - o) K-major, so that the inner loop is an
+// 8-byte and a 16-byte shared load and eight FMAs per k: every z stays one
+// FMA chain over j ascending. The list is short (a few hundred entries) and
+// each chain is D FMAs long, so the time is set by the busiest SM: small
+// tiles (about two CTAs of 4 warps per SM for 350 entries at D = 1024, up to
+// four resident) keep the FMA work even across the SMs. A fixed grid walks
 // the entry tiles, so a short list still spreads over the SMs.
-constexpr int kLsN = 64, kLsK = 32, kLsStages = 4;
-constexpr int kSrListRows = 16;                  // entries per tile of the list product (8 measured slower)
-constexpr int kSrListThreads = 128;              // two entries x 4 columns per thread (256 threads, one entry each: slower)
-constexpr int kLsLdA = kLsK + 4, kLsLdB = kLsN + 4;
+constexpr int kLsE = 16, kLsN = 64, kLsK = 32, kLsStages = 4, kLsThreads = 128;
+constexpr int kLsLdX = kLsK + 4, kLsLdB = kLsN + 4, kLsLdA = kLsE + 4;   // floats per row
+constexpr size_t kLsSmem =
+    sizeof(float) * ((size_t)kLsStages * (kLsE * kLsLdX + kLsK + kLsK * kLsLdB) + (size_t)kLsK * kLsLdA);
 
-// kLsM entries per tile, kLsThreads threads: 16 column groups x kLsThreads / 16
-// row groups, RPT = kLsM * 16 / kLsThreads entries per thread.
-template <bool VEC, int kLsM, int kLsThreads>
 __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
   griddep_wait();                                  // the previous kernel of the generation is done
   griddep_launch_dependents();
-  constexpr int RPT = kLsM * 16 / kLsThreads;
-  static_assert(RPT == 1 || RPT == 2, "one or two entries per thread");
-  constexpr int kLsLdT = kLsM + 4;
   const GenParams& p = sp.g;
-  __shared__ __align__(16) float Araw[kLsStages][kLsM][kLsLdA];
-  __shared__ __align__(16) float Osh[kLsStages][kLsK];
-  __shared__ __align__(16) float Bsh[kLsStages][kLsK][kLsLdB];
-  __shared__ __align__(16) float At[kLsK][kLsLdT];
-  __shared__ const float* rowp[kLsM];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;   // rows RPT ty .. RPT ty + RPT - 1
+  extern __shared__ __align__(16) float ls_smem[];
+  float* Xs = ls_smem;                             // [stage][entry][kLsLdX]: raw x
+  float* Os = Xs + kLsStages * kLsE * kLsLdX;      // [stage][k]: o
+  float* Bs = Os + kLsStages * kLsK;               // [stage][k][kLsLdB]: R^T rows
+  float* As = Bs + kLsStages * kLsK * kLsLdB;      // [k][kLsLdA]: a per entry
+  __shared__ const float* rowp[kLsE];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int tx = lane & 15;
+  const int ebase = warp * 4 + (lane >> 4) * 2;    // the lane's first entry in the tile
   const int n0 = blockIdx.x * kLsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
-  const int KS = (p.D + kLsK - 1) / kLsK;
+  const int KS = p.D / kLsK;
 
-  // one stage: A kLsM rows x 8 chunks (row t >> 3, chunk t & 7), o 8 chunks
-  // (threads 0..7), B 32 rows of R^T x 16 chunks (q = t + 128 i: row q >> 4,
-  // chunk q & 15); out-of-range pieces are zero-filled
+  // one stage: x 16 entries x 8 chunks of 16 bytes (one per thread), o 8
+  // chunks, R^T 32 rows x 16 chunks (4 per thread); entries past the list
+  // read zeros
   auto issue = [&](int step) {
     const int st = step % kLsStages, k0 = step * kLsK;
-    if (t < 8 * kLsM) {
-      const int m = t >> 3, c = (t & 7) * 4, j = k0 + c;
+    {
+      const int m = t >> 3, c = (t & 7) * 4;
       const float* xa = rowp[m];
-      if constexpr (VEC) {
-        const bool ok = xa && j < p.D;
-        cp_async16(sr_smem_u32(&Araw[st][m][c]), ok ? xa + j : sp.shift, ok ? 16u : 0u);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool ok = xa && j + u < p.D;
-          cp_async4(sr_smem_u32(&Araw[st][m][c + u]), ok ? xa + j + u : sp.shift, ok ? 4u : 0u);
-        }
-      }
+      cp_async16(sr_smem_u32(Xs + (st * kLsE + m) * kLsLdX + c), xa ? xa + k0 + c : sp.shift, xa ? 16u : 0u);
     }
-    if (t < kLsK / 4) {
-      const int c = t * 4, j = k0 + c;
-      if constexpr (VEC) {
-        const bool ok = j < p.D;
-        cp_async16(sr_smem_u32(&Osh[st][c]), ok ? sp.shift + j : sp.shift, ok ? 16u : 0u);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool ok = j + u < p.D;
-          cp_async4(sr_smem_u32(&Osh[st][c + u]), ok ? sp.shift + j + u : sp.shift, ok ? 4u : 0u);
-        }
-      }
-    }
+    if (t < kLsK / 4) cp_async16(sr_smem_u32(Os + st * kLsK + 4 * t), sp.shift + k0 + 4 * t, 16u);
 #pragma unroll
     for (int i = 0; i < (kLsK * kLsN / 4) / kLsThreads; ++i) {
-      const int q = t + kLsThreads * i;
-      const int kr = q >> 4, c = (q & 15) * 4, j = k0 + kr, n = n0 + c;
-      if constexpr (VEC) {
-        const bool ok = j < p.D && n < p.D;
-        cp_async16(sr_smem_u32(&Bsh[st][kr][c]), ok ? sp.rot_t + (size_t)j * p.D + n : sp.rot_t, ok ? 16u : 0u);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool ok = j < p.D && n + u < p.D;
-          cp_async4(sr_smem_u32(&Bsh[st][kr][c + u]), ok ? sp.rot_t + (size_t)j * p.D + n + u : sp.rot_t,
-                    ok ? 4u : 0u);
-        }
-      }
+      const int q = t + kLsThreads * i, kr = q >> 4, c = (q & 15) * 4;
+      cp_async16(sr_smem_u32(Bs + (st * kLsK + kr) * kLsLdB + c), sp.rot_t + (size_t)(k0 + kr) * p.D + n0 + c, 16u);
     }
   };
 
-  for (int r0 = blockIdx.y * kLsM; r0 < nrows; r0 += gridDim.y * kLsM) {
+  for (int r0 = blockIdx.y * kLsE; r0 < nrows; r0 += gridDim.y * kLsE) {
     __syncthreads();                                // rowp and the stages are reused
-    if (t < kLsM) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
+    if (t < kLsE) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
     __syncthreads();
 #pragma unroll
     for (int s0 = 0; s0 < kLsStages - 1; ++s0) {
       if (s0 < KS) issue(s0);
       cp_async_commit();
     }
-    float acc[RPT][4];
+    float acc[2][4];
 #pragma unroll
-    for (int a = 0; a < RPT; ++a)
+    for (int e = 0; e < 2; ++e)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+      for (int c = 0; c < 4; ++c) acc[e][c] = 0.0f;
     for (int step = 0; step < KS; ++step) {
       cp_async_wait<kLsStages - 2>();
-      __syncthreads();                              // this stage landed; the previous step is done
+      __syncthreads();                              // this stage landed; every lane is done with As and
+                                                    // with the slot refilled next
       if (step + kLsStages - 1 < KS) issue(step + kLsStages - 1);
       cp_async_commit();
       const int st = step % kLsStages;
-#pragma unroll
-      for (int i = 0; i < kLsM * kLsK / kLsThreads; ++i) {   // a = x - o, K-major
-        const int e = t + kLsThreads * i, m = e % kLsM, k = e / kLsM;
-        At[k][m] = __fsub_rn(Araw[st][m][k], Osh[st][k]);
+      {                                             // a = fl(x - o): k = t mod 32, entries 4 (t / 32) ..
+        const int k = t & 31, m0 = (t >> 5) * 4;
+        const float* xs = Xs + (st * kLsE + m0) * kLsLdX + k;
+        const float o = Os[st * kLsK + k];
+        *reinterpret_cast<float4*>(As + k * kLsLdA + m0) =
+            make_float4(__fsub_rn(xs[0], o), __fsub_rn(xs[kLsLdX], o), __fsub_rn(xs[2 * kLsLdX], o),
+                        __fsub_rn(xs[3 * kLsLdX], o));
       }
       __syncthreads();
+      const float* as = As + ebase;
+      const float* bs = Bs + st * kLsK * kLsLdB + 4 * tx;
 #pragma unroll 8
-      for (int kk = 0; kk < kLsK; ++kk) {
-        float ar[RPT];
-        if constexpr (RPT == 2) {
-          const float2 av = *reinterpret_cast<const float2*>(&At[kk][ty * 2]);
-          ar[0] = av.x;
-          ar[RPT - 1] = av.y;
-        } else {
-          ar[0] = At[kk][ty];
-        }
-        const float4 bv = *reinterpret_cast<const float4*>(&Bsh[st][kk][tx * 4]);
-        const float br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-        for (int a = 0; a < RPT; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ar[a], br[b], acc[a][b]);
+      for (int k = 0; k < kLsK; ++k) {
+        const float2 av = *reinterpret_cast<const float2*>(as + k * kLsLdA);
+        const float4 bv = *reinterpret_cast<const float4*>(bs + k * kLsLdB);
+        acc[0][0] = fmaf(av.x, bv.x, acc[0][0]);
+        acc[0][1] = fmaf(av.x, bv.y, acc[0][1]);
+        acc[0][2] = fmaf(av.x, bv.z, acc[0][2]);
+        acc[0][3] = fmaf(av.x, bv.w, acc[0][3]);
+        acc[1][0] = fmaf(av.y, bv.x, acc[1][0]);
+        acc[1][1] = fmaf(av.y, bv.y, acc[1][1]);
+        acc[1][2] = fmaf(av.y, bv.z, acc[1][2]);
+        acc[1][3] = fmaf(av.y, bv.w, acc[1][3]);
       }
     }
     cp_async_wait<0>();
 #pragma unroll
-    for (int a = 0; a < RPT; ++a) {
-      const int e = r0 + ty * RPT + a;
+    for (int e = 0; e < 2; ++e) {
+      const int ent = r0 + ebase + e;
       float sg, sw;
-      sr_tile_reduce(sp, acc[a], n0 + tx * 4, sg, sw);
-      if (tx == 0 && e < nrows) {
-        sp.part2_g[(size_t)e * sp.nct2 + blockIdx.x] = sg;
-        sp.part2_w[(size_t)e * sp.nct2 + blockIdx.x] = sw;
+      sr_tile_reduce(sp, acc[e], n0 + 4 * tx, sg, sw);
+      if (tx == 0 && ent < nrows) {
+        sp.part2_g[(size_t)ent * sp.nct2 + blockIdx.x] = sg;
+        sp.part2_w[(size_t)ent * sp.nct2 + blockIdx.x] = sw;
       }
     }
   }
+}
+
+cudaError_t prepare_sr_list() {
+  return cudaFuncSetAttribute(sr_gemm_fp32_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLsSmem);
 }
 
 // R^T for the list kernel's contiguous B tiles (once, at set-up).
@@ -493,21 +482,22 @@ __device__ __forceinline__ float sr_row_value(const float* pg, int nct) {
   return (f != f) ? __int_as_float(0x7F800000) : f;
 }
 
-// Bound on |f_BF16 - f_FP32path| of one row from n^2 = |a|_2^2, the row's
-// sum_k w_k |z_k| and its value f.
-// Worst case: |dz_k| <= delta = c n for every k; Rastrigin |dg| <= delta (2|z|
-// + 20 pi + 3 delta); elliptic |dg_k| <= w_k delta (2|z_k| + delta); plus the
-// reductions' relative error.
+// Bound on |f_split - f_FP32path| of one row (BF16 or FP16 split operands)
+// from n^2 = |a|_2^2, the row's sum_k w_k |z_k| and its value f.
+// Worst case: |dz_k| <= delta = c n + delta_abs for every k; Rastrigin |dg| <=
+// delta (2|z| + 20 pi + 3 delta); elliptic |dg_k| <= w_k delta (2|z_k| +
+// delta); plus the reductions' relative error.
 // Probabilistic: the first-order change sum_k g'(z_k) dz_k is a sum of
 // independent zero-mean terms (operand-split residuals, accumulation
 // roundings) whose bounds give the standard deviations; the g evaluations and
 // the sums over k add theirs. The tensor cores' FP32 accumulator rounds
 // toward zero, which shrinks every |z_k| a little: one rounding of at most
-// 2^-23 |z_k| per MMA step bounds that bias. Second-order terms are bounded
-// by the mean of |dz|_2^2 with a factor 2.
+// 2^-23 |z_k| per MMA step of the leading product bounds that bias, and the
+// correction products' steps, on partial sums ~2 u_s smaller, add a term in
+// n H. Second-order terms are bounded by the mean of |dz|_2^2 with a factor 2.
 __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, float f, int D, const SrBound& b) {
   if (b.mode == 1) {
-    const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f;
+    const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f + b.delta_abs;
     float e;
     if (obj == kSrElliptic) e = delta * (2.0f * sumw + delta * b.sum_w);
     else e = delta * (2.0f * sumw + (float)D * (20.0f * 3.14159274f + 3.0f * delta));
@@ -518,10 +508,32 @@ __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, floa
   const float H = (obj == kSrElliptic) ? 2.0f * sqrtf(b.wmax * af * 1.0001f) : 2.0002f * n + b.hconst;
   const float s_rep = b.rep_c * H, s_acc = b.acc_c * n * H, s_ev = b.eval_c * af;
   const float sig = sqrtf(s_rep * s_rep + s_acc * s_acc + s_ev * s_ev);
-  const float bias = b.bias_c * ((obj == kSrElliptic) ? 2.0f * af : n * H);
+  const float bias = b.bias_c * ((obj == kSrElliptic) ? 2.0f * af : n * H) + b.bias_c2 * n * H;
   return (b.lambda * sig + bias + b.quad_a + b.quad_b * norm2) * 1.001f;
 }
 
+// Warp-aggregated updates of the generation's counters: one atomic per warp
+// instead of one per row (every lane of the warp calls these).
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void warp_note_accepts(DevState* st, bool acc, unsigned long long key) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, acc);
+  if (m == 0u) return;                             // uniform across the warp
+  const unsigned long long k = warp_min_u64(acc ? key : ~0ull);
+  if ((threadIdx.x & 31) == __ffs(m) - 1) {
+    atomicMin(&st->best_key, k);
+    atomicAdd(&st->accepts, (unsigned long long)__popc(m));
+  }
+}
+
+// One row per thread (the grid covers N once).
 __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bnd) {
   griddep_wait();                                  // the previous kernel of the generation is done
   griddep_launch_dependents();
@@ -529,9 +541,14 @@ __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bn
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   uint8_t* slot_out = p.slots + (size_t)((gen + 1) & 1) * p.N;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += gridDim.x * blockDim.x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  if (i == 0) *sp.finish_due = (sp.inc_every > 0 && (gen + 1) % sp.inc_every == 0) ? 1 : 0;
+  int decision = 0;                                // 1 accept, 0 reject, 2 ambiguous
+  float f = 0.0f, bx = 0.0f;
+  if (i < p.N) {
     const int si = slot_in[i];
-    const float f = sr_row_value(sp.part_g + (size_t)i * sp.nct, sp.nct);
+    f = sr_row_value(sp.part_g + (size_t)i * sp.nct, sp.nct);
     float bu = 0.0f;
     if (sp.prec != 0) {
       float sw = 0.0f;
@@ -539,8 +556,8 @@ __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bn
         for (int c = 0; c < sp.nct; ++c) sw += sp.part_w[(size_t)i * sp.nct + c];
       bu = sr_bound(sp.obj, sp.norm2[i], sw, f, p.D, bnd);
     }
-    const float fx = p.fit[i], bx = sp.fit_err[i];
-    int decision;                                    // 1 accept, 0 reject, 2 ambiguous
+    const float fx = p.fit[i];
+    bx = sp.fit_err[i];
     if (bu == 0.0f && bx == 0.0f) decision = (f < fx) ? 1 : 0;
     else if (f + bu < fx - bx) decision = 1;
     else if (f - bu >= fx + bx) decision = 0;
@@ -549,23 +566,41 @@ __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bn
       slot_out[i] = (uint8_t)(1 - si);
       p.fit[i] = f;
       sp.fit_err[i] = bu;
-      atomicMin(&p.st->best_key, best_key_of(f, i));
-      atomicAdd(&p.st->accepts, 1ull);
     } else {
       slot_out[i] = (uint8_t)si;
-    }
-    if (decision == 2) {
-      const unsigned k = atomicAdd(sp.amb_count, bx > 0.0f ? 2u : 1u);
-      sp.amb[k] = i << 1;                            // the trial
-      if (bx > 0.0f) sp.amb[k + 1] = (i << 1) | 1;   // and the parent, when its value is inexact
-      atomicAdd(&p.st->reselected, 1ull);
     }
     if (p.dbg_ftrial) p.dbg_ftrial[i] = f;
     if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)(decision == 1);
   }
+  warp_note_accepts(p.st, decision == 1, best_key_of(f, i));
+  // ambiguous rows: the trial, and the parent when its stored value is inexact,
+  // in consecutive entries; one reservation per warp
+  const unsigned need = (decision == 2) ? (bx > 0.0f ? 2u : 1u) : 0u;
+  unsigned incl = need;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  if (total > 0u) {                                // uniform across the warp
+    const unsigned rows = __popc(__ballot_sync(0xFFFFFFFFu, need > 0u));
+    unsigned base = 0u;
+    if (lane == 31) {
+      base = atomicAdd(sp.amb_count, total);
+      atomicAdd(&p.st->reselected, (unsigned long long)rows);
+    }
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    if (need > 0u) {
+      const unsigned k = base + incl - need;
+      sp.amb[k] = i << 1;                          // the trial
+      if (need == 2u) sp.amb[k + 1] = (i << 1) | 1;  // and the parent
+    }
+  }
 }
 
 // Ambiguous rows: decide with FP32-path values of the trial (and the parent).
+// One entry per thread (the grid covers 2N entries once).
 __global__ void sr_resolve_kernel(const __grid_constant__ SrParams sp) {
   griddep_wait();                                  // the previous kernel of the generation is done
   griddep_launch_dependents();
@@ -574,28 +609,31 @@ __global__ void sr_resolve_kernel(const __grid_constant__ SrParams sp) {
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   uint8_t* slot_out = p.slots + (size_t)((gen + 1) & 1) * p.N;
   const unsigned n = *sp.amb_count;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    if (sp.amb[e] & 1) continue;                     // parents are read by their trial's entry
-    const int i = sp.amb[e] >> 1;
-    const float fu = sr_row_value(sp.part2_g + (size_t)e * sp.nct2, sp.nct2);
+  const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x * blockDim.x >= n) return;        // uniform across the CTA
+  bool acc = false;
+  float fu = 0.0f;
+  int i = 0;
+  if (e < n && !(sp.amb[e] & 1)) {                 // parents are read by their trial's entry
+    i = sp.amb[e] >> 1;
+    fu = sr_row_value(sp.part2_g + (size_t)e * sp.nct2, sp.nct2);
     float fx = p.fit[i];
     if (e + 1 < n && sp.amb[e + 1] == ((i << 1) | 1)) {
       fx = sr_row_value(sp.part2_g + (size_t)(e + 1) * sp.nct2, sp.nct2);
-      p.fit[i] = fx;                                 // the parent's exact FP32-path value
+      p.fit[i] = fx;                               // the parent's exact FP32-path value
       sp.fit_err[i] = 0.0f;
     }
     const int si = slot_in[i];
-    const int acc = (fu < fx) ? 1 : 0;
+    acc = fu < fx;
     if (acc) {
       slot_out[i] = (uint8_t)(1 - si);
       p.fit[i] = fu;
       sp.fit_err[i] = 0.0f;
-      atomicMin(&p.st->best_key, best_key_of(fu, i));
-      atomicAdd(&p.st->accepts, 1ull);
     }
     if (p.dbg_ftrial) p.dbg_ftrial[i] = fu;
     if (p.dbg_accept) p.dbg_accept[i] = (uint8_t)acc;
   }
+  warp_note_accepts(p.st, acc, best_key_of(fu, i));
 }
 
 // Initial evaluation (always the FP32 product, whose partials have nct2
@@ -622,12 +660,11 @@ cudaError_t launch_sr_trial(int xo, int /*vidx*/, const SrParams& sp, int /*bloc
 
 cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cudaStream_t s) {
   const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
-  if (mode == 2) {
-    constexpr int M = kSrListRows, T = kSrListThreads;
-    const int tiles = (max_rows + M - 1) / M;
-    const dim3 grid((unsigned)sp.nct2, (unsigned)std::max(1, std::min(tiles, 128)));
-    if (sp.g.D % 4 == 0) return launch_pdl(sr_gemm_fp32_list_kernel<true, M, T>, grid, dim3(T), 0, s, sp);
-    return launch_pdl(sr_gemm_fp32_list_kernel<false, M, T>, grid, dim3(T), 0, s, sp);
+  if (mode == 2) {                                // split-operand paths: D % 256 == 0
+    if (sp.g.D % kLsN != 0) return cudaErrorInvalidValue;
+    const int tiles = (max_rows + kLsE - 1) / kLsE;
+    const dim3 grid((unsigned)(sp.g.D / kLsN), (unsigned)std::max(1, std::min(tiles, 128)));
+    return launch_pdl(sr_gemm_fp32_list_kernel, grid, dim3(kLsThreads), kLsSmem, s, sp);
   }
   const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
   if (sp.g.D % 4 == 0) return launch_pdl(sr_gemm_fp32_kernel<true>, grid, dim3(256), 0, s, sp, mode);
@@ -651,18 +688,28 @@ cudaError_t launch_sr_store_eval(const SrParams& sp, cudaStream_t s) {
 
 namespace de {
 
-// R -> bf16(R), bf16(R - bf16(R)).
-__global__ void sr_split_kernel(const float* rot, uint16_t* hi, uint16_t* lo, size_t n) {
+// R -> hi(R), lo(R) = the rounded remainder: BF16 halves of R, or FP16
+// halves of 2^sr R (scale = 2^sr, exact).
+__global__ void sr_split_kernel(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, int fp16, float scale) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     const float r = rot[k];
-    const __nv_bfloat16 h = __float2bfloat16_rn(r);
-    hi[k] = __bfloat16_as_ushort(h);
-    lo[k] = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(r, __bfloat162float(h))));
+    if (fp16) {
+      const float rs = r * scale;
+      const __half h = __float2half_rn(rs);
+      hi[k] = __half_as_ushort(h);
+      lo[k] = __half_as_ushort(__float2half_rn(__fsub_rn(rs, __half2float(h))));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(r);
+      hi[k] = __bfloat16_as_ushort(h);
+      lo[k] = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(r, __bfloat162float(h))));
+    }
   }
 }
 
-cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, cudaStream_t s) {
-  sr_split_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(rot, hi, lo, n);
+cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* lo, size_t n, bool fp16, float scale,
+                                     cudaStream_t s) {
+  sr_split_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(rot, hi, lo, n, fp16 ? 1 : 0,
+                                                                                     scale);
   return cudaGetLastError();
 }
 
@@ -678,15 +725,36 @@ cudaError_t launch_sr_split_rotation(const float* rot, uint16_t* hi, uint16_t* l
 // one writes it.
 constexpr int kIncWarps = 8;
 
+// The close of a generation: best value and its generation, the counter, the
+// base row of the next generation, an empty ambiguous list.
+__device__ __forceinline__ void sr_close_generation(DevState* st, long long gnext, unsigned* amb_count) {
+  const float bf = from_ordered_bits((uint32_t)(st->best_key >> 32));
+  if (bf < st->best_f) {
+    st->best_f = bf;
+    st->best_gen = gnext;
+  }
+  st->gen = gnext;
+  st->base_row = (int)(uint32_t)(st->best_key & 0xFFFFFFFFull);
+  *amb_count = 0u;
+}
+
 __global__ void __launch_bounds__(kIncWarps * 32) sr_finish_kernel(const __grid_constant__ SrParams sp, int every,
                                                                   int close) {
   griddep_wait();                                  // the previous kernel of the generation is done
   griddep_launch_dependents();
   const GenParams& p = sp.g;
-  const long long gen = p.st->gen;
-  const long long gnext = close ? gen + 1 : gen;
-  const bool due = every > 0 && gnext % every == 0;
+  // Closing a generation: whether the incumbent is due was recorded by this
+  // generation's selection kernel, so that CTA 0 may close the generation
+  // (write the counter) alone while the other CTAs are still deciding.
+  // Without a close nothing writes the counter.
+  const bool due = close ? (*sp.finish_due != 0) : (every > 0 && p.st->gen % every == 0);
   if (!due && !close) return;                       // uniform across the grid
+  if (!due) {                                       // nothing to re-evaluate: CTA 0 closes alone
+    if (blockIdx.x == 0 && threadIdx.x == 0) sr_close_generation(p.st, p.st->gen + 1, sp.amb_count);
+    return;
+  }
+  const long long gen = p.st->gen;                  // written only by the last CTA below
+  const long long gnext = close ? gen + 1 : gen;
   const int idx = (int)(uint32_t)(p.st->best_key & 0xFFFFFFFFull);
   const bool have = due && idx >= 0 && idx < p.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -732,17 +800,7 @@ __global__ void __launch_bounds__(kIncWarps * 32) sr_finish_kernel(const __grid_
       p.st->incumbent_f64 = f;
       p.st->incumbent_gen = gnext;
     }
-    if (close) {
-      DevState* st = p.st;
-      const float bf = from_ordered_bits((uint32_t)(st->best_key >> 32));
-      if (bf < st->best_f) {
-        st->best_f = bf;
-        st->best_gen = gnext;
-      }
-      st->gen = gnext;
-      st->base_row = (int)(uint32_t)(st->best_key & 0xFFFFFFFFull);
-      *sp.amb_count = 0u;
-    }
+    if (close) sr_close_generation(p.st, gnext, sp.amb_count);
     *sp.inc_count = 0u;
   }
 }

@@ -1,7 +1,11 @@
 // sr_tc.cu — tcgen05 product of the shifted-rotated objectives with a fused
-// fitness epilogue: Z = A' B'^T over K' = 3D, the split BF16 operands
-// concatenated along K as (a_hi, R_hi), (a_lo, R_hi), (a_hi, R_lo), FP32
-// accumulation in tensor memory.
+// fitness epilogue: Z = A' B'^T over K' = 3D, the split operands (BF16, or
+// FP16 of power-of-two-scaled values) concatenated along K as (a_lo, R_hi),
+// (a_hi, R_lo), (a_hi, R_hi), FP32 accumulation in tensor memory. The two
+// correction products come first: their partial sums are about 2^-8 (BF16)
+// or 2^-11 (FP16) of the leading product's, so their 2D/16 accumulation
+// steps add almost nothing to the accumulator's rounding, which the leading
+// D/16 steps then dominate (the error bound counts it that way).
 //
 // One CTA per 128 x 256 output tile; 6 warps:
 //   warp 0      one thread issues 2D tensor loads (TMA, 128-byte swizzle) of
@@ -9,12 +13,13 @@
 //               (full / empty mbarriers);
 //   warp 1      allocates 256 TMEM columns; one thread issues
 //               tcgen05.mma.cta_group::1.kind::f16 (M 128, N 256, K 16, BF16
-//               inputs, FP32 accumulator), commits each stage's MMAs to the
+//               or FP16 inputs, FP32 accumulator), commits each stage's MMAs to the
 //               stage's empty barrier and the last to the accumulator barrier;
 //               frees TMEM at the end;
 //   warps 2..5  read the accumulator with tcgen05.ld (warp w reads TMEM lanes
-//               32 (w mod 4) .. + 31 = its 32 tile rows) and reduce g(z) and
-//               w |z| over the tile's 256 columns into per-row partials.
+//               32 (w mod 4) .. + 31 = its 32 tile rows), undo the operands'
+//               power-of-two scaling (FP16) and reduce g(z) and w |z| over
+//               the tile's 256 columns into per-row partials.
 // Every mbarrier wait is bounded (1 s); on a timeout the kernel records
 // DE_ETIMEOUT, lets issued copies and MMAs drain (bounded), frees TMEM and
 // returns.
@@ -38,6 +43,7 @@ constexpr size_t kTcSmem = 1024 /*alignment slack*/ + kTcStages * (kTcStageA + k
 struct TcParams {
   SrParams sp;
   CUtensorMap ta_hi, ta_lo, tr_hi, tr_lo;
+  uint32_t idesc;          // instruction descriptor (operand type)
 };
 
 // K-major, 128-byte-swizzled shared-memory matrix descriptor: start address,
@@ -53,10 +59,10 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
-// N = 256, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcBN >> 3) << 17) |
-                              ((uint32_t)(kTcBM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (type code 1) or
+// both FP16 (type code 0), both K-major, N = 256, M = 128.
+constexpr uint32_t kTcIdescF16 = (1u << 4) | ((uint32_t)(kTcBN >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
+constexpr uint32_t kTcIdescBF16 = kTcIdescF16 | (1u << 7) | (1u << 10);
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
   asm volatile(
@@ -65,12 +71,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -141,8 +148,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sr_tc_kernel(const __grid_const
         break;
       }
       const int seg = it / KT, kt = it - seg * KT;
-      const CUtensorMap* ma = (seg == 1) ? &tp.ta_lo : &tp.ta_hi;
-      const CUtensorMap* mb = (seg == 2) ? &tp.tr_lo : &tp.tr_hi;
+      const CUtensorMap* ma = (seg == 0) ? &tp.ta_lo : &tp.ta_hi;
+      const CUtensorMap* mb = (seg == 1) ? &tp.tr_lo : &tp.tr_hi;
       const uint32_t fb = smem_u32(full + s);
       mbar_arrive_expect_tx(fb, kTcStageA + kTcStageB);
       tma_load_2d(smem_u32(sA + s * kTcStageA), ma, kt * kTcBK, tile_m * kTcBM, fb);
@@ -164,7 +171,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) sr_tc_kernel(const __grid_const
       const uint32_t a0 = smem_u32(sA + s * kTcStageA), b0 = smem_u32(sB + s * kTcStageB);
 #pragma unroll
       for (int kk = 0; kk < kTcBK / 16; ++kk)
-        umma_bf16(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
+        umma_f16(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), tp.idesc,
+                 (it > 0 || kk > 0) ? 1u : 0u);
       umma_commit(smem_u32(empty + s));
     }
     umma_commit(smem_u32(accum));              // after every MMA issued above has completed
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sr_tc_kernel(const __grid_const
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-          const float z = __uint_as_float(r[c]);
+          const float z = __uint_as_float(r[c]) * sp.z_scale;   // exact: a power of two
           const float w = sr_weight(sp.obj, tile_n * kTcBN + c0 + c, p.ell_k);
           sg += sr_g(sp.obj, z, w);
           sw = fmaf(w, fabsf(z), sw);
@@ -222,14 +230,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-static bool encode_bf16_2d(CUtensorMap* tm, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+static bool encode_half_2d(CUtensorMap* tm, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_outer,
+                           bool fp16) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {inner, outer};
   const cuuint64_t strides[1] = {inner * 2};
   const cuuint32_t box[2] = {(cuuint32_t)kTcBK, box_outer};
   const cuuint32_t estr[2] = {1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+  return enc(tm, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr),
+             dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -256,10 +266,12 @@ cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s) {
   std::memset(&tp, 0, sizeof(tp));
   tp.sp = sp;
   const int N = sp.g.N, D = sp.g.D;
-  if (!encode_bf16_2d(&tp.ta_hi, sp.a_hi, (uint64_t)D, (uint64_t)N, kTcBM) ||
-      !encode_bf16_2d(&tp.ta_lo, sp.a_lo, (uint64_t)D, (uint64_t)N, kTcBM) ||
-      !encode_bf16_2d(&tp.tr_hi, sp.rot_hi, (uint64_t)D, (uint64_t)D, kTcBN) ||
-      !encode_bf16_2d(&tp.tr_lo, sp.rot_lo, (uint64_t)D, (uint64_t)D, kTcBN))
+  const bool fp16 = sp.prec == 3;
+  tp.idesc = fp16 ? kTcIdescF16 : kTcIdescBF16;
+  if (!encode_half_2d(&tp.ta_hi, sp.a_hi, (uint64_t)D, (uint64_t)N, kTcBM, fp16) ||
+      !encode_half_2d(&tp.ta_lo, sp.a_lo, (uint64_t)D, (uint64_t)N, kTcBM, fp16) ||
+      !encode_half_2d(&tp.tr_hi, sp.rot_hi, (uint64_t)D, (uint64_t)D, kTcBN, fp16) ||
+      !encode_half_2d(&tp.tr_lo, sp.rot_lo, (uint64_t)D, (uint64_t)D, kTcBN, fp16))
     return cudaErrorInvalidValue;
   const dim3 grid((unsigned)(D / kTcBN), (unsigned)((N + kTcBM - 1) / kTcBM));
   return launch_pdl(sr_tc_kernel, grid, dim3(kTcThreads), kTcSmem, s, tp);

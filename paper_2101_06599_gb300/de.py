@@ -19,7 +19,7 @@ DE_OK, DE_EINVAL, DE_ENOMEM, DE_ECUDA, DE_ETIMEOUT, DE_ESTATE, DE_EUNSUPPORTED =
 XOVER = {"bin": 0, "exp": 1, "nec": 2}
 OBJECTIVE = {"sphere": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "griewank": 4,
              "elliptic": 5, "sr_rastrigin": 6, "sr_elliptic": 7}
-PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
+PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
 BOUND = {"probabilistic": 0, "worst_case": 1}
 BASE = {"distinct": 0, "random": 1, "offset": 2, "permutation": 3, "best": 4}
 REPAIR = {"clip": 0, "midpoint": 1}

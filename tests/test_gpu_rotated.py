@@ -106,15 +106,17 @@ def test_rotated_identity_matches_plain_objective_shift():
         opt.close()
 
 
-# ---- the tensor-core path: split BF16 operands, interval decisions, FP32 re-evaluation ---------
+# ---- the tensor-core paths: split BF16 / FP16 operands, interval decisions, FP32 re-evaluation --
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
 @pytest.mark.parametrize("N,D,xo,bound", [(256, 256, "nec", "probabilistic"), (300, 512, "bin", "probabilistic"),
                                           (128, 1024, "exp", "probabilistic"), (128, 512, "nec", "worst_case")])
-def test_rotated_bf16_selections_equal_fp32_path(obj, N, D, xo, bound):
-    """Same seed and population on the FP32 path and the BF16 tensor-core path:
-    identical trials and identical selections generation after generation."""
+def test_rotated_bf16_selections_equal_fp32_path(obj, N, D, xo, bound, prec):
+    """Same seed and population on the FP32 path and a split-operand
+    tensor-core path: identical trials and identical selections generation
+    after generation."""
     a, o, R = make(N, D, xo, obj, prec="fp32", seed=5)
-    b, _, _ = make(N, D, xo, obj, prec="bf16", seed=5, bound=bound)
+    b, _, _ = make(N, D, xo, obj, prec=prec, seed=5, bound=bound)
     try:
         lo, hi = W.BOXES[obj]
         pop = W.population(N, D, lo, hi, 55)
@@ -141,9 +143,10 @@ def test_rotated_bf16_selections_equal_fp32_path(obj, N, D, xo, bound):
         b.close()
 
 
-def test_rotated_bf16_against_oracle():
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_rotated_bf16_against_oracle(prec):
     N, D, obj, xo = 200, 256, "sr_rastrigin", "nec"
-    opt, o, R = make(N, D, xo, obj, prec="bf16", seed=9)
+    opt, o, R = make(N, D, xo, obj, prec=prec, seed=9)
     try:
         lo, hi = W.BOXES[obj]
         pop = W.population(N, D, lo, hi, 77)
@@ -161,18 +164,40 @@ def test_rotated_bf16_against_oracle():
         opt.close()
 
 
-# ---- the error bound that decides which BF16 selections are certain ---------------------------
+# ---- the error bound that decides which split-operand selections are certain -----------------
 U, UTC = 2.0 ** -24, 2.0 ** -23
 
 
-def bf16_bound(obj, D, o, box, trial, f, lam=8.0):
-    """The probabilistic bound on |f_BF16 - f_FP32| of each row, written out
-    from its derivation: Hoeffding deviations of the operand-split residuals,
-    of the accumulation roundings and of the g evaluations, the tensor cores'
-    truncation bias, and a second-order term."""
+def scale_exp(m):
+    """s with m 2^s in [2^14, 2^15): the FP16 operands' power-of-two scaling."""
+    s = 14 - int(np.floor(np.log2(m)))
+    while m * 2.0 ** s >= 32768.0:
+        s -= 1
+    while m * 2.0 ** s < 16384.0:
+        s += 1
+    return s
+
+
+def split_bound(prec, obj, D, o, R, box, trial, f, lam=8.0):
+    """The probabilistic bound on |f_split - f_FP32| of each row, written out
+    from its derivation: Hoeffding deviations of the operand-split residuals
+    (unit roundoff u_s of the halves, plus FP16's subnormal floor), of the
+    accumulation roundings (the leading product's D additions and the
+    corrections' 2D on partial sums 2.01 u_s smaller) and of the g
+    evaluations, the tensor cores' truncation bias (D/16 leading steps, 2D/16
+    correction steps), and a second-order term."""
     lo, hi = box
     o64 = o.astype(np.float64)
     amax = max(np.max(np.abs(lo - o64)), np.max(np.abs(hi - o64))) * (1 + 2.0 ** -22)
+    if prec == "fp16":
+        us = 2.0 ** -11
+        fa = 2.0 ** (-25 - scale_exp(amax))
+        fr = 2.0 ** (-25 - scale_exp(float(np.max(np.abs(R.astype(np.float64))))))
+    else:
+        us, fa, fr = 2.0 ** -8, 0.0, 0.0
+    rep = 1.005 * us * us * amax + fa + fr * np.sqrt(D) * amax
+    cs = 2.01 * us
+    acc2 = UTC ** 2 * (1 + 2 * cs ** 2) + U ** 2
     a = (trial - o[None, :]).astype(np.float32).astype(np.float64)
     n2 = (a * a).sum(1)
     n = np.sqrt(n2)
@@ -180,29 +205,31 @@ def bf16_bound(obj, D, o, box, trial, f, lam=8.0):
     if obj == "sr_elliptic":
         wmax = 10.0 ** 6
         H = 2 * np.sqrt(wmax * af)
-        bias = (3 * D / 16) * UTC * 2 * af
+        bias = (D / 16) * UTC * 2 * af
         g2half = wmax
     else:
         H = 2 * n + 20 * np.pi * np.sqrt(D)
-        bias = (3 * D / 16) * UTC * n * H
+        bias = (D / 16) * UTC * n * H
         g2half = 1 + 20 * np.pi ** 2
-    s_rep = np.sqrt(3) * 1.005 * 2.0 ** -16 * amax * H
-    s_acc = 4 * np.sqrt(3 * UTC ** 2 + U ** 2) * n * H
+    bias = bias + (2 * D / 16) * UTC * cs * 4 * n * H
+    s_rep = np.sqrt(3) * rep * H
+    s_acc = 4 * np.sqrt(acc2) * n * H
     s_ev = U * (np.sqrt(2 * (D + D // 256)) + 12) * af
-    quad = g2half * 2 * D * (3 * 2.0 ** -32 * amax ** 2 + (3 * UTC ** 2 + U ** 2) * 16 * n2)
+    quad = g2half * 2 * D * (3 * rep ** 2 + acc2 * 16 * n2)
     return lam * np.sqrt(s_rep ** 2 + s_acc ** 2 + s_ev ** 2) + bias + quad
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
 @pytest.mark.parametrize("D", [256, 1024, 2048])
-def test_rotated_bf16_error_within_bound(obj, D):
-    """Raw BF16-path values (almost no margin, so nearly every row is decided
+def test_rotated_bf16_error_within_bound(obj, D, prec):
+    """Raw split-path values (almost no margin, so nearly every row is decided
     on them) against the FP32 path's values on the same parents and trials,
     at the start and after 100 generations: every row's difference stays well
     inside the bound the selection uses."""
     N = 1024
     a, o, R = make(N, D, "nec", obj, prec="fp32", seed=11)
-    b, _, _ = make(N, D, "nec", obj, prec="bf16", seed=11, margin_sigmas=1e-6)
+    b, _, _ = make(N, D, "nec", obj, prec=prec, seed=11, margin_sigmas=1e-6)
     try:
         done = 0
         for G0 in (0, 100):
@@ -216,24 +243,65 @@ def test_rotated_bf16_error_within_bound(obj, D):
             tb, fb, _, _ = b.debug_step()
             done += 1
             assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
-            B = bf16_bound(obj, D, o, W.BOXES[obj], tb, fb)
+            B = split_bound(prec, obj, D, o, R, W.BOXES[obj], tb, fb)
             r = np.abs(fb.astype(np.float64) - fa) / B
-            print("D=%d %s gen %d: max |f_bf16 - f_fp32| / bound = %.3f, mean signed (f_bf16 - f_fp32) / bound = %.3f"
-                  % (D, obj, G0, r.max(), float(np.mean((fb.astype(np.float64) - fa) / B))))
+            print("%s D=%d %s gen %d: max |f_split - f_fp32| / bound = %.3f, mean signed (f_split - f_fp32) / bound "
+                  "= %.3f" % (prec, D, obj, G0, r.max(), float(np.mean((fb.astype(np.float64) - fa) / B))))
             assert r.max() <= 0.25, r.max()
     finally:
         a.close()
         b.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
-def test_rotated_bf16_lockstep_full_size(obj):
+@pytest.mark.parametrize("spread", [1e-2, 1e-5, 1e-7])
+def test_rotated_split_near_the_optimum(obj, prec, spread):
+    """A population within `spread` of the optimum o: |x - o| far below the
+    box's reach, where FP16 remainders of 2^sa (x - o) fall into the
+    subnormal range. The raw split values stay inside the bound (which counts
+    that floor), and with the default margin the selections are the FP32
+    path's, generation after generation."""
+    N, D = 512, 256
+    a, o, R = make(N, D, "nec", obj, prec="fp32", seed=21)
+    b, _, _ = make(N, D, "nec", obj, prec=prec, seed=21)
+    c, _, _ = make(N, D, "nec", obj, prec=prec, seed=21, margin_sigmas=1e-6)
+    try:
+        rng = np.random.default_rng(4)
+        pop = (o[None, :].astype(np.float64) + spread * rng.uniform(-1.0, 1.0, size=(N, D))).astype(np.float32)
+        for opt in (a, b, c):
+            opt.set_population(pop)
+        for g in range(3):
+            ta, fa, acca, _ = a.debug_step()
+            tb, fb, accb, _ = b.debug_step()
+            tc, fc, _, _ = c.debug_step()
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            assert np.array_equal(ta.view(np.uint32), tc.view(np.uint32))
+            assert np.array_equal(acca, accb), "generation %d: selections differ" % g
+            B = split_bound(prec, obj, D, o, R, W.BOXES[obj], tc, fc)
+            r = np.abs(fc.astype(np.float64) - fa) / B
+            print("%s %s spread %g gen %d: max |f_split - f_fp32| / bound = %.3f" % (prec, obj, spread, g, r.max()))
+            assert r.max() <= 0.25, r.max()
+            c.set_population(a.population()[0])      # the raw-decision copy follows the FP32 path
+        pa, _ = a.population()
+        pb, _ = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+    finally:
+        a.close()
+        b.close()
+        c.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
+def test_rotated_bf16_lockstep_full_size(obj, prec):
     """The shifted-rotated workload at its full size (N = 4096, D = 1024):
-    the BF16 path with its default bound makes the FP32 path's selections in
-    every one of 30 generations, re-evaluating a small share of rows."""
+    the split-operand path with its default bound makes the FP32 path's
+    selections in every one of 30 generations, re-evaluating a small share of
+    rows."""
     N, D, G = 4096, 1024, 30
     a, o, R = make(N, D, "nec", obj, prec="fp32", seed=1, every=10)
-    b, _, _ = make(N, D, "nec", obj, prec="bf16", seed=1, every=10)
+    b, _, _ = make(N, D, "nec", obj, prec=prec, seed=1, every=10)
     try:
         for g in range(G):
             ta, fa, acca, _ = a.debug_step()
@@ -249,7 +317,7 @@ def test_rotated_bf16_lockstep_full_size(obj):
         x, f, idx, _ = b.best()
         ref = O.evaluate(obj, x, shift=o, rot=R)
         assert sb["incumbent_f64"] == pytest.approx(ref, rel=1e-12)
-        print("%s: rows re-evaluated in FP32: %.2f%%" % (obj, 100.0 * sb["reselected"] / (N * G)))
+        print("%s %s: rows re-evaluated in FP32: %.2f%%" % (prec, obj, 100.0 * sb["reselected"] / (N * G)))
         assert sb["reselected"] < 0.2 * N * G
     finally:
         a.close()
