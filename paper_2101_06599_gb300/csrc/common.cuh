@@ -155,15 +155,38 @@ __device__ __forceinline__ float clip_box(float v, float lo, float hi) {
 // Bound repair of a mutant gene v whose target (parent) gene is x, itself in
 // the box: clip to [lo, hi], or (repair = 1) the midpoint between the
 // violated bound and x, fl(fl(bound + x) 0.5), which stays in the box.
-__device__ __forceinline__ float repair_gene(float v, float x, const GenParams& p) {
-  if (v < p.lo) return p.repair ? __fmul_rn(__fadd_rn(p.lo, x), 0.5f) : p.lo;
-  if (v > p.hi) return p.repair ? __fmul_rn(__fadd_rn(p.hi, x), 0.5f) : p.hi;
+__device__ __forceinline__ float midpoint_box(float v, float x, float lo, float hi) {
+  if (v < lo) return __fmul_rn(__fadd_rn(lo, x), 0.5f);
+  if (v > hi) return __fmul_rn(__fadd_rn(hi, x), 0.5f);
   return v;
+}
+__device__ __forceinline__ float repair_gene(float v, float x, const GenParams& p) {
+  return p.repair ? midpoint_box(v, x, p.lo, p.hi) : clip_box(v, p.lo, p.hi);
 }
 
 // Eq. (1) for one gene, each operation rounded once: x1 + F (x2 - x3).
 __device__ __forceinline__ float mutate(float x1, float x2, float x3, float F) {
   return __fadd_rn(x1, __fmul_rn(F, __fsub_rn(x2, x3)));
+}
+
+// The masked genes (bits of m) of one float4 slot v of a target row take the
+// mutant x1 + F (x2 - x3) of the donor slots a1, a2, a3, repaired. The repair
+// mode is tested once per slot (uniform across the launch), so clipping, the
+// common case, stays two comparisons per gene.
+template <int kRepair = -1>                      // 0 clip, 1 midpoint, -1 as p.repair says
+__device__ __forceinline__ void mutate_slot(float4& v, const float4& a1, const float4& a2, const float4& a3,
+                                            unsigned m, const GenParams& p) {
+  if (kRepair == 0 || (kRepair < 0 && !p.repair)) {
+    if (m & 1u) v.x = clip_box(mutate(a1.x, a2.x, a3.x, p.F), p.lo, p.hi);
+    if (m & 2u) v.y = clip_box(mutate(a1.y, a2.y, a3.y, p.F), p.lo, p.hi);
+    if (m & 4u) v.z = clip_box(mutate(a1.z, a2.z, a3.z, p.F), p.lo, p.hi);
+    if (m & 8u) v.w = clip_box(mutate(a1.w, a2.w, a3.w, p.F), p.lo, p.hi);
+  } else {
+    if (m & 1u) v.x = midpoint_box(mutate(a1.x, a2.x, a3.x, p.F), v.x, p.lo, p.hi);
+    if (m & 2u) v.y = midpoint_box(mutate(a1.y, a2.y, a3.y, p.F), v.y, p.lo, p.hi);
+    if (m & 4u) v.z = midpoint_box(mutate(a1.z, a2.z, a3.z, p.F), v.z, p.lo, p.hi);
+    if (m & 8u) v.w = midpoint_box(mutate(a1.w, a2.w, a3.w, p.F), v.w, p.lo, p.hi);
+  }
 }
 
 }  // namespace de

@@ -185,10 +185,7 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
       m &= (1u << valid) - 1u;                      // padding genes never cross
       if (m) {
         const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
-        if (m & 1u) x[k].x = repair_gene(mutate(a1.x, a2.x, a3.x, p.F), x[k].x, p);
-        if (m & 2u) x[k].y = repair_gene(mutate(a1.y, a2.y, a3.y, p.F), x[k].y, p);
-        if (m & 4u) x[k].z = repair_gene(mutate(a1.z, a2.z, a3.z, p.F), x[k].z, p);
-        if (m & 8u) x[k].w = repair_gene(mutate(a1.w, a2.w, a3.w, p.F), x[k].w, p);
+        mutate_slot(x[k], a1, a2, a3, m, p);
       }
       if constexpr (XO == kBin) cnt += __popc(m);
     }

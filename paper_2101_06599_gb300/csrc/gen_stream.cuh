@@ -35,7 +35,7 @@ struct StreamRow {
 // The trial slots q = q0 + lane + 32 u of row r; m[u] gets the mask bits.
 // Binomial: the masks are drawn and written to mc[q] (pass 1, kCached false)
 // or read back from it (pass 2).
-template <int XO, bool kCached>
+template <int XO, bool kCached, int kRepair>
 __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const StreamRow& r, int q0, int lane,
                                                    float4 (&v)[kStreamU], unsigned (&m)[kStreamU], uint8_t* mc) {
 #pragma unroll
@@ -80,12 +80,7 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
   }
 #pragma unroll
   for (int u = 0; u < kStreamU; ++u) {
-    if (m[u]) {
-      if (m[u] & 1u) v[u].x = repair_gene(mutate(a1[u].x, a2[u].x, a3[u].x, p.F), v[u].x, p);
-      if (m[u] & 2u) v[u].y = repair_gene(mutate(a1[u].y, a2[u].y, a3[u].y, p.F), v[u].y, p);
-      if (m[u] & 4u) v[u].z = repair_gene(mutate(a1[u].z, a2[u].z, a3[u].z, p.F), v[u].z, p);
-      if (m[u] & 8u) v[u].w = repair_gene(mutate(a1[u].w, a2[u].w, a3[u].w, p.F), v[u].w, p);
-    }
+    if (m[u]) mutate_slot<kRepair>(v[u], a1[u], a2[u], a3[u], m[u], p);
   }
 }
 
@@ -93,7 +88,7 @@ __device__ __forceinline__ void stream_trial_chunk(const GenParams& p, const Str
 // slots of a chunk into two independent partial sums: shorter dependency
 // chains) reduced over the warp; every lane returns the value (NaN as +inf).
 // cnt gets the binomial mask's popcount. Writes the trial to p.dbg_trial when set.
-template <int XO, int OBJ>
+template <int XO, int OBJ, int kRepair>
 __device__ __forceinline__ float stream_row_value(const GenParams& p, const StreamRow& r, int lane, int& cnt,
                                                   uint8_t* mc) {
   Acc s{0.0f, 0.0f, 0.0f}, s2{0.0f, 0.0f, 0.0f};
@@ -102,7 +97,7 @@ __device__ __forceinline__ float stream_row_value(const GenParams& p, const Stre
   for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
     float4 v[kStreamU];
     unsigned m[kStreamU];
-    stream_trial_chunk<XO, false>(p, r, q0, lane, v, m, mc);
+    stream_trial_chunk<XO, false, kRepair>(p, r, q0, lane, v, m, mc);
     if (p.dbg_trial) {
       float4* o = reinterpret_cast<float4*>(p.dbg_trial + (size_t)r.i * p.pitch);
 #pragma unroll
@@ -129,11 +124,15 @@ __device__ __forceinline__ float stream_row_value(const GenParams& p, const Stre
           if (j0 + 4 < p.D && !(lane == 31 && u + 1 == kStreamU)) accum_pair(su, v[u].w, nb);
         }
       } else {
-        if (q < p.D4) {
+        if (j0 + 4 <= p.D) {                       // a full slot: the common case
+          accum_gene<OBJ>(su, v[u].x, j0, p);
+          accum_gene<OBJ>(su, v[u].y, j0 + 1, p);
+          accum_gene<OBJ>(su, v[u].z, j0 + 2, p);
+          accum_gene<OBJ>(su, v[u].w, j0 + 3, p);
+        } else if (q < p.D4) {
           accum_gene<OBJ>(su, v[u].x, j0, p);
           if (j0 + 1 < p.D) accum_gene<OBJ>(su, v[u].y, j0 + 1, p);
           if (j0 + 2 < p.D) accum_gene<OBJ>(su, v[u].z, j0 + 2, p);
-          if (j0 + 3 < p.D) accum_gene<OBJ>(su, v[u].w, j0 + 3, p);
         }
       }
     }
@@ -156,13 +155,13 @@ __device__ __forceinline__ float stream_row_value(const GenParams& p, const Stre
 }
 
 // Pass 2 of a winning row: its trial again, chunk by chunk, stored to `out`.
-template <int XO>
+template <int XO, int kRepair>
 __device__ __forceinline__ void stream_row_store(const GenParams& p, const StreamRow& r, int lane, float4* out,
                                                  uint8_t* mc) {
   for (int q0 = 0; q0 < p.D4; q0 += 32 * kStreamU) {
     float4 v[kStreamU];
     unsigned m[kStreamU];
-    stream_trial_chunk<XO, true>(p, r, q0, lane, v, m, mc);
+    stream_trial_chunk<XO, true, kRepair>(p, r, q0, lane, v, m, mc);
 #pragma unroll
     for (int u = 0; u < kStreamU; ++u) {
       const int q = q0 + lane + 32 * u;
@@ -212,7 +211,9 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
     r.d3 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd3, 0));
 
     int cnt = 0;
-    const float f = stream_row_value<XO, OBJ>(p, r, lane, cnt, mc);
+    // the repair mode is uniform across the launch: one copy of the row code each
+    const float f = p.repair ? stream_row_value<XO, OBJ, 1>(p, r, lane, cnt, mc)
+                             : stream_row_value<XO, OBJ, 0>(p, r, lane, cnt, mc);
     acc = (f < p.fit[i]) ? 1 : 0;
     __syncwarp();                                    // every lane has read fit[i] before lane 0 writes it
     Lrow = (XO == kBin) ? cnt : r.L;
@@ -231,7 +232,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
       // pass 2: the winning trial again, into the other slot buffer
       float4* out = reinterpret_cast<float4*>((si ? p.pop0 : p.pop1) + (size_t)i * p.pitch);
       __syncwarp();                                  // every lane's mask bytes are written
-      stream_row_store<XO>(p, r, lane, out, mc);
+      if (p.repair) stream_row_store<XO, 1>(p, r, lane, out, mc);
+      else stream_row_store<XO, 0>(p, r, lane, out, mc);
     }
   }
   if (lane == 0) {

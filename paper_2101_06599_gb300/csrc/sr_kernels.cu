@@ -110,10 +110,7 @@ __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid
         float4 v = x[u];
         if (m) {
           const float4 a1 = ld_ro(d1 + q), a2 = ld_ro(d2 + q), a3 = ld_ro(d3 + q);
-          if (m & 1u) v.x = repair_gene(mutate(a1.x, a2.x, a3.x, p.F), v.x, p);
-          if (m & 2u) v.y = repair_gene(mutate(a1.y, a2.y, a3.y, p.F), v.y, p);
-          if (m & 4u) v.z = repair_gene(mutate(a1.z, a2.z, a3.z, p.F), v.z, p);
-          if (m & 8u) v.w = repair_gene(mutate(a1.w, a2.w, a3.w, p.F), v.w, p);
+          mutate_slot(v, a1, a2, a3, m, p);
         }
         if constexpr (XO == kBin) cnt += __popc(m);
         st_stream(trow + q, v);
