@@ -174,7 +174,7 @@ def time_variant(DE, torch, N, D, xo, obj, steps, warmup, seed, ramp_s=0.0, samp
         d_acc = st1["accepts"] - st0["accepts"]
         d_msk = st1["masked_genes"] - st0["masked_genes"]
         if opt.kernel() == 3:
-            shape = "gen_stream_kernel<%s, %s>: one warp per row, 8 rows per CTA, chunks of 512 genes, " \
+            shape = "gen_stream_kernel<%s, %s>: one warp per row, 8 rows per CTA, chunks of 256 genes, " \
                     "winning trials recomputed and stored" % (xo.upper(), obj)
         elif opt.kernel() == 2:
             nc, stages, span, cps = opt.pipeline()
