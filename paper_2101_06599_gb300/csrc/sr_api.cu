@@ -34,21 +34,33 @@ namespace de_host {
 // Probabilistic (Hoeffding's inequality over independent zero-mean rounding
 // errors): sum_k g'(z_k) rho_k has standard deviation at most
 // sqrt(3) (1.005 u_s^2 max|a_j| + f_a + f_r sqrt(D) max|a_j|) |g'|_2 (each of
-// the three residual vectors, |R_hi|_2 <= 1.005); the accumulation terms at
+// the three residual vectors, |R_hi|_2 <= 1.005; max|a_j| the row's own, which
+// the trial kernel records); the accumulation terms at
 // most |g'|_2 c_rw |a|_2 sqrt(u_tc^2 (1 + 2 (2.01 u_s)^2) + u^2) when the
 // partial sums stay within c_rw |a|_2 / sqrt(D), c_rw = 4; the g evaluations
-// (<= 12 roundings each) and the sums of D values and nct partials on both
-// paths at most u |f| (sqrt(2 (D + nct)) + 12) because every g is >= 0. The
-// tensor cores' accumulator truncates: the leading product's D / 16 MMA
-// steps (K = 16 each) round each z_k toward zero by at most 2^-23 |z_k|
-// (partial sums taken no larger than |z_k|), a bias of at most
-// (D/16) 2^-23 sum_k |g'(z_k)| |z_k|, which is at most n (2 n + 20 pi sqrt(D))
-// for Rastrigin and 2 |f| for the elliptic function; the corrections' 2D / 16
-// steps, with partial sums within 2.01 u_s c_rw n / sqrt(D), add at most
-// (2D/16) 2^-23 2.01 u_s c_rw n |g'|_2. The second-order term is bounded by
-// max|g''| / 2 times twice the mean of |dz|_2^2.
-static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas, double amax, int nct, double us,
-                          double fa, double fr) {
+// and the sums of D values and their tile partials on both
+// paths: each g carries at most 12 roundings (12 u g, summed: 12 u |f|, every
+// g being >= 0), and each FP32 addition of the sums errs by at most u times
+// its partial sum. The FP32 path adds 63 values inside each 64-column tile
+// (partials within the tile's sum T_c; sum_c T_c^2 <= f_FP32^2 <= 1.21 f^2,
+// the two values of a row being far closer than 10 %)
+// and nct2 tile sums (partials within f_FP32); the split path adds 256
+// values per 256-column tile (partials within that tile's sum T'_c, known to
+// the selection) and nct tile sums. So the sums' deviation is at most
+// u sqrt(((63 + nct2) 1.21 + nct) f^2 + 256 sum_c T'_c^2). The tensor
+// cores' accumulator truncates: under the same model a truncation error is
+// uniform between zero and one ulp toward zero, so the leading product's
+// D / 16 MMA steps (K = 16 each) shift each z_k toward zero by half an ulp,
+// at most 2^-24 |z_k| (partial sums taken no larger than |z_k|), on average,
+// a bias of at most (D/16) 2^-24 sum_k |g'(z_k)| |z_k|, which is at most
+// n (2 n + 20 pi sqrt(D)) for Rastrigin and 2 |f| for the elliptic function,
+// while the errors' fluctuation about that mean is inside the accumulation
+// term; the corrections' 2D / 16 steps, with partial sums within
+// 2.01 u_s c_rw n / sqrt(D), add at most (2D/16) 2^-24 2.01 u_s c_rw n |g'|_2.
+// The second-order term is bounded by max|g''| / 2 times twice the mean of
+// |dz|_2^2.
+static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas, int nct, double us, double fa,
+                          double fr) {
   SrBound b{};
   const double u = std::ldexp(1.0, -24), utc = std::ldexp(1.0, -23);
   const double us2 = us * us, sD = std::sqrt((double)D);
@@ -68,18 +80,22 @@ static SrBound make_bound(int D, int obj, double ell_k, int kind, double sigmas,
   const double pi = 3.14159265358979323846, c_rw = 4.0;
   const double cs = 2.01 * us;                                       // corrections / leading product
   const double acc2 = utc * utc * (1.0 + 2.0 * cs * cs) + u * u;
-  const double rep = 1.005 * us2 * amax + fa + fr * sD * amax;       // per-entry residual scale
   const double g2half = (obj == DE_OBJ_SR_ELLIPTIC) ? std::exp2((double)(D - 1) * ell_k)   // w_max
                                                      : 1.0 + 20.0 * pi * pi;               // (2 + 40 pi^2) / 2
   b.lambda = (float)(sigmas > 0.0 ? sigmas : 8.0);
-  b.rep_c = (float)(std::sqrt(3.0) * rep * 1.001);
+  b.rep_k = (float)((1.005 * us2 + fr * sD) * 1.001);
+  b.rep_f = (float)(fa * 1.001);
   b.acc_c = (float)(c_rw * std::sqrt(acc2) * 1.001);
-  b.eval_c = (float)(u * (std::sqrt(2.0 * (D + nct)) + 12.0) * 1.001);
-  b.quad_a = (float)(g2half * 2.0 * D * 3.0 * rep * rep);
+  const int nct2 = (D + 63) / 64;
+  b.eval_c = (float)(u * 12.0 * 1.001);
+  b.sum_f2 = (float)((63.0 + nct2) * 1.21 + nct);
+  b.sum_t2 = 256.0f;
+  b.sum_u = (float)(u * 1.001);
+  b.quad_a = (float)(g2half * 2.0 * D * 3.0 * 1.001);
   b.quad_b = (float)(g2half * 2.0 * D * acc2 * c_rw * c_rw);
   b.hconst = (float)(20.0 * pi * sD);
-  b.bias_c = (float)((D / 16.0) * utc * 1.001);
-  b.bias_c2 = (float)((2.0 * D / 16.0) * utc * cs * c_rw * 1.001);
+  b.bias_c = (float)((D / 16.0) * 0.5 * utc * 1.001);
+  b.bias_c2 = (float)((2.0 * D / 16.0) * 0.5 * utc * cs * c_rw * 1.001);
   b.wmax = (float)((obj == DE_OBJ_SR_ELLIPTIC) ? std::exp2((double)(D - 1) * ell_k) * 1.0001 : 0.0);
   return b;
 }
@@ -111,6 +127,7 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
   sp.part_g = (float*)ctx_alloc(c, (size_t)N * sp.nct * sizeof(float));
   sp.part_w = (float*)ctx_alloc(c, (size_t)N * sp.nct * sizeof(float));
   sp.norm2 = (float*)ctx_alloc(c, (size_t)N * sizeof(float));
+  sp.amax = (float*)ctx_alloc(c, (size_t)N * sizeof(float));
   sp.fit_err = (float*)ctx_alloc(c, (size_t)N * sizeof(float));
   sp.amb = (int*)ctx_alloc(c, 2 * (size_t)N * sizeof(int));
   sp.amb_count = (unsigned*)ctx_alloc(c, sizeof(unsigned));
@@ -120,7 +137,7 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
   sp.inc_count = (unsigned*)ctx_alloc(c, sizeof(unsigned));
   sp.finish_due = (int*)ctx_alloc(c, sizeof(int));
   sp.inc_every = c->incumbent_every;
-  if (!shift || !rot || !sp.part_g || !sp.part_w || !sp.norm2 || !sp.fit_err || !sp.amb || !sp.amb_count ||
+  if (!shift || !rot || !sp.part_g || !sp.part_w || !sp.norm2 || !sp.amax || !sp.fit_err || !sp.amb || !sp.amb_count ||
       !sp.part2_g || !sp.part2_w || !sp.inc_part || !sp.inc_count || !sp.finish_due)
     return DE_ENOMEM;
   sp.shift = shift;
@@ -171,7 +188,7 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
     if (prepare_sr_tc() != cudaSuccess || prepare_sr_list() != cudaSuccess) return DE_ECUDA;
     sp.nct = D / 256;                    // one partial per 256-column tile of the tensor-core product
   }
-  c->sbound = make_bound(D, c->obj, (double)c->p.ell_k, (int)prm->bound, prm->margin_sigmas, amax, sp.nct, us, fa, fr);
+  c->sbound = make_bound(D, c->obj, (double)c->p.ell_k, (int)prm->bound, prm->margin_sigmas, sp.nct, us, fa, fr);
   return sync_stream(c);                 // host shift / rotation consumed
 }
 

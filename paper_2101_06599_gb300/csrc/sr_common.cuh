@@ -31,6 +31,7 @@ struct SrParams {
   float* part_g;           // N x nct: sum of g(z) over the column tile
   float* part_w;           // N x nct: sum of w_k |z_k| (w = 1 Rastrigin, c_k elliptic)
   float* norm2;            // N: |u - o|^2 of the trial (FP32)
+  float* amax;             // N: max_j |u_j - o_j| of the trial
   float* fit_err;          // N: bound on |fit - FP32-path value| of the stored parent
   int* amb;                // ambiguous entries: row << 1 | (1 = parent row)
   unsigned* amb_count;     // number of entries in amb
@@ -44,7 +45,8 @@ struct SrParams {
 
 // Bound constants of the BF16 path (sr_select_kernel). For a row with a =
 // u - o, |a|_2 = n and FP32 value f, H bounds |g'(z)|_2: Rastrigin
-// 2 n + 20 pi sqrt(D) (|g'(z)| <= 2|z| + 20 pi, |z|_2 = n), elliptic
+// min(2 n + 20 pi sqrt(D), (2 + 40 pi^2) n) (|g'(z)| <= 2|z| + 20 pi |sin 2 pi z|
+// <= min(2|z| + 20 pi, (2 + 40 pi^2) |z|), |z|_2 = n), elliptic
 // 2 sqrt(w_max |f|) (sum w^2 z^2 <= w_max sum w z^2).
 struct SrBound {
   int mode;               // 0 probabilistic, 1 worst case
@@ -55,11 +57,13 @@ struct SrBound {
   float sum_w;            // sum of the elliptic weights
   // probabilistic: lambda * sqrt(s_rep^2 + s_acc^2 + s_eval^2) + bias + quad
   float lambda;           // margin in standard deviations
-  float rep_c;            // s_rep = rep_c * H  (operand-split residuals, sqrt(3) u_s^2 max|a_j|)
+  float rep_k, rep_f;     // per-entry residual scale rep = rep_k max_j |a_j| + rep_f (u_s^2, FP16 floors);
+                          // s_rep = sqrt(3) rep H
   float acc_c;            // s_acc = acc_c * n * H (accumulation roundings of both products)
-  float eval_c;           // s_eval = eval_c * |f| (g evaluation and the sums over k)
-  float quad_a, quad_b;   // second-order term quad_a + quad_b * n^2
-  float bias_c;           // truncation bias of the leading product: bias_c * sum_k |g'(z_k)| |z_k|
+  float eval_c;           // g evaluations: eval_c * |f|
+  float sum_u, sum_f2, sum_t2;   // sums over k: sum_u * sqrt(sum_f2 f^2 + sum_t2 sum_c T'_c^2)
+  float quad_a, quad_b;   // second-order term quad_a rep^2 + quad_b n^2
+  float bias_c;           // mean truncation of the leading product: bias_c * sum_k |g'(z_k)| |z_k|
                           // (n H Rastrigin, 2|f| elliptic)
   float bias_c2;          // truncation bias of the two correction products (and the subnormal
                           // halves' absolute part): bias_c2 * n * H

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid
     const float4* d2 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd2, 0));
     const float4* d3 = reinterpret_cast<const float4*>(__shfl_sync(0xFFFFFFFFu, pd3, 0));
     int cnt = 0;
-    float nrm = 0.0f;
+    float nrm = 0.0f, amx = 0.0f;
     for (int q0 = 0; q0 < p.D4; q0 += 32 * kTrialUnroll) {
       if (q0 > 0) {
 #pragma unroll
@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid
           const int j = j0 + e;
           a[e] = (j < p.D) ? __fsub_rn(lane_of(v, e), sp.shift[j]) : 0.0f;
           nrm = fmaf(a[e], a[e], nrm);
+          amx = fmaxf(amx, fabsf(a[e]));
         }
         if (sp.prec != 0) {                        // D % 256 == 0 on this path: 8-byte aligned
           uint32_t h[4], l[4];
@@ -150,11 +151,13 @@ __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, o);
+      amx = fmaxf(amx, __shfl_xor_sync(0xFFFFFFFFu, amx, o));
       cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
     }
     Lrow = (XO == kBin) ? cnt : L;
     if (lane == 0) {
       sp.norm2[i] = nrm;
+      sp.amax[i] = amx;
       if (p.dbg_draws) {
         int* o = p.dbg_draws + 5 * (size_t)i;
         o[0] = d.r1; o[1] = d.r2; o[2] = d.r3; o[3] = d.jrand; o[4] = Lrow;
@@ -487,12 +490,14 @@ __device__ __forceinline__ float sr_row_value(const float* pg, int nct) {
 // Probabilistic: the first-order change sum_k g'(z_k) dz_k is a sum of
 // independent zero-mean terms (operand-split residuals, accumulation
 // roundings) whose bounds give the standard deviations; the g evaluations and
-// the sums over k add theirs. The tensor cores' FP32 accumulator rounds
-// toward zero, which shrinks every |z_k| a little: one rounding of at most
-// 2^-23 |z_k| per MMA step of the leading product bounds that bias, and the
-// correction products' steps, on partial sums ~2 u_s smaller, add a term in
-// n H. Second-order terms are bounded by the mean of |dz|_2^2 with a factor 2.
-__device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, float f, int D, const SrBound& b) {
+// the sums over k add theirs (tsq: the sum of the squares of the row's tile
+// partials). The tensor cores' FP32 accumulator rounds toward zero, which
+// shrinks every |z_k| a little: half an ulp, at most 2^-24 |z_k|, per MMA step
+// of the leading product on average bounds that bias, and the correction
+// products' steps, on partial sums ~2 u_s smaller, add a term in n H.
+// Second-order terms are bounded by the mean of |dz|_2^2 with a factor 2.
+__device__ __forceinline__ float sr_bound(int obj, float norm2, float amax, float sumw, float f, float tsq, int D,
+                                         const SrBound& b) {
   if (b.mode == 1) {
     const float delta = b.delta_per_norm * sqrtf(norm2) * 1.0001f + b.delta_abs;
     float e;
@@ -502,11 +507,18 @@ __device__ __forceinline__ float sr_bound(int obj, float norm2, float sumw, floa
   }
   const float n = sqrtf(norm2) * 1.0001f;
   const float af = fabsf(f);
-  const float H = (obj == kSrElliptic) ? 2.0f * sqrtf(b.wmax * af * 1.0001f) : 2.0002f * n + b.hconst;
-  const float s_rep = b.rep_c * H, s_acc = b.acc_c * n * H, s_ev = b.eval_c * af;
+  // |g'(z)| for Rastrigin: 2|z| + 20 pi |sin 2 pi z| <= min(2|z| + 20 pi, (2 + 40 pi^2) |z|)
+  const float H = (obj == kSrElliptic) ? 2.0f * sqrtf(b.wmax * af * 1.0001f)
+                                       : fminf(2.0002f * n + b.hconst, 396.7843f * n);
+  const float rep = fmaf(b.rep_k, amax * 1.0001f, b.rep_f);
+  const float s_rep = 1.7320509f * rep * H, s_acc = b.acc_c * n * H;
+  const float s_ev = b.eval_c * af + b.sum_u * sqrtf(b.sum_f2 * af * af + b.sum_t2 * tsq);
   const float sig = sqrtf(s_rep * s_rep + s_acc * s_acc + s_ev * s_ev);
   const float bias = b.bias_c * ((obj == kSrElliptic) ? 2.0f * af : n * H) + b.bias_c2 * n * H;
-  return (b.lambda * sig + bias + b.quad_a + b.quad_b * norm2) * 1.001f;
+  // A row with a = 0 exactly has z = 0 exactly on both paths: B = 0. Any other
+  // row keeps a floor, so that terms underflowing in FP32 never leave B = 0.
+  const float B = (b.lambda * sig + bias + b.quad_a * rep * rep + b.quad_b * norm2) * 1.001f;
+  return amax > 0.0f ? fmaxf(B, 1e-36f) : B;
 }
 
 // Warp-aggregated updates of the generation's counters: one atomic per warp
@@ -548,10 +560,14 @@ __global__ void sr_select_kernel(const __grid_constant__ SrParams sp, SrBound bn
     f = sr_row_value(sp.part_g + (size_t)i * sp.nct, sp.nct);
     float bu = 0.0f;
     if (sp.prec != 0) {
-      float sw = 0.0f;
+      float sw = 0.0f, tsq = 0.0f;                 // sum of the tile partials' squares
+      for (int c = 0; c < sp.nct; ++c) {
+        const float t = sp.part_g[(size_t)i * sp.nct + c];
+        tsq = fmaf(t, t, tsq);
+      }
       if (bnd.mode == 1)
         for (int c = 0; c < sp.nct; ++c) sw += sp.part_w[(size_t)i * sp.nct + c];
-      bu = sr_bound(sp.obj, sp.norm2[i], sw, f, p.D, bnd);
+      bu = sr_bound(sp.obj, sp.norm2[i], sp.amax[i], sw, f, tsq * 1.0001f, p.D, bnd);
     }
     const float fx = p.fit[i];
     bx = sp.fit_err[i];
