@@ -236,9 +236,10 @@ int de_set_population(de_ctx *ctx, const float *pop, const float *fit);
 
 /* ---- checkpoint / resume ----------------------------------------------- */
 /* Serialise the whole state (parameters, generation, counters, best,
- * population, fitness). With buf = NULL, *len receives the size needed;
- * otherwise *len must be at least that and receives the bytes written.
- * Synchronises. */
+ * population, fitness; for a shifted-rotated context with a BF16 or FP16
+ * product also the error bounds of the stored fitness values). With buf =
+ * NULL, *len receives the size needed; otherwise *len must be at least that
+ * and receives the bytes written. Synchronises. */
 int de_save(de_ctx *ctx, void *buf, size_t *len);
 
 /* Restore a state saved by de_save into a context created with the same N,

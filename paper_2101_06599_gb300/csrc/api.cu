@@ -545,10 +545,20 @@ int de_set_population(de_ctx* c, const float* pop, const float* fit) {
   return sync_stream(c);
 }
 
+// Checkpoint layout: header, population (N x D), fitness (N); a shifted-rotated
+// context with a split-operand product adds the error bounds of the stored
+// fitness values (N), without which a resumed run would take split values as
+// exact.
+static size_t save_bytes(const de_ctx* c, bool with_err) {
+  return sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float) +
+         (with_err ? (size_t)c->N * sizeof(float) : 0);
+}
+
 int de_save(de_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return DE_EINVAL;
   if (c->batch) return DE_EUNSUPPORTED;
-  const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
+  const bool with_err = c->rotated && c->sp.prec != 0;
+  const size_t need = save_bytes(c, with_err);
   if (!buf) {
     *len = need;
     return DE_OK;
@@ -574,6 +584,10 @@ int de_save(de_ctx* c, void* buf, size_t* len) {
   int rc = de_get_population(c, reinterpret_cast<float*>(o + sizeof(SaveHeader)),
                              reinterpret_cast<float*>(o + sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float)));
   if (rc != DE_OK) return rc;
+  if (with_err &&
+      cudaMemcpyAsync(o + save_bytes(c, false), c->sp.fit_err, (size_t)c->N * sizeof(float), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
+    return DE_ECUDA;
   if (cudaMemcpyAsync(c->host_pinned, c->p.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) !=
       cudaSuccess)
     return DE_ECUDA;
@@ -591,7 +605,10 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
   if (len < sizeof(SaveHeader)) return DE_EINVAL;
   SaveHeader h;
   std::memcpy(&h, buf, sizeof(h));
-  const size_t need = sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float) + (size_t)c->N * sizeof(float);
+  // a split-operand context reads the bounds when present (checkpoints written
+  // before they were stored have none: their values are then taken as exact)
+  const bool with_err = c->rotated && c->sp.prec != 0 && len >= save_bytes(c, true);
+  const size_t need = save_bytes(c, with_err);
   if (h.magic != kSaveMagic || h.version != kSaveVersion || len < need) return DE_EINVAL;
   if (h.N != c->N || h.D != c->D || h.F != c->F || h.CR != c->CR || h.xo != c->xo || h.obj != c->obj ||
       h.lo != c->b.lo || h.hi != c->b.hi || h.seed != c->seed || h.inst != c->inst || h.ackley_b != c->ackley_b ||
@@ -613,7 +630,10 @@ int de_load(de_ctx* c, const void* buf, size_t len) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->p.fit, in + sizeof(SaveHeader) + (size_t)c->N * c->D * sizeof(float),
                         (size_t)c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess && c->rotated)
+  if (e == cudaSuccess && with_err)
+    e = cudaMemcpyAsync(c->sp.fit_err, in + save_bytes(c, false), (size_t)c->N * sizeof(float),
+                        cudaMemcpyHostToDevice, c->stream);
+  else if (e == cudaSuccess && c->rotated)
     e = cudaMemsetAsync(c->sp.fit_err, 0, (size_t)c->N * sizeof(float), c->stream);
   if (e != cudaSuccess) return DE_ECUDA;
   const int rc = sync_stream(c);

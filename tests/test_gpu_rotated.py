@@ -341,6 +341,36 @@ def test_rotated_bf16_lockstep_full_size(obj, prec):
         b.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_rotated_checkpoint_resume(prec):
+    """A split-path run saved after some generations and resumed in a fresh
+    context continues bit for bit like the uninterrupted run (population,
+    fitness, counters): the checkpoint carries the error bounds of the stored
+    values, so split values are not taken as exact after the resume."""
+    N, D = 512, 256
+    a, o, R = make(N, D, "nec", "sr_rastrigin", prec=prec, seed=13)
+    b, _, _ = make(N, D, "nec", "sr_rastrigin", prec=prec, seed=13)
+    c, _, _ = make(N, D, "nec", "sr_rastrigin", prec="fp32", seed=13)
+    try:
+        a.run(7)
+        blob = a.save()
+        assert len(blob) == len(c.save()) + 4 * N          # the bounds: one float per row
+        b.load(blob)
+        a.run(9)
+        b.run(9)
+        pa, fa = a.population()
+        pb, fb = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+        sa, sb = a.stats(), b.stats()
+        for k in ("generation", "accepts", "reselected", "best_gen"):
+            assert sa[k] == sb[k], k
+    finally:
+        a.close()
+        b.close()
+        c.close()
+
+
 def test_rotated_midpoint_repair():
     """The shifted-rotated path's trial kernel with DE_REPAIR_MIDPOINT (F = 1.4
     sends many mutants out of the box): trials bit for bit with the oracle,
