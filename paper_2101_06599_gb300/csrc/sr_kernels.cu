@@ -37,7 +37,7 @@ namespace de {
 constexpr int kTrialWarps = 8, kTrialUnroll = 4;
 
 template <int XO>
-__global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid_constant__ SrParams sp) {
+__global__ void __launch_bounds__(kTrialWarps * 32, 4) sr_trial_kernel(const __grid_constant__ SrParams sp) {
   griddep_wait();                                  // the previous kernel of the generation is done
   griddep_launch_dependents();
   const GenParams& p = sp.g;
@@ -116,10 +116,21 @@ __global__ void __launch_bounds__(kTrialWarps * 32) sr_trial_kernel(const __grid
         st_stream(trow + q, v);
         if (p.dbg_trial) reinterpret_cast<float4*>(p.dbg_trial + (size_t)i * p.pitch)[q] = v;
         float a[4];
+        if (j0 + 4 <= p.D) {                       // a full slot: o by one 16-byte load
+          const float4 o4 = __ldg(reinterpret_cast<const float4*>(sp.shift) + q);
+          a[0] = __fsub_rn(v.x, o4.x);
+          a[1] = __fsub_rn(v.y, o4.y);
+          a[2] = __fsub_rn(v.z, o4.z);
+          a[3] = __fsub_rn(v.w, o4.w);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e;
+            a[e] = (j < p.D) ? __fsub_rn(lane_of(v, e), sp.shift[j]) : 0.0f;
+          }
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int j = j0 + e;
-          a[e] = (j < p.D) ? __fsub_rn(lane_of(v, e), sp.shift[j]) : 0.0f;
           nrm = fmaf(a[e], a[e], nrm);
           amx = fmaxf(amx, fabsf(a[e]));
         }
