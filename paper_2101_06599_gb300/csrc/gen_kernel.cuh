@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
   uint8_t* slot_out = p.slots + (size_t)((gen + 1) & 1) * p.N;
   const int si = slot_in[i];
   const float4* xrow = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)i * p.pitch);
+  // the parent's fitness is only needed at the selection: load it now, off
+  // the generation's chain of dependent steps
+  const float fi = (t == 0) ? p.fit[i] : 0.0f;
 
   // 1. parent row -> registers (all loads in flight before anything waits)
   float4 x[V];
@@ -196,7 +199,6 @@ __global__ void __launch_bounds__(kMaxThreads) gen_kernel(const __grid_constant_
 
   // 4. selection (thread 0)
   if (t == 0) {
-    const float fi = p.fit[i];
     const int acc = (f < fi) ? 1 : 0;
     sh.accept = acc;
     slot_out[i] = (uint8_t)(acc ? 1 - si : si);

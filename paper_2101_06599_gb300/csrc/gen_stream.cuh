@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
   int Lrow = 0, acc = 0;
   if (i < p.N) {                                     // warp-uniform
     const int si = slot_in[i];
+    const float fi = p.fit[i];                       // needed at the selection; loaded off the row's chain
     StreamRow r;
     r.x = reinterpret_cast<const float4*>((si ? p.pop1 : p.pop0) + (size_t)i * p.pitch);
     r.i = i;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 4) gen_stream_kernel(const 
     // the repair mode is uniform across the launch: one copy of the row code each
     const float f = p.repair ? stream_row_value<XO, OBJ, 1>(p, r, lane, cnt, mc)
                              : stream_row_value<XO, OBJ, 0>(p, r, lane, cnt, mc);
-    acc = (f < p.fit[i]) ? 1 : 0;
+    acc = (f < fi) ? 1 : 0;
     __syncwarp();                                    // every lane has read fit[i] before lane 0 writes it
     Lrow = (XO == kBin) ? cnt : r.L;
     if (lane == 0) {
