@@ -341,6 +341,39 @@ def test_rotated_bf16_lockstep_full_size(obj, prec):
         b.close()
 
 
+@pytest.mark.parametrize("obj", ["sr_rastrigin", "sr_elliptic"])
+@pytest.mark.parametrize("scale", [1e-3, 1e3])
+def test_rotated_fp16_scaling_far_from_unit_boxes(obj, scale):
+    """The FP16 operands' power-of-two scaling chosen for a box and shift
+    scaled by 1e-3 and 1e3 (2^sa far from 1): the same trials and selections
+    as the FP32 path over several generations."""
+    N, D = 512, 256
+    o = (W.shift_vector(D, seed=2).astype(np.float64) * scale).astype(np.float32)
+    R = W.rotation(D, seed=3)
+    box = (-100.0 * scale, 100.0 * scale)
+    opts = []
+    try:
+        for prec in ("fp32", "fp16"):
+            opts.append(DE.Optimizer(N, D, F=0.5, CR=0.9, xo="nec", obj=obj, bounds=box, seed=17,
+                                     params={"shift": o, "rotation": R, "prec": prec}))
+        pop = W.population(N, D, box[0], box[1], 19)
+        for opt in opts:
+            opt.set_population(pop)
+        for g in range(4):
+            ta, fa, acca, _ = opts[0].debug_step()
+            tb, fb, accb, _ = opts[1].debug_step()
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            assert np.array_equal(acca, accb), "generation %d: selections differ" % g
+            rel = np.abs(fb.astype(np.float64) - fa) / np.maximum(1e-30, np.abs(fa))
+            assert np.median(rel) < 1e-5, np.median(rel)
+        pa, _ = opts[0].population()
+        pb, _ = opts[1].population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+    finally:
+        for opt in opts:
+            opt.close()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_rotated_checkpoint_resume(prec):
     """A split-path run saved after some generations and resumed in a fresh
