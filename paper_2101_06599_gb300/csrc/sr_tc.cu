@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -184,18 +185,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) sr_tc_kernel(const __grid_const
     const int m = tile_m * kTcBM + 32 * q + lane;
     float sg = 0.0f, sw = 0.0f;
     if (ok) {
+      // one loop per objective (the objective is uniform): no per-value test
+      auto tile_sums = [&](auto obj_tag) {
+        constexpr int OBJ = decltype(obj_tag)::value;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kTcBN; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
+        for (int c0 = 0; c0 < kTcBN; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float z = __uint_as_float(r[c]) * sp.z_scale;   // exact: a power of two
-          const float w = sr_weight(sp.obj, tile_n * kTcBN + c0 + c, p.ell_k);
-          sg += sr_g(sp.obj, z, w);
-          sw = fmaf(w, fabsf(z), sw);
+          for (int c = 0; c < 32; ++c) {
+            const float z = __uint_as_float(r[c]) * sp.z_scale;   // exact: a power of two
+            const float w = sr_weight(OBJ, tile_n * kTcBN + c0 + c, p.ell_k);
+            sg += sr_g(OBJ, z, w);
+            sw = fmaf(w, fabsf(z), sw);
+          }
         }
-      }
+      };
+      if (sp.obj == kSrElliptic) tile_sums(std::integral_constant<int, kSrElliptic>{});
+      else tile_sums(std::integral_constant<int, kSrRastrigin>{});
     } else {
       atomicExch(&p.st->error, 4u);
     }
