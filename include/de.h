@@ -184,6 +184,14 @@ int de_step(de_ctx *ctx);
  * once per distinct count into a CUDA graph and replayed. */
 int de_run(de_ctx *ctx, int32_t generations);
 
+/* Capture and instantiate the graph that de_run(ctx, generations) replays,
+ * without launching it: the population, fitness, best and generation count
+ * are unchanged, and a later de_run of the same count only launches the
+ * graph. A no-op returning DE_OK for counts below 2. DE_EINVAL for a NULL
+ * context or a negative count, DE_ESTATE for a failed context, DE_ECUDA if
+ * the capture or the instantiation fails. */
+int de_prepare_run(de_ctx *ctx, int32_t generations);
+
 /* Block until the context's stream is idle; DE_ECUDA if queued work failed,
  * the device error code (DE_ETIMEOUT) if a kernel recorded one. */
 int de_synchronize(de_ctx *ctx);

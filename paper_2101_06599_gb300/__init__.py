@@ -10,7 +10,7 @@ from .de import (Batch, DEError, Optimizer, de_batch_best, de_batch_create, de_b
                  de_batch_autotune, de_batch_get_groups, de_batch_get_population, de_batch_set_groups,
                  de_batch_set_population, de_batch_size, de_batch_stats, de_best, de_best_async, de_create,
                  de_debug_step, de_destroy, de_get_kernel, de_get_pipeline, de_get_launch, de_get_population, de_load,
-                 de_run, de_save, de_set_kernel, de_set_launch, de_set_pipeline, de_set_population,
+                 de_prepare_run, de_run, de_save, de_set_kernel, de_set_launch, de_set_pipeline, de_set_population,
                  de_stats, de_step, de_strerror, de_synchronize, de_version, load_library,
                  de_nec_step_noalloc, use_torch_allocator, best_record_bytes, parse_best_record)
 
@@ -18,6 +18,6 @@ __all__ = ["Batch", "DEError", "Optimizer", "de_batch_best", "de_batch_create", 
            "de_batch_autotune", "de_batch_get_groups", "de_batch_get_population", "de_batch_set_groups",
            "de_batch_set_population", "de_batch_size", "de_batch_stats", "de_best", "de_best_async", "de_create",
            "de_debug_step", "de_destroy", "de_get_kernel", "de_get_pipeline", "de_get_launch", "de_get_population",
-           "de_load", "de_run", "de_save", "de_set_kernel", "de_set_launch", "de_set_pipeline",
+           "de_load", "de_prepare_run", "de_run", "de_save", "de_set_kernel", "de_set_launch", "de_set_pipeline",
            "de_set_population", "de_stats", "de_step", "de_strerror", "de_synchronize", "de_version",
            "load_library", "de_nec_step_noalloc", "use_torch_allocator", "best_record_bytes", "parse_best_record"]

@@ -395,6 +395,38 @@ int de_step(de_ctx* c) {
   return rc;
 }
 
+// The cached graph of `generations` generations, captured and instantiated on
+// first use. Capture records launches without running them, so the context's
+// device state is unchanged; nullptr on a CUDA error.
+static cudaGraphExec_t run_graph(de_ctx* c, int32_t generations) {
+  auto it = c->graphs.find(generations);
+  if (it != c->graphs.end()) return it->second;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return nullptr;
+  cudaError_t le = cudaSuccess;
+  for (int32_t k = 0; k < generations && le == cudaSuccess; ++k) le = launch_generation(c, c->p);
+  e = cudaStreamEndCapture(c->stream, &graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return nullptr;
+  c->graphs.emplace(generations, exec);
+  return exec;
+}
+
+int de_prepare_run(de_ctx* c, int32_t generations) {
+  if (!c || generations < 0) return DE_EINVAL;
+  if (c->failed) return DE_ESTATE;
+  if (generations <= 1 || c->stream == nullptr) return DE_OK;
+  return run_graph(c, generations) ? DE_OK : DE_ECUDA;
+}
+
 int de_run(de_ctx* c, int32_t generations) {
   if (!c || generations < 0) return DE_EINVAL;
   if (c->failed) return DE_ESTATE;
@@ -406,27 +438,9 @@ int de_run(de_ctx* c, int32_t generations) {
     }
     return DE_OK;
   }
-  auto it = c->graphs.find(generations);
-  if (it == c->graphs.end()) {
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return DE_ECUDA;
-    cudaError_t le = cudaSuccess;
-    for (int32_t k = 0; k < generations && le == cudaSuccess; ++k) le = launch_generation(c, c->p);
-    e = cudaStreamEndCapture(c->stream, &graph);
-    if (le != cudaSuccess || e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return DE_ECUDA;
-    }
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return DE_ECUDA;
-    it = c->graphs.emplace(generations, exec).first;
-  }
-  const cudaError_t e = cudaGraphLaunch(it->second, c->stream);
-  if (e != cudaSuccess) return DE_ECUDA;
+  const cudaGraphExec_t exec = run_graph(c, generations);
+  if (!exec) return DE_ECUDA;
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) return DE_ECUDA;
   c->host_gen += generations;
   return DE_OK;
 }

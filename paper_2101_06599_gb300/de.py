@@ -84,6 +84,7 @@ def load_library(build_if_missing: bool = True):
         "de_destroy": ([vp], None),
         "de_step": ([vp], C.c_int),
         "de_run": ([vp, i32], C.c_int),
+        "de_prepare_run": ([vp, i32], C.c_int),
         "de_synchronize": ([vp], C.c_int),
         "de_best": ([vp, vp, C.POINTER(f64), C.POINTER(i32), C.POINTER(i64)], C.c_int),
         "de_best_async": ([vp, vp], C.c_int),
@@ -228,6 +229,10 @@ def de_step(ctx):
 
 def de_run(ctx, generations):
     _check(load_library().de_run(C.c_void_p(ctx), int(generations)), "de_run")
+
+
+def de_prepare_run(ctx, generations):
+    _check(load_library().de_prepare_run(C.c_void_p(ctx), int(generations)), "de_prepare_run")
 
 
 def de_synchronize(ctx):
@@ -487,6 +492,10 @@ class Batch:
     def run(self, generations):
         de_run(self.ctx, generations)
 
+    def prepare_run(self, generations):
+        """Build the graph that run(generations) replays, without running it."""
+        de_prepare_run(self.ctx, generations)
+
     def synchronize(self):
         de_synchronize(self.ctx)
 
@@ -580,6 +589,10 @@ class Optimizer:
 
     def run(self, generations):
         de_run(self.ctx, generations)
+
+    def prepare_run(self, generations):
+        """Build the graph that run(generations) replays, without running it."""
+        de_prepare_run(self.ctx, generations)
 
     def synchronize(self):
         de_synchronize(self.ctx)

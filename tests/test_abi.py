@@ -112,6 +112,7 @@ def test_crossover_apply_rejects_aliasing_and_bad_counters(lib):
 def test_null_context_calls_are_rejected(lib):
     assert lib.de_step(None) == DE.DE_EINVAL
     assert lib.de_run(None, 3) == DE.DE_EINVAL
+    assert lib.de_prepare_run(None, 3) == DE.DE_EINVAL
     assert lib.de_synchronize(None) == DE.DE_EINVAL
     assert lib.de_best(None, None, None, None, None) == DE.DE_EINVAL
     assert lib.de_batch_autotune(None, 3, None) == DE.DE_EINVAL

@@ -128,6 +128,7 @@ def test_batch_run_graph_stats_and_best():
     try:
         for _ in range(7):
             a.step()
+        b.prepare_run(4)                       # builds the graph only
         b.run(3)
         b.run(4)
         tot_acc = tot_msk = 0

@@ -181,6 +181,41 @@ def test_run_graph_matches_steps_and_stats():
 
 
 @pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
+def test_prepared_run_changes_nothing_until_launched(xo):
+    """de_prepare_run captures the graph without running it: the population,
+    fitness and counters stay as they were, and the prepared runs then give
+    what unprepared ones give."""
+    N, D = 96, 200
+    a, _, _ = make(N, D, xo, "rastrigin", seed=8)
+    b, _, _ = make(N, D, xo, "rastrigin", seed=8)
+    try:
+        p0, f0 = b.population()
+        b.prepare_run(6)
+        b.prepare_run(6)                       # cached: a second call builds nothing
+        b.prepare_run(1)
+        b.prepare_run(0)
+        b.synchronize()
+        p1, f1 = b.population()
+        assert np.array_equal(p0.view(np.uint32), p1.view(np.uint32))
+        assert np.array_equal(f0.view(np.uint32), f1.view(np.uint32))
+        assert b.stats()["generation"] == 0
+        a.run(6)
+        a.run(6)
+        b.run(6)
+        b.run(6)
+        pa, fa = a.population()
+        pb, fb = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+        assert np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+        assert a.stats() == b.stats() and b.stats()["generation"] == 12
+        with pytest.raises(DE.DEError):
+            b.prepare_run(-1)
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("xo", ["bin", "exp", "nec"])
 def test_save_load_resumes_bit_identically(xo):
     N, D = 50, 77
     a, lo, hi = make(N, D, xo, "ackley", CR=0.7, seed=9)

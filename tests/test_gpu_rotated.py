@@ -389,6 +389,7 @@ def test_rotated_checkpoint_resume(prec):
         blob = a.save()
         assert len(blob) == len(c.save()) + 4 * N          # the bounds: one float per row
         b.load(blob)
+        b.prepare_run(9)                                    # graph only: the loaded state is kept
         a.run(9)
         b.run(9)
         pa, fa = a.population()
