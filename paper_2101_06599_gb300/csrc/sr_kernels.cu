@@ -349,15 +349,17 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 // columns per lane: lanes 0-15 take entries 0-1 of the warp, lanes 16-31
 // entries 2-3, and lane tx = lane & 15 columns 4 tx .. 4 tx + 3 of the
 // 64-column tile, the layout the tile reduction expects. The entries' rows of
-// x, o and rows of R^T land by cp.async in a 4-stage ring; once a stage has
+// x, o and rows of R^T land by cp.async in an 8-stage ring (seven stages in
+// flight cover the L2 latency of the short per-stage work); once a stage has
 // landed, one pass forms a = fl(x - o) K-major, so that the inner loop is an
 // 8-byte and a 16-byte shared load and eight FMAs per k: every z stays one
 // FMA chain over j ascending. The list is short (a few hundred entries) and
 // each chain is D FMAs long, so the time is set by the busiest SM: small
-// tiles (about two CTAs of 4 warps per SM for 350 entries at D = 1024, up to
-// four resident) keep the FMA work even across the SMs. A fixed grid walks
-// the entry tiles, so a short list still spreads over the SMs.
-constexpr int kLsE = 16, kLsN = 64, kLsK = 32, kLsStages = 4, kLsThreads = 128;
+// tiles (about two CTAs of 4 warps per SM for 350 entries at D = 1024, two
+// resident with the ring's 92 KB) keep the FMA work even across the SMs. A
+// fixed grid walks the entry tiles, so a short list still spreads over the
+// SMs.
+constexpr int kLsE = 16, kLsN = 64, kLsK = 32, kLsStages = 8, kLsThreads = 128;
 constexpr int kLsLdX = kLsK + 4, kLsLdB = kLsN + 4, kLsLdA = kLsE + 4;   // floats per row
 constexpr size_t kLsSmem =
     sizeof(float) * ((size_t)kLsStages * (kLsE * kLsLdX + kLsK + kLsK * kLsLdB) + (size_t)kLsK * kLsLdA);
