@@ -147,7 +147,7 @@ cudaError_t launch_sr_finish(const SrParams& sp, int every, bool close, cudaStre
 // D % 256 == 0. sr_tc_supported tells whether this build and device have it.
 cudaError_t launch_sr_gemm_tc(const SrParams& sp, cudaStream_t s);
 cudaError_t prepare_sr_tc();
-cudaError_t prepare_sr_list();
+cudaError_t prepare_sr_list(int* ctas);
 bool sr_tc_supported(int D);
 
 constexpr size_t kStagingHeader = 32;

@@ -185,7 +185,7 @@ int sr_setup(de_ctx* c, const de_objparams* prm) {
     if (launch_sr_split_rotation(rot, hi, lo, (size_t)D * D, sp.prec == 3, std::ldexp(1.0f, sr), c->stream) !=
         cudaSuccess)
       return DE_ECUDA;
-    if (prepare_sr_tc() != cudaSuccess || prepare_sr_list() != cudaSuccess) return DE_ECUDA;
+    if (prepare_sr_tc() != cudaSuccess || prepare_sr_list(&sp.list_ctas) != cudaSuccess) return DE_ECUDA;
     sp.nct = D / 256;                    // one partial per 256-column tile of the tensor-core product
   }
   c->sbound = make_bound(D, c->obj, (double)c->p.ell_k, (int)prm->bound, prm->margin_sigmas, sp.nct, us, fa, fr);

@@ -41,6 +41,7 @@ struct SrParams {
   unsigned* inc_count;     // CTAs of the incumbent re-evaluation done (last one sums)
   int inc_every;           // FP64 incumbent every inc_every generations
   int* finish_due;         // set by the selection kernel: the incumbent is due at this close
+  int list_ctas;           // grid of the ambiguous-entry GEMM: one CTA per SM
 };
 
 // Bound constants of the BF16 path (sr_select_kernel). For a row with a =

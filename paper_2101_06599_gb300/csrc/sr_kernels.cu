@@ -345,43 +345,54 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 }
 
 // The ambiguous entries (mode 2; split-operand paths only, so D % 256 == 0):
-// 16 entries x 64 columns per CTA, 4 warps of 4 entries, 2 entries x 4
-// columns per lane: lanes 0-15 take entries 0-1 of the warp, lanes 16-31
-// entries 2-3, and lane tx = lane & 15 columns 4 tx .. 4 tx + 3 of the
-// 64-column tile, the layout the tile reduction expects. The entries' rows of
-// x, o and rows of R^T land by cp.async in an 8-stage ring (seven stages in
-// flight cover the L2 latency of the short per-stage work); once a stage has
-// landed, one pass forms a = fl(x - o) K-major, so that the inner loop is an
-// 8-byte and a 16-byte shared load and eight FMAs per k: every z stays one
-// FMA chain over j ascending. The list is short (a few hundred entries) and
-// each chain is D FMAs long, so the time is set by the busiest SM: small
-// tiles (about two CTAs of 4 warps per SM for 350 entries at D = 1024, two
-// resident with the ring's 92 KB) keep the FMA work even across the SMs. A
-// fixed grid walks the entry tiles, so a short list still spreads over the
-// SMs.
-constexpr int kLsE = 16, kLsN = 64, kLsK = 32, kLsStages = 8, kLsThreads = 128;
+// work items of 16 entries x 64 columns, taken by groups of 4 warps (2
+// entries x 4 columns per lane: lanes 0-15 take entries 0-1 of the warp, lanes
+// 16-31 entries 2-3, and lane tx = lane & 15 columns 4 tx .. 4 tx + 3 of the
+// 64-column tile, the layout the tile reduction expects). Each group has its
+// own 8-stage cp.async ring of the entries' rows of x, o and rows of R^T
+// (seven stages in flight cover the L2 latency of the short per-stage work)
+// and its own named barrier. Once a stage has landed, each warp forms
+// a = fl(x - o) K-major for its own four entries (so only a warp barrier
+// follows), and the inner loop is an 8-byte and a 16-byte shared load and
+// eight FMAs per k: every z stays one FMA chain over j ascending. The list is
+// short (a few hundred entries) and each chain is D FMAs long, so the time is
+// set by the busiest SM. Two groups per CTA and a ring per group that needs
+// more than half an SM's shared memory for the pair put exactly one CTA on
+// each SM; the grid is one CTA per SM, group g of CTA b takes items
+// b + g * grid, b + (2 + g) * grid, ..., so the first items of a short list
+// land on distinct SMs whatever order the CTAs are placed in.
+constexpr int kLsE = 16, kLsN = 64, kLsK = 32, kLsStages = 8, kLsGroupThreads = 128, kLsGroups = 2;
+constexpr int kLsThreads = kLsGroups * kLsGroupThreads;
 constexpr int kLsLdX = kLsK + 4, kLsLdB = kLsN + 4, kLsLdA = kLsE + 4;   // floats per row
-constexpr size_t kLsSmem =
-    sizeof(float) * ((size_t)kLsStages * (kLsE * kLsLdX + kLsK + kLsK * kLsLdB) + (size_t)kLsK * kLsLdA);
+constexpr int kLsGroupFloats = kLsStages * (kLsE * kLsLdX + kLsK + kLsK * kLsLdB) + kLsK * kLsLdA;
+constexpr size_t kLsSmem = sizeof(float) * (size_t)kLsGroups * kLsGroupFloats;
+static_assert(kLsSmem > 114 * 1024 && kLsSmem <= 227 * 1024, "one CTA per SM");
 
-__global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
+__device__ __forceinline__ void ls_group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kLsGroupThreads) : "memory");
+}
+
+__global__ void __launch_bounds__(kLsThreads, 1) sr_gemm_fp32_list_kernel(const __grid_constant__ SrParams sp) {
   griddep_wait();                                  // the previous kernel of the generation is done
   griddep_launch_dependents();
   const GenParams& p = sp.g;
   extern __shared__ __align__(16) float ls_smem[];
-  float* Xs = ls_smem;                             // [stage][entry][kLsLdX]: raw x
+  const int g = threadIdx.x / kLsGroupThreads, t = threadIdx.x % kLsGroupThreads;
+  float* Xs = ls_smem + (size_t)g * kLsGroupFloats;  // [stage][entry][kLsLdX]: raw x
   float* Os = Xs + kLsStages * kLsE * kLsLdX;      // [stage][k]: o
   float* Bs = Os + kLsStages * kLsK;               // [stage][k][kLsLdB]: R^T rows
   float* As = Bs + kLsStages * kLsK * kLsLdB;      // [k][kLsLdA]: a per entry
-  __shared__ const float* rowp[kLsE];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  __shared__ const float* rowp_all[kLsGroups][kLsE];
+  const float** rowp = rowp_all[g];
+  const int lane = t & 31, warp = t >> 5;
   const int tx = lane & 15;
   const int ebase = warp * 4 + (lane >> 4) * 2;    // the lane's first entry in the tile
-  const int n0 = blockIdx.x * kLsN;
   const long long gen = p.st->gen;
   const uint8_t* slot_in = p.slots + (size_t)(gen & 1) * p.N;
   const int nrows = (int)*sp.amb_count;
-  const int KS = p.D / kLsK;
+  const int KS = p.D / kLsK, ctiles = p.D / kLsN;
+  const int items = ((nrows + kLsE - 1) / kLsE) * ctiles;
+  int n0 = 0;
 
   // one stage: x 16 entries x 8 chunks of 16 bytes (one per thread), o 8
   // chunks, R^T 32 rows x 16 chunks (4 per thread); entries past the list
@@ -395,16 +406,18 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
     }
     if (t < kLsK / 4) cp_async16(sr_smem_u32(Os + st * kLsK + 4 * t), sp.shift + k0 + 4 * t, 16u);
 #pragma unroll
-    for (int i = 0; i < (kLsK * kLsN / 4) / kLsThreads; ++i) {
-      const int q = t + kLsThreads * i, kr = q >> 4, c = (q & 15) * 4;
+    for (int i = 0; i < (kLsK * kLsN / 4) / kLsGroupThreads; ++i) {
+      const int q = t + kLsGroupThreads * i, kr = q >> 4, c = (q & 15) * 4;
       cp_async16(sr_smem_u32(Bs + (st * kLsK + kr) * kLsLdB + c), sp.rot_t + (size_t)(k0 + kr) * p.D + n0 + c, 16u);
     }
   };
 
-  for (int r0 = blockIdx.y * kLsE; r0 < nrows; r0 += gridDim.y * kLsE) {
-    __syncthreads();                                // rowp and the stages are reused
+  for (int item = blockIdx.x + g * gridDim.x; item < items; item += kLsGroups * gridDim.x) {
+    const int r0 = (item / ctiles) * kLsE, ct = item % ctiles;
+    n0 = ct * kLsN;
+    ls_group_sync(g);                              // rowp and the stages are reused
     if (t < kLsE) rowp[t] = (r0 + t < nrows) ? sr_row_ptr(sp, 2, r0 + t, slot_in) : nullptr;
-    __syncthreads();
+    ls_group_sync(g);
 #pragma unroll
     for (int s0 = 0; s0 < kLsStages - 1; ++s0) {
       if (s0 < KS) issue(s0);
@@ -417,23 +430,23 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
       for (int c = 0; c < 4; ++c) acc[e][c] = 0.0f;
     for (int step = 0; step < KS; ++step) {
       cp_async_wait<kLsStages - 2>();
-      __syncthreads();                              // this stage landed; every lane is done with As and
-                                                    // with the slot refilled next
+      ls_group_sync(g);                             // this stage landed; every lane is done with the
+                                                    // slot refilled next
       if (step + kLsStages - 1 < KS) issue(step + kLsStages - 1);
       cp_async_commit();
       const int st = step % kLsStages;
-      {                                             // a = fl(x - o): k = t mod 32, entries 4 (t / 32) ..
-        const int k = t & 31, m0 = (t >> 5) * 4;
-        const float* xs = Xs + (st * kLsE + m0) * kLsLdX + k;
-        const float o = Os[st * kLsK + k];
-        *reinterpret_cast<float4*>(As + k * kLsLdA + m0) =
+      {                                             // a = fl(x - o): k = lane, the warp's 4 entries
+        const int m0 = warp * 4;
+        const float* xs = Xs + (st * kLsE + m0) * kLsLdX + lane;
+        const float o = Os[st * kLsK + lane];
+        *reinterpret_cast<float4*>(As + lane * kLsLdA + m0) =
             make_float4(__fsub_rn(xs[0], o), __fsub_rn(xs[kLsLdX], o), __fsub_rn(xs[2 * kLsLdX], o),
                         __fsub_rn(xs[3 * kLsLdX], o));
       }
-      __syncthreads();
+      __syncwarp();                                 // a of the warp's entries, written by the warp
       const float* as = As + ebase;
       const float* bs = Bs + st * kLsK * kLsLdB + 4 * tx;
-#pragma unroll 8
+#pragma unroll
       for (int k = 0; k < kLsK; ++k) {
         const float2 av = *reinterpret_cast<const float2*>(as + k * kLsLdA);
         const float4 bv = *reinterpret_cast<const float4*>(bs + k * kLsLdB);
@@ -446,7 +459,7 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
         acc[1][2] = fmaf(av.y, bv.z, acc[1][2]);
         acc[1][3] = fmaf(av.y, bv.w, acc[1][3]);
       }
-    }
+    }                                               // (the next step's group barrier orders the As reuse)
     cp_async_wait<0>();
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -454,14 +467,19 @@ __global__ void __launch_bounds__(kLsThreads) sr_gemm_fp32_list_kernel(const __g
       float sg, sw;
       sr_tile_reduce(sp, acc[e], n0 + 4 * tx, sg, sw);
       if (tx == 0 && ent < nrows) {
-        sp.part2_g[(size_t)ent * sp.nct2 + blockIdx.x] = sg;
-        sp.part2_w[(size_t)ent * sp.nct2 + blockIdx.x] = sw;
+        sp.part2_g[(size_t)ent * sp.nct2 + ct] = sg;
+        sp.part2_w[(size_t)ent * sp.nct2 + ct] = sw;
       }
     }
   }
 }
 
-cudaError_t prepare_sr_list() {
+cudaError_t prepare_sr_list(int* ctas) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *ctas = sms > 0 ? sms : 1;
   return cudaFuncSetAttribute(sr_gemm_fp32_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLsSmem);
 }
 
@@ -688,9 +706,9 @@ cudaError_t launch_sr_gemm_fp32(const SrParams& sp, int mode, int max_rows, cuda
   const unsigned gx = (unsigned)((sp.g.D + kGbN - 1) / kGbN);
   if (mode == 2) {                                // split-operand paths: D % 256 == 0
     if (sp.g.D % kLsN != 0) return cudaErrorInvalidValue;
-    const int tiles = (max_rows + kLsE - 1) / kLsE;
-    const dim3 grid((unsigned)(sp.g.D / kLsN), (unsigned)std::max(1, std::min(tiles, 128)));
-    return launch_pdl(sr_gemm_fp32_list_kernel, grid, dim3(kLsThreads), kLsSmem, s, sp);
+    const int items = ((max_rows + kLsE - 1) / kLsE) * (sp.g.D / kLsN);
+    const int grid = std::max(1, std::min(sp.list_ctas, (items + kLsGroups - 1) / kLsGroups));
+    return launch_pdl(sr_gemm_fp32_list_kernel, dim3((unsigned)grid), dim3(kLsThreads), kLsSmem, s, sp);
   }
   const dim3 grid(gx, (unsigned)((max_rows + kGbM - 1) / kGbM));
   if (sp.g.D % 4 == 0) return launch_pdl(sr_gemm_fp32_kernel<true>, grid, dim3(256), 0, s, sp, mode);
