@@ -349,19 +349,19 @@ __global__ void __launch_bounds__(256, 2) sr_gemm_fp32_kernel(const __grid_const
 // entries x 4 columns per lane: lanes 0-15 take entries 0-1 of the warp, lanes
 // 16-31 entries 2-3, and lane tx = lane & 15 columns 4 tx .. 4 tx + 3 of the
 // 64-column tile, the layout the tile reduction expects). Each group has its
-// own 8-stage cp.async ring of the entries' rows of x, o and rows of R^T
-// (seven stages in flight cover the L2 latency of the short per-stage work)
-// and its own named barrier. Once a stage has landed, each warp forms
-// a = fl(x - o) K-major for its own four entries (so only a warp barrier
-// follows), and the inner loop is an 8-byte and a 16-byte shared load and
-// eight FMAs per k: every z stays one FMA chain over j ascending. The list is
+// own 4-stage cp.async ring of 64-deep slices of the entries' rows of x, o
+// and rows of R^T (three stages in flight cover the L2 latency of the short
+// per-stage work) and its own named barrier. Once a stage has landed, each
+// warp forms a = fl(x - o) K-major for its own four entries (so only a warp
+// barrier follows), and the inner loop is an 8-byte and a 16-byte shared load
+// and eight FMAs per k: every z stays one FMA chain over j ascending. The list is
 // short (a few hundred entries) and each chain is D FMAs long, so the time is
 // set by the busiest SM. Two groups per CTA and a ring per group that needs
 // more than half an SM's shared memory for the pair put exactly one CTA on
 // each SM; the grid is one CTA per SM, group g of CTA b takes items
 // b + g * grid, b + (2 + g) * grid, ..., so the first items of a short list
 // land on distinct SMs whatever order the CTAs are placed in.
-constexpr int kLsE = 16, kLsN = 64, kLsK = 32, kLsStages = 8, kLsGroupThreads = 128, kLsGroups = 2;
+constexpr int kLsE = 16, kLsN = 64, kLsK = 64, kLsStages = 4, kLsGroupThreads = 128, kLsGroups = 2;
 constexpr int kLsThreads = kLsGroups * kLsGroupThreads;
 constexpr int kLsLdX = kLsK + 4, kLsLdB = kLsN + 4, kLsLdA = kLsE + 4;   // floats per row
 constexpr int kLsGroupFloats = kLsStages * (kLsE * kLsLdX + kLsK + kLsK * kLsLdB) + kLsK * kLsLdA;
@@ -394,13 +394,14 @@ __global__ void __launch_bounds__(kLsThreads, 1) sr_gemm_fp32_list_kernel(const 
   const int items = ((nrows + kLsE - 1) / kLsE) * ctiles;
   int n0 = 0;
 
-  // one stage: x 16 entries x 8 chunks of 16 bytes (one per thread), o 8
-  // chunks, R^T 32 rows x 16 chunks (4 per thread); entries past the list
+  // one stage: x 16 entries x 16 chunks of 16 bytes (two per thread), o 16
+  // chunks, R^T 64 rows x 16 chunks (8 per thread); entries past the list
   // read zeros
   auto issue = [&](int step) {
     const int st = step % kLsStages, k0 = step * kLsK;
-    {
-      const int m = t >> 3, c = (t & 7) * 4;
+#pragma unroll
+    for (int i = 0; i < (kLsE * kLsK / 4) / kLsGroupThreads; ++i) {
+      const int qx = t + kLsGroupThreads * i, m = qx / (kLsK / 4), c = (qx % (kLsK / 4)) * 4;
       const float* xa = rowp[m];
       cp_async16(sr_smem_u32(Xs + (st * kLsE + m) * kLsLdX + c), xa ? xa + k0 + c : sp.shift, xa ? 16u : 0u);
     }
@@ -435,11 +436,12 @@ __global__ void __launch_bounds__(kLsThreads, 1) sr_gemm_fp32_list_kernel(const 
       if (step + kLsStages - 1 < KS) issue(step + kLsStages - 1);
       cp_async_commit();
       const int st = step % kLsStages;
-      {                                             // a = fl(x - o): k = lane, the warp's 4 entries
+#pragma unroll
+      for (int kk = lane; kk < kLsK; kk += 32) {   // a = fl(x - o): k = kk, the warp's 4 entries
         const int m0 = warp * 4;
-        const float* xs = Xs + (st * kLsE + m0) * kLsLdX + lane;
-        const float o = Os[st * kLsK + lane];
-        *reinterpret_cast<float4*>(As + lane * kLsLdA + m0) =
+        const float* xs = Xs + (st * kLsE + m0) * kLsLdX + kk;
+        const float o = Os[st * kLsK + kk];
+        *reinterpret_cast<float4*>(As + kk * kLsLdA + m0) =
             make_float4(__fsub_rn(xs[0], o), __fsub_rn(xs[kLsLdX], o), __fsub_rn(xs[2 * kLsLdX], o),
                         __fsub_rn(xs[3 * kLsLdX], o));
       }
