@@ -177,6 +177,8 @@ __global__ void close_eval_kernel(DevState* st) {
 // block 0 also writes the header. `out` may be device memory or a mapped,
 // page-locked host record.
 __global__ void best_gather_kernel(const __grid_constant__ GenParams p, unsigned char* out) {
+  griddep_wait();                                  // the generation before it has closed
+  griddep_launch_dependents();                     // the next generation's CTAs may take their places
   const unsigned long long bk = p.st->best_key;
   int idx = (int)(uint32_t)(bk & 0xFFFFFFFFull);
   if (idx < 0 || idx >= p.N) idx = 0;   // only before any evaluation
@@ -238,8 +240,8 @@ cudaError_t launch_close_eval(const GenParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_best_gather(const GenParams& p, void* staging, cudaStream_t s) {
-  best_gather_kernel<<<(unsigned)((p.D4 + 127) / 128), 128, 0, s>>>(p, static_cast<unsigned char*>(staging));
-  return cudaGetLastError();
+  return launch_pdl(best_gather_kernel, dim3((unsigned)((p.D4 + 127) / 128)), dim3(128), 0, s, p,
+                    static_cast<unsigned char*>(staging));
 }
 cudaError_t launch_normalize(const GenParams& p, cudaStream_t s) {
   normalize_kernel<<<(unsigned)p.N, 128, 0, s>>>(p);
