@@ -180,14 +180,18 @@ void de_destroy(de_ctx *ctx);
  * evaluation of every trial (FP32), strict '<' selection, best tracking. */
 int de_step(de_ctx *ctx);
 
-/* Enqueue `generations` (>= 0) generations. Runs of 2 or more are captured
- * once per distinct count into a CUDA graph and replayed. */
+/* Enqueue `generations` (>= 0) generations. Runs of 2 or more on a context
+ * with its own stream are captured once per distinct count into a CUDA graph
+ * (on the first run of that count, or by de_prepare_run) and replayed; a
+ * setter that changes the launch (kernel, launch shape, pipeline, base rule,
+ * wait limit) drops the cached graphs. */
 int de_run(de_ctx *ctx, int32_t generations);
 
 /* Capture and instantiate the graph that de_run(ctx, generations) replays,
  * without launching it: the population, fitness, best and generation count
  * are unchanged, and a later de_run of the same count only launches the
- * graph. A no-op returning DE_OK for counts below 2. DE_EINVAL for a NULL
+ * graph. A no-op returning DE_OK for counts below 2 and for a context on the
+ * legacy (NULL) stream, whose runs are not captured. DE_EINVAL for a NULL
  * context or a negative count, DE_ESTATE for a failed context, DE_ECUDA if
  * the capture or the instantiation fails. */
 int de_prepare_run(de_ctx *ctx, int32_t generations);
