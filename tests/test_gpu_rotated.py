@@ -375,6 +375,41 @@ def test_rotated_fp16_scaling_far_from_unit_boxes(obj, scale):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_rotated_long_ambiguous_list(prec):
+    """A population within 1e-7 of the optimum at D = 1024 sends most rows,
+    trial and parent, to the FP32 re-evaluation: over a thousand entries, more
+    work items than the re-evaluation's resident groups, so each group walks
+    several items. The re-evaluated values decide exactly as the FP32 path,
+    and the populations stay bit-identical to its own."""
+    N, D = 1024, 1024
+    a, o, R = make(N, D, "nec", "sr_rastrigin", prec="fp32", seed=23)
+    b, _, _ = make(N, D, "nec", "sr_rastrigin", prec=prec, seed=23)
+    try:
+        rng = np.random.default_rng(6)
+        pop = (o[None, :].astype(np.float64) + 1e-7 * rng.uniform(-1.0, 1.0, size=(N, D))).astype(np.float32)
+        a.set_population(pop)
+        b.set_population(pop)
+        most = 0
+        for g in range(3):
+            r0 = b.stats()["reselected"]
+            ta, fa, acca, _ = a.debug_step()
+            tb, fb, accb, _ = b.debug_step()
+            assert np.array_equal(ta.view(np.uint32), tb.view(np.uint32))
+            assert np.array_equal(acca, accb), "generation %d: selections differ" % g
+            most = max(most, b.stats()["reselected"] - r0)
+        # 320 rows or more in one generation: 20 tiles of 16 entries x 16 column
+        # tiles = 320 work items, more than the 2 x 152 resident groups
+        print("%s: at most %d rows re-evaluated in one generation" % (prec, most))
+        assert most >= 320, most
+        pa, _ = a.population()
+        pb, _ = b.population()
+        assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_rotated_checkpoint_resume(prec):
     """A split-path run saved after some generations and resumed in a fresh
     context continues bit for bit like the uninterrupted run (population,
